@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Benchmark of the simplex-domain hot path on GB300.
+
+Headline workload (one "step"): the Axilrod-Teller-Muto triple-dipole energy
+over all i < j < k of n = 1024 points uniform in a cube of side 10 (seed 1),
+nu = 1, eps = 1e-4: 178,433,024 triples on the lambda-mapped 3-simplex grid
+(two-branch recursive map plus the J = K plane), FP32 per triple, FP64
+reduction.  Metric: triples per second (whole job), with the same step timed
+for the bounding-box and linear (cube-root) maps, the dominant kernel timed
+live against the FP32 ALU roofline, an end-to-end number through the C ABI
+with host buffers, and the FP64 CPU oracle timed on the host cores.
+
+``--rows`` (default on at one GPU) also times every other kernel on the path
+at its own configuration (EDM n=1024 d=3, ATM energy+forces n=4096 and
+n=16384, EDM n=32768 d=256, stress loss forward/backward n=65536 d=64).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one replica per GPU under torchrun (the workload is independent
+per rank, no data collective; "scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "pairs/s and triplets/s, λ-map vs bounding-box on 1 GB300; % of HBM/FP32 roofline"
+WORKLOAD = "atm_n1024"
+NU, EPS = 1.0, 1e-4
+# FP32 operations per triple in the energy kernel's inner loop, pair terms
+# hoisted: three 3-vector dot products (3 FMUL + 6 FFMA), the cosine product
+# (2 FMUL), R = r_ij r_ik r_jk (2 FMUL), R^2 and R^3 (2 FMUL), and two FFMA
+# for the bracket and the sum: 9 FMUL + 8 FFMA = 25 flops (FMA = 2).
+FLOPS_PER_TRIPLE = 25
+FP32_LANES_PER_SM = 128
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rows", choices=["auto", "on", "off"], default="auto")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def time_steps(torch, fn, steps, warmup, flush=None):
+    """CUDA-event time of each step (ms) on the current stream, L2 flushed
+    (untimed) before every step when `flush` is given."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        if flush is not None:
+            flush()
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def triples(n):
+    return n * (n - 1) * (n - 2) // 6
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_energy_rate(x, seconds_min=10.0, i_hi=None):
+    """Times the FP64 oracle on this host: the whole sum (i_hi None) or the
+    triples with i < i_hi, repeated until `seconds_min` have passed."""
+    import oracle
+    oracle.build()
+    n = len(x)
+    if i_hi is None:
+        units = triples(n)
+        run = lambda: oracle.atm_energy(x, NU, EPS)  # noqa: E731
+    else:
+        units = sum((n - 1 - i) * (n - 2 - i) // 2 for i in range(i_hi))
+        run = lambda: oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)  # noqa: E731
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        run()
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_min:
+            break
+    return units * reps / el, units, reps, el
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    x = synth.make_points(WORKLOAD)
+    import oracle
+    oracle.build()
+    n = len(x)
+    i_hi = 40
+    units = sum((n - 1 - i) * (n - 2 - i) // 2 for i in range(i_hi))
+    for _ in range(args.warmup):
+        oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = units / (ms / 1e3)
+    sample = (f"triples with i < {i_hi} of the n=1024 workload ({units} of {triples(n)}) per step, "
+              "FP64 oracle, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "triplets/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(),
+        "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block():
+    w = synth.WORKLOADS[WORKLOAD]
+    return {"workload": f"ATM triple-dipole energy over i<j<k, n={w['n']} uniform in a cube of "
+                        f"side {w['side']:g}, seed {w['seed']}, nu=1, eps=1e-4 ({triples(w['n'])} triples)",
+            "map": "lambda (two-branch recursive 3-simplex map + J=K plane)",
+            "n": w["n"], "triples": triples(w["n"]),
+            "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write)"}
+
+
+# ------------------------------------------------------------------ our arm
+
+def rows_measure(torch, sx, peaks):
+    """Every other kernel of the path at its own configuration."""
+    out = {}
+    dev = "cuda"
+    hbm = peaks["hbm_gbs"]
+
+    def t_ms(fn, steps, warmup=1):
+        return statistics.median(time_steps(torch, fn, steps, warmup))
+
+    def kernel_ms(fn, steps=3, warmup=1):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        sx.simplex_profile(True)
+        for _ in range(steps):
+            fn()
+        ms, k, _ = sx.simplex_profile_read()
+        sx.simplex_profile(False)
+        return ms / max(k, 1)
+
+    # EDM n=1024, d=3: 524,800 FP32 outputs (2.1 MB): one launch is a few
+    # microseconds, so a step is a batch of 100 launches.
+    x = torch.from_numpy(synth.make_points("edm_n1024_d3")).to(dev)
+    o = torch.empty(1024 * 1025 // 2, device=dev)
+    pairs = 1024 * 1025 // 2
+    r = {"unit": "pairs/s", "pairs": pairs, "note": "batch of 100 launches per timed step; output L2-resident"}
+    for mp in ("lambda", "bbox", "linear"):
+        f = lambda: [sx.simplex_edm_packed(x, o, mp, "fp32") for _ in range(100)]  # noqa: E731
+        ms = t_ms(f, 5) / 100
+        r[mp] = pairs / (ms / 1e3)
+        r[mp + "_us"] = ms * 1e3
+    r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    out["edm_n1024_d3"] = r
+
+    # EDM n=32768, d=256 (FP32 SIMT path): 536,887,296 outputs, 2.15 GB written.
+    x = torch.from_numpy(synth.make_points("edm_n32768_d256")).to(dev)
+    o = torch.empty(32768 * 32769 // 2, device=dev)
+    pairs = o.numel()
+    r = {"unit": "pairs/s", "pairs": pairs, "prec": "fp32"}
+    for mp in ("lambda", "bbox"):
+        ms = kernel_ms(lambda: sx.simplex_edm_packed(x, o, mp, "fp32"))
+        r[mp] = pairs / (ms / 1e3)
+        r[mp + "_ms"] = ms
+    r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    r["hbm_frac_lambda"] = (4.0 * pairs / (r["lambda_ms"] / 1e3) / 1e9) / hbm
+    out["edm_n32768_d256"] = r
+    del x, o
+    torch.cuda.empty_cache()
+
+    # ATM n=4096 (differentiation config): energy, energy+forces.
+    x = torch.from_numpy(synth.make_points("atm_n4096")).to(dev)
+    n = 4096
+    r = {"unit": "triplets/s", "triples": triples(n)}
+    e = torch.empty((), dtype=torch.float64, device=dev)
+    for mp in ("lambda", "bbox", "linear"):
+        ws = sx.workspace("atm_energy", n, 3, mp)
+        ms = t_ms(lambda: sx.simplex_atm_energy(x, NU, EPS, e, mp, ws), 3)
+        r["energy_" + mp] = triples(n) / (ms / 1e3)
+    r["energy_lambda_vs_bbox"] = r["energy_lambda"] / r["energy_bbox"]
+    f = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    for mp in ("lambda", "bbox"):
+        ws = sx.workspace("atm_forces", n, 3, mp)
+        ms = t_ms(lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws), 3)
+        r["energy_forces_" + mp] = triples(n) / (ms / 1e3)
+    r["energy_forces_lambda_vs_bbox"] = r["energy_forces_lambda"] / r["energy_forces_bbox"]
+    out["atm_n4096"] = r
+
+    # ATM n=16384 (scale config): 7.33e11 triples.
+    n = 16384
+    x = torch.from_numpy(synth.make_points("atm_n16384")).to(dev)
+    r = {"unit": "triplets/s", "triples": triples(n)}
+    ws = sx.workspace("atm_forces", n, 3, "lambda")
+    ms = t_ms(lambda: sx.simplex_atm_energy(x, NU, EPS, e, "lambda", ws), 1, 0)
+    r["energy_lambda"] = triples(n) / (ms / 1e3)
+    f = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    ms = t_ms(lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, "lambda", ws), 1, 0)
+    r["energy_forces_lambda"] = triples(n) / (ms / 1e3)
+    out["atm_n16384"] = r
+    del ws
+    torch.cuda.empty_cache()
+
+    # Stress loss n=65536, d=64: forward (loss only) and backward.
+    w = synth.WORKLOADS["stress_n65536_d64"]
+    xn = synth.normal(w["n"], w["d"], w["seed"])
+    yn = synth.perturbed(xn, w["sigma"], w["y_seed"])
+    x = torch.from_numpy(xn).to(dev)
+    y = torch.from_numpy(yn).to(dev)
+    n = w["n"]
+    pairs = n * (n - 1) // 2
+    r = {"unit": "pairs/s", "pairs": pairs}
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    ws = sx.workspace("stress_fwd", n, w["d"], "lambda")
+    ms = t_ms(lambda: sx.simplex_stress_fwd(x, y, None, loss, "lambda", "fp32", ws), 2)
+    r["fwd_lambda"] = pairs / (ms / 1e3)
+    g = torch.empty_like(x)
+    ms = t_ms(lambda: sx.simplex_stress_bwd(x, y, 1.0, g, "lambda", "fp32"), 2)
+    r["bwd_lambda"] = pairs / (ms / 1e3)
+    out["stress_n65536_d64"] = r
+    return out
+
+
+def our_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1610_07394_gb300 as sx
+    sx.lib()  # fails loudly when the CUDA library is missing
+
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+
+    w = synth.WORKLOADS[WORKLOAD]
+    n = w["n"]
+    xh = synth.make_points(WORKLOAD)
+    x = torch.from_numpy(xh).cuda()
+    e = torch.empty((), dtype=torch.float64, device="cuda")
+    units = triples(n)
+    flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = lambda: flush_buf.fill_(1)  # noqa: E731
+    ws = {mp: sx.workspace("atm_energy", n, 3, mp) for mp in ("lambda", "bbox", "linear")}
+
+    def step(mp="lambda"):
+        sx.simplex_atm_energy(x, NU, EPS, e, mp, ws[mp])
+
+    clocks = Clocks(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sx.simplex_profile(True)
+    times = time_steps(torch, step, args.steps, 0, flush)
+    main_ms, main_k, launches = sx.simplex_profile_read()
+    sx.simplex_profile(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_step = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = t.item()
+    value = world * units / (ms_step / 1e3)
+    k_ms = main_ms / max(main_k, 1)
+    achieved = FLOPS_PER_TRIPLE * units / (k_ms / 1e3) / 1e12
+
+    # the same step on the other maps (same kernel body, same tile)
+    maps = {"lambda": units / (ms_step / 1e3)}
+    for mp in ("bbox", "linear"):
+        tt = time_steps(torch, lambda: step(mp), args.steps, 3, flush)
+        maps[mp] = units / (sum(tt) / len(tt) / 1e3)
+    maps["lambda_vs_bbox"] = maps["lambda"] / maps["bbox"]
+    maps["lambda_vs_linear"] = maps["lambda"] / maps["linear"]
+    maps["grid_blocks"] = {mp: sx.simplex_grid_blocks(3, -(-n // sx.simplex_block_rho("atm_energy")), mp)
+                           for mp in ("lambda", "bbox", "linear")}
+
+    # end to end through the C ABI with host buffers: H2D of x, the call, D2H of E
+    xp = torch.from_numpy(xh).pin_memory()
+    ep = torch.empty((), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        x.copy_(xp, non_blocking=True)
+        step()
+        ep.copy_(e, non_blocking=True)
+
+    te = time_steps(torch, e2e_step, args.steps, 3, flush)
+    e2e_ms = sum(te) / len(te)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e = {"value": world * units / (e2e_ms / 1e3), "unit": "triplets/s",
+           "h2d_bytes_per_step": int(xp.numel() * xp.element_size()),
+           "d2h_bytes_per_step": int(ep.numel() * ep.element_size())}
+
+    do_rows = args.rows == "on" or (args.rows == "auto" and world == 1)
+    rows = rows_measure(torch, sx, peaks) if (do_rows and rank == 0) else None
+    clk = clocks.stop()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_block(),
+        "maps": maps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "k_atm_energy<lambda>", "kernel_ms": k_ms,
+                     "flops_per_triple": FLOPS_PER_TRIPLE,
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
+                                   f"(unit counts and max clock; {peak_src} peaks file has no FP32 figure)"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1:
+        rate, u, reps, el = oracle_energy_rate(xh)
+        line["cpu_baseline"] = {"value": rate, "unit": "triplets/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the whole n=1024 sum ({u} triples) x{reps}, {el:.1f} s, "
+                                          "FP64 C oracle, 1 thread"}
+    if rows is not None:
+        line["rows"] = rows
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * simplex.h -- C ABI of libsimplex: block-space maps over discrete orthogonal
+ * simplices and the simplex-domain kernels they drive, for one GB300 (sm_103a).
+ *
+ * Paper: C. A. Navarro, B. Bustos, N. Hitschfeld, "Possibilities of Recursive
+ * GPU Mapping for Discrete Orthogonal Simplices", arXiv 1610.07394.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *    the library never frees or retains them.  `stream` is a cudaStream_t
+ *    (NULL = legacy default stream).  Work is enqueued on `stream` and the
+ *    call returns without synchronising; outputs are valid once the stream
+ *    reaches that point.
+ *  - Points are FP32, row-major n x d (row stride d floats).
+ *  - 2-simplex elements are pairs (i, j) with 0 <= j <= i < n, stored packed
+ *    row-major lower: index i(i+1)/2 + j (64-bit).  3-simplex elements are
+ *    triples 0 <= i <= j <= k < n, index k(k+1)(k+2)/6 + j(j+1)/2 + i.
+ *  - A block is a tile of rho consecutive points; nb = ceil(n / rho).  The
+ *    maps send grid blocks to data blocks:
+ *      SIMPLEX_MAP_LAMBDA  the recursive O(1) map (Sec. III-A eq. (map2d) for
+ *                          m=2; Sec. III-C two-branch map for m=3), nb padded
+ *                          up to a power of two and filtered ("approach n
+ *                          from above", Sec. III-A);
+ *      SIMPLEX_MAP_BBOX    bounding box f(x) = x with out-of-domain blocks
+ *                          exiting at once (Sec. I);
+ *      SIMPLEX_MAP_LINEAR  linear enumeration inverted with square / cube
+ *                          roots plus an exact integer fix-up (Sec. I and
+ *                          Sec. II on the earlier block-space maps).
+ *  - Return value: a simplex_status.  Argument errors are detected before
+ *    anything is enqueued and leave outputs untouched.  A failed launch
+ *    returns SIMPLEX_ECUDA; simplex_last_cuda_error() gives the cudaError_t.
+ *    Asynchronous faults surface at the caller's next synchronisation.
+ *  - Scratch: entry points that need scratch take (workspace, ws_bytes),
+ *    device memory owned by the caller, at least simplex_workspace_bytes()
+ *    bytes and 256-byte aligned.  The library allocates no device memory.
+ */
+#ifndef SIMPLEX_H
+#define SIMPLEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIMPLEX_OK = 0,
+    SIMPLEX_EINVAL = 1,       /* bad size, map, precision, or NULL pointer   */
+    SIMPLEX_EALIGN = 2,       /* pointer not aligned as documented           */
+    SIMPLEX_EOVERFLOW = 3,    /* size exceeds 64-bit indices or grid limits  */
+    SIMPLEX_EUNSUPPORTED = 4, /* valid request this build does not serve     */
+    SIMPLEX_ECUDA = 5,        /* a CUDA call failed                          */
+    SIMPLEX_EWORKSPACE = 6    /* workspace missing, too small or misaligned  */
+} simplex_status;
+
+typedef enum {
+    SIMPLEX_MAP_LAMBDA = 0,
+    SIMPLEX_MAP_BBOX = 1,
+    SIMPLEX_MAP_LINEAR = 2
+} simplex_map;
+
+typedef enum {
+    SIMPLEX_PREC_FP32 = 0,    /* every step in FP32 (difference form)        */
+    SIMPLEX_PREC_BF16X3 = 1,  /* Gram term on tensor cores, split BF16 hi+lo */
+    SIMPLEX_PREC_AUTO = 2     /* library choice by d                          */
+} simplex_prec;
+
+typedef enum {
+    SIMPLEX_OP_MAP2 = 0, SIMPLEX_OP_MAP3 = 1, SIMPLEX_OP_EDM = 2,
+    SIMPLEX_OP_ATM_ENERGY = 3, SIMPLEX_OP_ATM_FORCES = 4,
+    SIMPLEX_OP_STRESS_FWD = 5, SIMPLEX_OP_STRESS_BWD = 6
+} simplex_op;
+
+/* ABI version of this header (bumped on any signature change). */
+int simplex_abi_version(void);
+
+/* Human-readable text of a status code (static storage). */
+const char *simplex_strerror(int status);
+
+/* cudaError_t of the last failed CUDA call made by this library on the
+ * calling thread (0 if none). */
+int simplex_last_cuda_error(void);
+
+/* Block edge rho used by an operation (the library's tile size), for callers
+ * that want nb = ceil(n / rho). */
+int simplex_block_rho(int op, int64_t d, int prec);
+
+/*
+ * Number of grid blocks a map launches over nb data blocks per side for an
+ * m-simplex (m = 2 or 3), or -1 on bad arguments.  Grid shapes: LAMBDA m=2
+ * (p/2) x p, m=3 (p/2) x (p/2) x (p/2 + p/4 + 2) with p the power of two
+ * >= max(nb, 2) (the last two z-layers are the plane J = K, mapped by the
+ * 2-simplex map); BBOX nb^m; LINEAR nb(nb+1)/2 or nb(nb+1)(nb+2)/6.
+ */
+int64_t simplex_grid_blocks(int m, int64_t nb, int map);
+
+/*
+ * Decode table of a map (Sec. III-A eq. (map2d) / Sec. III-C): for every
+ * grid block w (x fastest, then y, then z) the data blocks it is sent to,
+ * (X0, Y0, X1, Y1) for m=2 (X = column block <= Y = row block) or
+ * (I0, J0, K0, I1, J1, K1) for m=3, with -1 in unused slots.  The second
+ * slot is used only by grid row 0 of the 2-simplex map, which takes the
+ * diagonal blocks 2w and 2w+1 (the paper leaves the diagonal out; this is
+ * the library's reading).
+ * out: device, simplex_grid_blocks(m, nb, map) * (2m) int32.
+ */
+int simplex_map_blocks(int m, int64_t nb, int map, int32_t *out, void *stream);
+
+/* The same table computed on the host by the same decode functions
+ * (no GPU needed).  out: host memory of the same size. */
+int simplex_map_blocks_host(int m, int64_t nb, int map, int32_t *out);
+
+/*
+ * Coverage of Delta_n^2 (Sec. III-A): launch the map's grid with rho x rho
+ * threads per block, every thread adds 1 to count[] for each element it is
+ * sent to, and threads sent to no element add 1 to *idle.
+ * Thread (r, c) of a block sent to (X, Y) takes element (Y rho + r, X rho + c)
+ * when column <= row < n.  A grid-row-0 block of the 2-simplex map reads its
+ * two diagonal triangles as one rho x (rho+1) rectangle: cell (r, c) is
+ * element (r, c) of block 2w when c <= r, else element (rho-1-r, c-r-1) of
+ * block 2w+1; thread (r, c) takes cell (r, c) and, if c == 0, cell (r, rho).
+ * n >= 1; rho in [1, 32] (0 = 16).
+ * count: device, n(n+1)/2 int32 (zeroed by the call); idle: device, 1 int64.
+ */
+int simplex_map2(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
+                 void *stream);
+
+/*
+ * Coverage of Delta_n^3 (Sec. III-B/III-C): rho^3 threads per block; a block
+ * walks its list of data blocks in order and thread (a, b, c) takes element
+ * (I rho + a, J rho + b, K rho + c) of each when i <= j <= k < n.
+ * n >= 1; rho in [1, 10] (0 = 8).
+ * count: device, n(n+1)(n+2)/6 int32 (zeroed by the call); idle: device, 1 int64.
+ */
+int simplex_map3(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
+                 void *stream);
+
+/*
+ * Packed lower-triangular Euclidean distance matrix (Sec. I: the EDM is a
+ * 2-simplex problem): out[i(i+1)/2 + j] = |x_i - x_j|^2 (squared distance)
+ * for 0 <= j <= i < n; the diagonal is exactly 0.
+ * x: device, n*d FP32, 4-byte aligned.  out: device, n(n+1)/2 FP32.
+ * prec: SIMPLEX_PREC_FP32 (difference form, any d) or SIMPLEX_PREC_BF16X3
+ * (Gram form on tensor cores with a hi+lo BF16 split and an FP32 recompute of
+ * near-zero entries; needs d % 16 == 0); AUTO picks BF16X3 when d >= 32 and
+ * d % 16 == 0.  Needs workspace for BF16X3 (see simplex_workspace_bytes).
+ */
+int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *out, int map,
+                       int prec, void *workspace, int64_t ws_bytes, void *stream);
+
+/*
+ * Axilrod-Teller-Muto triple-dipole energy over the 3-simplex (Sec. I:
+ * triple-interaction n-body is a 3-simplex problem):
+ *   E = sum_{i<j<k} nu (1 + 3 cos g_i cos g_j cos g_k) / (r_ij r_jk r_ki)^3,
+ * every squared side softened r^2 -> r^2 + eps in the cosines' norms and in
+ * the denominator (cosines from the law of cosines on unsoftened squares).
+ * d must be 3.  x: device, n*3 FP32.  energy: device, 1 double (written).
+ * Per-triple arithmetic is FP32; the reduction across blocks is FP64.
+ */
+int simplex_atm_energy(int64_t n, int64_t d, const float *x, float nu, float eps,
+                       double *energy, int map, void *workspace, int64_t ws_bytes,
+                       void *stream);
+
+/*
+ * ATM forces F = -dE/dx (n x 3 FP64, written) and, if `energy` is not NULL,
+ * the energy, on the same block grid: every triple adds dE/d(r^2) of its
+ * three sides to per-pair coefficients, which are turned into forces once
+ * per block; forces accumulate in FP64.
+ */
+int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu, float eps,
+                       double *energy, double *forces, int map, void *workspace,
+                       int64_t ws_bytes, void *stream);
+
+/*
+ * Stress loss over the packed EDM: L = sum_{i<j} (D_ij - delta_ij)^2 with
+ * D_ij = |x_i - x_j|^2 and delta_ij = |y_i - y_j|^2 recomputed from y.
+ * x, y: device, n*d FP32.  d_out: device, n(n+1)/2 FP32, or NULL to skip
+ * storing D.  loss: device, 1 double (written).
+ */
+int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const float *y,
+                       float *d_out, double *loss, int map, int prec,
+                       void *workspace, int64_t ws_bytes, void *stream);
+
+/*
+ * Gradient of the stress loss times `gscale`:
+ *   grad_i = gscale * 4 sum_{j != i} (D_ij - delta_ij)(x_i - x_j),
+ * with D and delta recomputed (never stored).  grad: device, n*d FP32,
+ * 16-byte aligned, written (zeroed by the call).
+ */
+int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
+                       double gscale, float *grad, int map, int prec,
+                       void *workspace, int64_t ws_bytes, void *stream);
+
+/* Bytes of workspace an operation needs (0 if none, -1 on bad arguments). */
+int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map, int prec);
+
+/*
+ * Tracing.  simplex_profile(1) clears the counters and starts recording;
+ * simplex_profile(0) stops.  While on, every entry point records a CUDA
+ * event pair around its main kernel on the call's stream (host bookkeeping
+ * only; at most 65536 pairs are kept).  The library counts every kernel it
+ * launches whether recording or not.
+ */
+int simplex_profile(int on);
+
+/* Waits for the recorded events and returns the summed duration of the
+ * timed main-kernel launches (ms), how many were timed, and how many kernels
+ * the library launched since the last simplex_profile(1).  Any pointer may
+ * be NULL. */
+int simplex_profile_read(double *main_ms, int64_t *main_launches, int64_t *all_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMPLEX_H */

@@ -1,0 +1,349 @@
+// atm.cu -- Axilrod-Teller-Muto triple-dipole energy and forces over the
+// 3-simplex {i < j < k} (Sec. I: the triple-interaction n-body problem is a
+// 3-simplex problem), one 32^3 tile of triples per data block, the block
+// chosen by a block-space map (Sec. III-C two-branch map, bounding box, or
+// linear enumeration with cube roots).
+//
+// Per triple (i, j, k) with edge vectors e_ij = x_j - x_i, e_ik = x_k - x_i,
+// e_jk = x_k - x_j and softened inverse lengths r = (|e|^2 + eps)^{-1/2}:
+//   e = nu R^3 (1 + 3 d_i d_j d_k R^2),  R = r_ij r_ik r_jk,
+// with the vertex dot products d_i = e_ij . e_ik, d_j = -e_ij . e_jk,
+// d_k = e_ik . e_jk (so cos g_i = d_i r_ij r_ik, and R^2 = 1/(s_a s_b s_c)).
+// The dot products are taken from the edge vectors, not from the law of
+// cosines on squared lengths: for a triangle with one short side the latter
+// cancels catastrophically in FP32, and such close triples dominate E.
+//
+// Tile layout (256 threads): thread (ti, tj), ti, tj in [0, 16), owns the
+// four pairs (i, j) = (ti + 16p, tj + 16q), p, q in {0, 1}, and walks the 32
+// points k of the third tile.  Pair terms are computed once per tile and
+// kept in shared memory: for each (j, k) and (i, k) the edge vector and its
+// r.  The order constraint and the padding past n are folded into r:
+// r_ij = 0 unless i < j < n and r_jk = 0 unless j < k < n, which zeroes every
+// term outside the simplex without a branch.  Per-thread sums are FP32 within
+// a tile and FP64 across tiles; the block sum is FP64 and one FP64 partial
+// per block goes to the workspace, reduced deterministically by a second
+// pass.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sx {
+
+constexpr int R_ = kAtmRho;  // 32
+
+struct AtmTables {
+    float4 xs[3][R_];        // tiles I, J, K: (x, y, z, 0)
+    float4 tb[R_][2][16];    // [k][q][t]: (e_jk, r_jk) of pair (j = t + 16q, k)
+    float4 tc[R_][2][16];    // [k][p][t]: (e_ik, r_ik) of pair (i = t + 16p, k)
+};
+
+// Loads the three point tiles (zero past n).
+__device__ __forceinline__ void load_tiles(const float *__restrict__ x, int64_t n, int I, int J,
+                                           int K, AtmTables &T) {
+    const int tid = threadIdx.x;
+    if (tid < 3 * R_) {
+        const int which = tid / R_, o = tid % R_;
+        const int blk = which == 0 ? I : which == 1 ? J : K;
+        const int64_t g = (int64_t)blk * R_ + o;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < n) v = make_float4(__ldg(x + 3 * g), __ldg(x + 3 * g + 1), __ldg(x + 3 * g + 2), 0.f);
+        T.xs[which][o] = v;
+    }
+}
+
+// Pair tables of the (j, k) and (i, k) sides.
+__device__ __forceinline__ float4 edge(float4 from, float4 to) {
+    return make_float4(to.x - from.x, to.y - from.y, to.z - from.z, 0.0f);
+}
+
+__device__ __forceinline__ float rinv(float4 e, float eps) {
+    return 1.0f / sqrtf(fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps))));
+}
+
+__device__ __forceinline__ void build_tables(int64_t n, int I, int J, int K, float eps,
+                                             AtmTables &T) {
+    for (int e = threadIdx.x; e < R_ * R_; e += 256) {
+        const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
+        const int64_t gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
+        float4 b = edge(T.xs[1][o], T.xs[2][k]);
+        b.w = (gj < gk && gk < n) ? rinv(b, eps) : 0.0f;
+        T.tb[k][half][t] = b;
+        float4 c = edge(T.xs[0][o], T.xs[2][k]);
+        c.w = rinv(c, eps);
+        T.tc[k][half][t] = c;
+    }
+}
+
+struct PairConst {
+    float4 e;    // e_ij = x_j - x_i, w = r_ij (0 outside i < j < n)
+    float3 f;    // -3 e_ij
+};
+
+__device__ __forceinline__ PairConst pair_const(int64_t n, int I, int J, int i, int j, float eps,
+                                                const AtmTables &T) {
+    PairConst c;
+    c.e = edge(T.xs[0][i], T.xs[1][j]);
+    const int64_t gi = (int64_t)I * R_ + i, gj = (int64_t)J * R_ + j;
+    c.e.w = (gi < gj && gj < n) ? rinv(c.e, eps) : 0.0f;
+    c.f = make_float3(-3.0f * c.e.x, -3.0f * c.e.y, -3.0f * c.e.z);
+    return c;
+}
+
+__device__ __forceinline__ float dot3(float4 a, float4 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+
+__device__ __forceinline__ float dot3(float3 a, float4 b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
+}
+
+// One triple's energy without nu: R^3 (1 + 3 d_i d_j d_k R^2) added to acc;
+// B = (e_jk, r_jk), C = (e_ik, r_ik).
+__device__ __forceinline__ void triple_energy(float4 B, float4 C, const PairConst &c, float &acc) {
+    const float di = dot3(c.e, C);                 // d_i
+    const float dj3 = dot3(c.f, B);                // 3 d_j
+    const float dk = dot3(C, B);                   // d_k
+    const float D3 = (di * dj3) * dk;              // 3 d_i d_j d_k
+    const float R = (c.e.w * C.w) * B.w;
+    const float R2 = R * R;
+    const float R3 = R2 * R;
+    acc = fmaf(R3, fmaf(D3, R2, 1.0f), acc);
+}
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_atm_energy(int64_t n, const float *__restrict__ x,
+                                                    float nu, float eps, int nb, int p,
+                                                    double *__restrict__ partials) {
+    __shared__ AtmTables T;
+    __shared__ double red[8];
+    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+    double total = 0.0;
+    for (int t = 0; t < L.cnt; ++t) {
+        const int I = L.i[t], J = L.j[t], K = L.k[t];
+        if (t) __syncthreads();
+        load_tiles(x, n, I, J, K, T);
+        __syncthreads();
+        build_tables(n, I, J, K, eps, T);
+        PairConst pc[2][2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+        __syncthreads();
+        float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
+        for (int k = 0; k < R_; ++k) {
+            const float4 B0 = T.tb[k][0][tj], B1 = T.tb[k][1][tj];
+            const float4 C0 = T.tc[k][0][ti], C1 = T.tc[k][1][ti];
+            triple_energy(B0, C0, pc[0][0], acc[0][0]);
+            triple_energy(B1, C0, pc[0][1], acc[0][1]);
+            triple_energy(B0, C1, pc[1][0], acc[1][0]);
+            triple_energy(B1, C1, pc[1][1], acc[1][1]);
+        }
+        total += ((double)acc[0][0] + (double)acc[0][1]) + ((double)acc[1][0] + (double)acc[1][1]);
+    }
+    const double s = block_sum_f64<256>(total, red);
+    if (threadIdx.x == 0) {
+        const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+        partials[bid] = (double)nu * s;
+    }
+}
+
+// ---------------------------------------------------------------- forces
+
+struct AtmForceSmem {
+    AtmTables T;
+    float wjk[R_][R_ + 1];   // [k][j]: sum over i of de/db
+    float wik[R_][R_ + 1];   // [k][i]: sum over j of de/dc
+    float wij[R_][R_ + 1];   // [i][j]: sum over k of de/da
+};
+
+// One triple: energy into acc and the derivatives of e (without nu) with
+// respect to the squared sides a = |e_ij|^2, b = |e_jk|^2, c = |e_ik|^2.
+// With D = d_i d_j d_k, Q = R^2 = 1/P, G = 1.5 (1 + 5 D Q):
+//   de/da = R^3 (3 Q dD/da - G / s_a), and likewise for b and c, where
+//   dD/da = (d_j d_k + d_i d_k - d_i d_j)/2, dD/db = (d_i d_k + d_i d_j - d_j d_k)/2,
+//   dD/dc = (d_j d_k + d_i d_j - d_i d_k)/2  (from 2 d_i = a + c - b, etc.),
+// and 1/s = r^2.
+__device__ __forceinline__ void triple_grad(float4 B, float4 C, const PairConst &c, float &acc,
+                                            float &ea, float &eb, float &ec) {
+    const float di = dot3(c.e, C);
+    const float dj = -dot3(c.e, B);
+    const float dk = dot3(C, B);
+    const float pij = di * dj, pjk = dj * dk, pik = di * dk;
+    const float D = pij * dk;
+    const float R = (c.e.w * C.w) * B.w;
+    const float Q = R * R;
+    const float R3 = Q * R;
+    const float DQ = D * Q;
+    acc = fmaf(R3, fmaf(3.0f, DQ, 1.0f), acc);
+    const float G = fmaf(7.5f, DQ, 1.5f);
+    const float hS = 0.5f * (pij + pjk + pik);
+    const float Q3 = 3.0f * Q;
+    ea = R3 * fmaf(Q3, hS - pij, -G * (c.e.w * c.e.w));
+    eb = R3 * fmaf(Q3, hS - pjk, -G * (B.w * B.w));
+    ec = R3 * fmaf(Q3, hS - pik, -G * (C.w * C.w));
+}
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__restrict__ x,
+                                                    float nu, float eps, int nb, int p,
+                                                    double *__restrict__ partials,
+                                                    double *__restrict__ forces) {
+    __shared__ AtmForceSmem S;
+    __shared__ double red[8];
+    AtmTables &T = S.T;
+    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4, lane = tid & 31;
+    double total = 0.0;
+    for (int t = 0; t < L.cnt; ++t) {
+        const int I = L.i[t], J = L.j[t], K = L.k[t];
+        if (t) __syncthreads();
+        load_tiles(x, n, I, J, K, T);
+        for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
+        __syncthreads();
+        build_tables(n, I, J, K, eps, T);
+        PairConst pc[2][2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+        __syncthreads();
+        float acc = 0.0f;
+        float wa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int k = 0; k < R_; ++k) {
+            const float4 B0 = T.tb[k][0][tj], B1 = T.tb[k][1][tj];
+            const float4 C0 = T.tc[k][0][ti], C1 = T.tc[k][1][ti];
+            float ea, eb[2][2], ec[2][2];
+            triple_grad(B0, C0, pc[0][0], acc, ea, eb[0][0], ec[0][0]); wa[0][0] += ea;
+            triple_grad(B1, C0, pc[0][1], acc, ea, eb[0][1], ec[0][1]); wa[0][1] += ea;
+            triple_grad(B0, C1, pc[1][0], acc, ea, eb[1][0], ec[1][0]); wa[1][0] += ea;
+            triple_grad(B1, C1, pc[1][1], acc, ea, eb[1][1], ec[1][1]); wa[1][1] += ea;
+            // side (j, k): sum over the 16 i of this half-warp (lanes with the same tj)
+            float sb0 = eb[0][0] + eb[1][0], sb1 = eb[0][1] + eb[1][1];
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                sb0 += __shfl_xor_sync(0xffffffffu, sb0, o);
+                sb1 += __shfl_xor_sync(0xffffffffu, sb1, o);
+            }
+            if (ti == 0) { S.wjk[k][tj] = sb0; S.wjk[k][tj + 16] = sb1; }
+            // side (i, k): sum over the two tj of this warp, then across warps
+            float sc0 = ec[0][0] + ec[0][1], sc1 = ec[1][0] + ec[1][1];
+            sc0 += __shfl_xor_sync(0xffffffffu, sc0, 16);
+            sc1 += __shfl_xor_sync(0xffffffffu, sc1, 16);
+            if (lane < 16) { atomicAdd(&S.wik[k][ti], sc0); atomicAdd(&S.wik[k][ti + 16], sc1); }
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) S.wij[ti + 16 * a][tj + 16 * b] = wa[a][b];
+        total += (double)acc;
+        __syncthreads();
+        // Pair coefficients -> gradient: grad_p += 2 sum_q w_pq (x_p - x_q).
+        if (tid < 6 * R_) {
+            const int atom = tid >> 1, half = tid & 1;
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            const int which = atom / R_, o = atom % R_;
+            const float4 xp = T.xs[which][o];
+            for (int q = 0; q < R_; ++q) {
+                float w;
+                float4 xq;
+                if (which == 0) {
+                    if (half == 0) { w = S.wij[o][q]; xq = T.xs[1][q]; }
+                    else { w = S.wik[q][o]; xq = T.xs[2][q]; }
+                } else if (which == 1) {
+                    if (half == 0) { w = S.wij[q][o]; xq = T.xs[0][q]; }
+                    else { w = S.wjk[q][o]; xq = T.xs[2][q]; }
+                } else {
+                    if (half == 0) { w = S.wjk[o][q]; xq = T.xs[1][q]; }
+                    else { w = S.wik[o][q]; xq = T.xs[0][q]; }
+                }
+                gx = fmaf(w, xp.x - xq.x, gx);
+                gy = fmaf(w, xp.y - xq.y, gy);
+                gz = fmaf(w, xp.z - xq.z, gz);
+            }
+            gx += __shfl_xor_sync(0xffffffffu, gx, 1);
+            gy += __shfl_xor_sync(0xffffffffu, gy, 1);
+            gz += __shfl_xor_sync(0xffffffffu, gz, 1);
+            const int blk = which == 0 ? I : which == 1 ? J : K;
+            const int64_t g = (int64_t)blk * R_ + o;
+            if (half == 0 && g < n) {
+                const double f = -2.0 * (double)nu;
+                atomicAdd(forces + 3 * g, f * gx);
+                atomicAdd(forces + 3 * g + 1, f * gy);
+                atomicAdd(forces + 3 * g + 2, f * gz);
+            }
+        }
+    }
+    if (partials) {
+        const double s = block_sum_f64<256>(total, red);
+        if (tid == 0) {
+            const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+            partials[bid] = (double)nu * s;
+        }
+    }
+}
+
+static int atm_check(int64_t n, int64_t d, const float *x, int map, void *ws, int64_t ws_bytes,
+                     Grid &g, int64_t &nb) {
+    if (n < 1 || d != 3 || !x || map < MAP_LAMBDA || map > MAP_LINEAR) return d != 3 && d > 0 ? SIMPLEX_EUNSUPPORTED : SIMPLEX_EINVAL;
+    if (!aligned(x, 4)) return SIMPLEX_EALIGN;
+    if (n > (1 << 22)) return SIMPLEX_EOVERFLOW;
+    nb = (n + R_ - 1) / R_;
+    g = grid3(nb, map);
+    if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
+    const int64_t need = 8 * (g.gx * g.gy * g.gz + kReduceSlots);
+    if (!ws || ws_bytes < need || !aligned(ws, 256)) return SIMPLEX_EWORKSPACE;
+    return SIMPLEX_OK;
+}
+
+}  // namespace sx
+
+using namespace sx;
+
+extern "C" int simplex_atm_energy(int64_t n, int64_t d, const float *x, float nu, float eps,
+                                  double *energy, int map, void *workspace, int64_t ws_bytes,
+                                  void *stream) {
+    if (!energy) return SIMPLEX_EINVAL;
+    Grid g;
+    int64_t nb;
+    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb);
+    if (st) return st;
+    if (!aligned(energy, 8)) return SIMPLEX_EALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = (double *)workspace;
+    const int64_t blocks = g.gx * g.gy * g.gz;
+    double *tmp = partials + blocks;
+    prof_begin(s);
+    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    prof_end(s);
+    note_launches(1);
+    if ((st = launch_status())) return st;
+    return reduce_partials(partials, blocks, tmp, energy, s);
+}
+
+extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu, float eps,
+                                  double *energy, double *forces, int map, void *workspace,
+                                  int64_t ws_bytes, void *stream) {
+    if (!forces) return SIMPLEX_EINVAL;
+    Grid g;
+    int64_t nb;
+    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb);
+    if (st) return st;
+    if (!aligned(forces, 8) || (energy && !aligned(energy, 8))) return SIMPLEX_EALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = energy ? (double *)workspace : nullptr;
+    const int64_t blocks = g.gx * g.gy * g.gz;
+    if ((st = cuda_status(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s)))) return st;
+    prof_begin(s);
+    if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    else k_atm_forces<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    prof_end(s);
+    note_launches(1);
+    if ((st = launch_status())) return st;
+    if (energy) return reduce_partials(partials, blocks, partials + blocks, energy, s);
+    return SIMPLEX_OK;
+}

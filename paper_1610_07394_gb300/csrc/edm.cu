@@ -1,0 +1,64 @@
+// edm.cu -- packed lower-triangular Euclidean distance matrix over the
+// 2-simplex {j <= i} (Sec. I names the EDM as a 2-simplex problem), one
+// 32 x 32 tile per data block, the block chosen by a block-space map
+// (Sec. III-A eq. (map2d), bounding box, or linear enumeration).
+#include "common.cuh"
+#include "kernels.h"
+#include "tile.cuh"
+
+namespace sx {
+
+// FP32 difference form: out[i(i+1)/2 + j] = sum_t (x_it - x_jt)^2.
+template <int MAP>
+__global__ void __launch_bounds__(256) k_edm_simt(int64_t n, int d, const float *__restrict__ x,
+                                                  float *__restrict__ out, int nb) {
+    __shared__ TileSmem sm;
+    const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = 0; t < L.cnt; ++t) {
+        const int64_t row0 = (int64_t)L.y[t] * kEdmRho, col0 = (int64_t)L.x[t] * kEdmRho;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        tile_sqdist(x, n, d, row0, col0, sm, acc);
+        const int64_t j = col0 + lane;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int64_t i = row0 + w + 8 * m;
+            if (j <= i && i < n) out[i * (i + 1) / 2 + j] = acc[m];
+        }
+    }
+}
+
+int edm_rho(int64_t d, int prec) {
+    (void)d; (void)prec;
+    return kEdmRho;
+}
+
+int64_t edm_workspace_bytes(int64_t n, int64_t d, int map, int prec) {
+    (void)n; (void)d; (void)map; (void)prec;
+    return 0;
+}
+
+}  // namespace sx
+
+using namespace sx;
+
+extern "C" int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *out, int map,
+                                  int prec, void *workspace, int64_t ws_bytes, void *stream) {
+    (void)workspace; (void)ws_bytes;
+    if (n < 1 || d < 1 || !x || !out || map < MAP_LAMBDA || map > MAP_LINEAR) return SIMPLEX_EINVAL;
+    if (prec < SIMPLEX_PREC_FP32 || prec > SIMPLEX_PREC_AUTO) return SIMPLEX_EINVAL;
+    if (prec == SIMPLEX_PREC_BF16X3) return SIMPLEX_EUNSUPPORTED;
+    if (!aligned(x, 4) || !aligned(out, 4)) return SIMPLEX_EALIGN;
+    if (d > (1 << 24) || n > ((int64_t)1 << 31) || n * d > ((int64_t)1 << 40)) return SIMPLEX_EOVERFLOW;
+    const int64_t nb = (n + kEdmRho - 1) / kEdmRho;
+    const Grid g = grid2(nb, map);
+    if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
+    cudaStream_t s = (cudaStream_t)stream;
+    prof_begin(s);
+    if (map == MAP_LAMBDA) k_edm_simt<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
+    else if (map == MAP_BBOX) k_edm_simt<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
+    else k_edm_simt<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
+    prof_end(s);
+    note_launches(1);
+    return launch_status();
+}

@@ -1,0 +1,232 @@
+// maps.cuh -- block-space maps from a CUDA grid onto discrete orthogonal
+// simplices, evaluated in registers at the start of a block.
+//
+// Paper: Navarro, Bustos, Hitschfeld, "Possibilities of Recursive GPU Mapping
+// for Discrete Orthogonal Simplices" (arXiv 1610.07394).
+//
+//  * lambda, m = 2 (Sec. III-A, eq. (map2d)): grid (p/2) x p for p = 2^k
+//    blocks per side.  For w_y >= 1, b = 2^floor(log2 w_y) and
+//    q = floor(w_x / b); the block goes to (w_x + q b, w_y + 2 q b), i.e.
+//    (column X, row Y) with X < Y.  floor(log2 y) is (32 - 1) - clz(y) and
+//    2^floor(log2 y) is 1 << that (the paper's printed bit formulas are off by
+//    one; these are the exact forms).  Grid row 0 is not part of the
+//    recursive set; this library gives block w_x of that row the two
+//    diagonal blocks 2 w_x and 2 w_x + 1.
+//  * lambda, m = 3 (Sec. III-C, "Alternative Map for 3-Simplices"): grid
+//    (p/2) x (p/2) x (p/2 + p/4 + 2).  z < p/2 is the main cube of the
+//    two-branch recursive set; p/2 <= z < 3p/4 holds the cubes of the
+//    recursive halves, level b = 2^floor(log2 w_y) in grid rows [b, 2b),
+//    sub-problem q = floor(w_x / b) at data offset 2 q b, cube depth b.  A
+//    cube of side h at offset off sends its local point (s, u, v) to
+//    (off+u, off+s, off+h+v) when u <= s (the paper's "inside" case) and to
+//    (off+v, off+h+s, off+h+u) otherwise (its reflected case), covering the
+//    blocks I <= J < K.  The last two z-layers form a (p/2) x p grid that the
+//    m = 2 map sends onto the plane J = K (left out of the recursive set).
+//  * bounding box (Sec. I): the identity, blocks outside the simplex exit.
+//  * linear (Sec. I, enumeration map g; the root-based block maps of the
+//    authors' earlier work, Sec. II): a 1-D grid over the row-major
+//    enumeration, inverted with sqrtf / cbrtf and then fixed up exactly in
+//    integer arithmetic.
+//
+// Every function is __host__ __device__ so the host-side decode table can be
+// compared against an independent construction without a GPU.
+#pragma once
+#include <cstdint>
+#include <cmath>
+
+#if defined(__CUDACC__)
+#define SX_HD __host__ __device__ __forceinline__
+#else
+#define SX_HD inline
+#endif
+
+namespace sx {
+
+enum MapKind { MAP_LAMBDA = 0, MAP_BBOX = 1, MAP_LINEAR = 2 };
+
+// floor(log2 v) for v >= 1: (word bits - 1) - clz(v).
+SX_HD int floor_log2(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+    return 31 - __clz(v);
+#else
+    return 31 - __builtin_clz(v);
+#endif
+}
+
+// The power of two p >= max(v, 2) the recursive maps are built on.
+SX_HD int64_t pow2_at_least(int64_t v) {
+    int64_t p = 2;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Up to two data blocks of a 2-simplex (x = column block, y = row block,
+// x <= y); `pair` marks the diagonal pair of grid row 0 of the lambda map,
+// whose blocks are d0 = 2 w_x and d1 = 2 w_x + 1 (before filtering).
+struct List2 {
+    int cnt;
+    int x[2], y[2];
+    bool pair;
+    int d0, d1;
+};
+
+// Up to two data blocks of a 3-simplex (i <= j <= k).
+struct List3 {
+    int cnt;
+    int i[2], j[2], k[2];
+    bool pair;
+};
+
+SX_HD void push2(List2 &L, int x, int y, int nb) {
+    if (y < nb) { L.x[L.cnt] = x; L.y[L.cnt] = y; ++L.cnt; }
+}
+
+SX_HD void push3(List3 &L, int i, int j, int k, int nb) {
+    if (k < nb) { L.i[L.cnt] = i; L.j[L.cnt] = j; L.k[L.cnt] = k; ++L.cnt; }
+}
+
+// ---------------------------------------------------------------- m = 2
+
+SX_HD List2 decode2_lambda(uint32_t wx, uint32_t wy, int nb) {
+    List2 L;
+    L.cnt = 0; L.pair = false; L.d0 = L.d1 = -1;
+    if (wy == 0) {
+        L.pair = true;
+        L.d0 = (int)(2 * wx);
+        L.d1 = (int)(2 * wx + 1);
+        push2(L, L.d0, L.d0, nb);
+        push2(L, L.d1, L.d1, nb);
+        return L;
+    }
+    const int l = floor_log2(wy);        // recursion level: b = 2^l
+    const uint32_t q = wx >> l;          // which square of that level
+    push2(L, (int)(wx + (q << l)), (int)(wy + (q << (l + 1))), nb);
+    return L;
+}
+
+SX_HD List2 decode2_bbox(uint32_t wx, uint32_t wy, int nb) {
+    List2 L;
+    L.cnt = 0; L.pair = false; L.d0 = L.d1 = -1;
+    if (wx <= wy) push2(L, (int)wx, (int)wy, nb);
+    return L;
+}
+
+// Row-major enumeration of {x <= y}: l = y(y+1)/2 + x.
+SX_HD void tri_root(int64_t l, int64_t &y, int64_t &x) {
+    float f = sqrtf(8.0f * (float)l + 1.0f);
+    int64_t r = (int64_t)((f - 1.0f) * 0.5f);
+    if (r < 0) r = 0;
+    while (r > 0 && r * (r + 1) / 2 > l) --r;
+    while ((r + 1) * (r + 2) / 2 <= l) ++r;
+    y = r;
+    x = l - r * (r + 1) / 2;
+}
+
+SX_HD List2 decode2_linear(int64_t l, int nb) {
+    List2 L;
+    L.cnt = 0; L.pair = false; L.d0 = L.d1 = -1;
+    int64_t y, x;
+    tri_root(l, y, x);
+    push2(L, (int)x, (int)y, nb);
+    return L;
+}
+
+// ---------------------------------------------------------------- m = 3
+
+SX_HD void cube3(List3 &L, int h, int off, int s, int u, int v, int nb) {
+    if (u <= s) push3(L, off + u, off + s, off + h + v, nb);
+    else push3(L, off + v, off + h + s, off + h + u, nb);
+}
+
+SX_HD List3 decode3_lambda(uint32_t wx, uint32_t wy, uint32_t wz, int p, int nb) {
+    List3 L;
+    L.cnt = 0; L.pair = false;
+    const uint32_t h0 = (uint32_t)p >> 1, q4 = (uint32_t)p >> 2;
+    if (wz < h0) {                       // main cube, h(w) = w + (0, n/2, 0)
+        cube3(L, (int)h0, 0, (int)wx, (int)wy, (int)wz, nb);
+    } else if (wz < h0 + q4) {           // cubes of the recursive halves
+        if (wy == 0) return L;
+        const int l = floor_log2(wy);
+        const uint32_t b = 1u << l, z = wz - h0;
+        if (z >= b) return L;
+        const uint32_t q = wx >> l;
+        cube3(L, (int)b, (int)(q << (l + 1)), (int)(wx - (q << l)), (int)(wy - b), (int)z, nb);
+    } else {                             // plane J = K via the m = 2 map
+        const uint32_t wy2 = wy + (wz - h0 - q4) * h0;
+        List2 P = decode2_lambda(wx, wy2, nb);
+        L.pair = P.pair;
+        for (int t = 0; t < P.cnt; ++t) push3(L, P.x[t], P.y[t], P.y[t], nb);
+    }
+    return L;
+}
+
+SX_HD List3 decode3_bbox(uint32_t wx, uint32_t wy, uint32_t wz, int nb) {
+    List3 L;
+    L.cnt = 0; L.pair = false;
+    if (wx <= wy && wy <= wz) push3(L, (int)wx, (int)wy, (int)wz, nb);
+    return L;
+}
+
+SX_HD int64_t tet(int64_t k) { return k * (k + 1) * (k + 2) / 6; }
+
+// Row-major enumeration of {i <= j <= k}: l = k(k+1)(k+2)/6 + j(j+1)/2 + i.
+SX_HD List3 decode3_linear(int64_t l, int nb) {
+    List3 L;
+    L.cnt = 0; L.pair = false;
+    float f = cbrtf(6.0f * (float)l);
+    int64_t k = (int64_t)f - 1;
+    if (k < 0) k = 0;
+    while (k > 0 && tet(k) > l) --k;
+    while (tet(k + 1) <= l) ++k;
+    int64_t j, i;
+    tri_root(l - tet(k), j, i);
+    push3(L, (int)i, (int)j, (int)k, nb);
+    return L;
+}
+
+// ---------------------------------------------------------------- grids
+
+struct Grid { int64_t gx, gy, gz; int p; };
+
+SX_HD Grid grid2(int64_t nb, int map) {
+    Grid g; g.gz = 1; g.p = 0;
+    if (map == MAP_LAMBDA) {
+        int64_t p = pow2_at_least(nb);
+        g.p = (int)p; g.gx = p / 2; g.gy = p;
+    } else if (map == MAP_BBOX) {
+        g.gx = nb; g.gy = nb;
+    } else {
+        g.gx = nb * (nb + 1) / 2; g.gy = 1;
+    }
+    return g;
+}
+
+SX_HD Grid grid3(int64_t nb, int map) {
+    Grid g; g.p = 0;
+    if (map == MAP_LAMBDA) {
+        int64_t p = pow2_at_least(nb);
+        g.p = (int)p; g.gx = p / 2; g.gy = p / 2; g.gz = p / 2 + p / 4 + 2;
+    } else if (map == MAP_BBOX) {
+        g.gx = nb; g.gy = nb; g.gz = nb;
+    } else {
+        g.gx = nb * (nb + 1) * (nb + 2) / 6; g.gy = 1; g.gz = 1;
+    }
+    return g;
+}
+
+// Decode of grid block (wx, wy, wz) for a map chosen at compile time.
+template <int MAP>
+SX_HD List2 decode2(uint32_t wx, uint32_t wy, int nb) {
+    if (MAP == MAP_LAMBDA) return decode2_lambda(wx, wy, nb);
+    if (MAP == MAP_BBOX) return decode2_bbox(wx, wy, nb);
+    return decode2_linear((int64_t)wx, nb);
+}
+
+template <int MAP>
+SX_HD List3 decode3(uint32_t wx, uint32_t wy, uint32_t wz, int p, int nb) {
+    if (MAP == MAP_LAMBDA) return decode3_lambda(wx, wy, wz, p, nb);
+    if (MAP == MAP_BBOX) return decode3_bbox(wx, wy, wz, nb);
+    return decode3_linear((int64_t)wx, nb);
+}
+
+}  // namespace sx

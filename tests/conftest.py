@@ -18,3 +18,17 @@ def oracle():
     import oracle as _oracle
     _oracle.build()
     return _oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library on a GPU; tests marked gpu use it."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_07394_gb300 import build as _build
+    import paper_1610_07394_gb300 as _sx
+    _build.build()
+    _sx.lib()
+    return _sx
+

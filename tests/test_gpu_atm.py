@@ -1,0 +1,121 @@
+"""GPU parity of the Axilrod-Teller-Muto energy and forces over the 3-simplex
+{i < j < k} against the FP64 oracle.  Energy within 1e-6 relative; forces
+(-dE/dx, adjoint kernel) within 1e-4 relative per atom, against the oracle's
+analytic gradient and FP64 central differences; properties that hold at any
+size (map agreement, force balance, Euler's theorem) at the full sizes."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import rel_err, to_gpu
+
+pytestmark = pytest.mark.gpu
+E_TOL = 1e-6
+F_TOL = 1e-4
+
+
+def energy(gpu, x, mp="lambda", nu=1.0, eps=1e-4):
+    return gpu.atm_energy_raw(to_gpu(x), nu, eps, mp).item()
+
+
+def atom_err(F, G):
+    """Per-atom |F - (-G)| / |G| for forces F and gradient G."""
+    return np.linalg.norm(F + G, axis=1) / np.linalg.norm(G, axis=1)
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("n", [3, 4, 31, 32, 33, 65, 100, 250])
+def test_energy_small(gpu, oracle, mp, n):
+    x = synth.uniform_cube(n, 3, 4.0, seed=200 + n)
+    assert energy(gpu, x, mp) == pytest.approx(oracle.atm_energy(x), rel=E_TOL)
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("n", [3, 5, 33, 64, 97])
+def test_forces_small(gpu, oracle, mp, n):
+    x = synth.uniform_cube(n, 3, 3.0, seed=300 + n)
+    F, E = gpu.atm_forces(to_gpu(x), 1.0, 1e-4, mp)
+    G = oracle.atm_grad(x)
+    assert atom_err(F.cpu().numpy(), G).max() <= F_TOL
+    assert E.item() == pytest.approx(oracle.atm_energy(x), rel=E_TOL)
+
+
+def test_parameters_nu_eps(gpu, oracle):
+    x = synth.uniform_cube(70, 3, 2.0, seed=7)
+    for nu, eps in ((0.5, 0.0), (2.0, 1e-2)):
+        assert energy(gpu, x, "lambda", nu, eps) == pytest.approx(oracle.atm_energy(x, nu, eps), rel=E_TOL)
+
+
+def test_closed_form_triangles(gpu):
+    """Equilateral (11/(8 L^9) at eps = 0) and collinear (-1/(4 a^9))."""
+    L = 1.25
+    x = np.array([[0, 0, 0], [L, 0, 0], [L / 2, L * np.sqrt(3) / 2, 0]], np.float32)
+    xd = x.astype(np.float64)
+    Lr = np.linalg.norm(xd[0] - xd[1])
+    assert energy(gpu, x, "lambda", 1.0, 0.0) == pytest.approx(11 / (8 * Lr ** 9), rel=1e-5)
+    a = 0.75
+    y = np.array([[0, 0, 0], [0, a, 0], [0, 2 * a, 0]], np.float32)
+    assert energy(gpu, y, "lambda", 1.0, 0.0) == pytest.approx(-1 / (4 * a ** 9), rel=1e-5)
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+def test_energy_config_n1024(gpu, oracle, mp):
+    """3-simplex plain: n = 1024 uniform in a cube of side 10, seed 1,
+    178,433,024 triples, nu = 1, eps = 1e-4."""
+    x = synth.make_points("atm_n1024")
+    assert energy(gpu, x, mp) == pytest.approx(oracle.atm_energy(x), rel=E_TOL)
+
+
+def test_differentiation_config_n4096(gpu, oracle):
+    """n = 4096 in a cube of side 20, seed 3: autograd backward (adjoint
+    kernel) on 64 sampled atoms against the oracle's analytic gradient, and
+    on 4 of them against FP64 central differences (h = 1e-4) of the
+    oracle's partial energy."""
+    x = synth.make_points("atm_n4096")
+    xt = to_gpu(x).requires_grad_(True)
+    E = gpu.atm_energy(xt)
+    E.backward()
+    g = xt.grad.double().cpu().numpy()
+    atoms = synth.sample_indices(64, 4096, seed=3 + 10 ** 6)
+    G = oracle.atm_grad_atoms(x, atoms)
+    err = np.linalg.norm(g[atoms] - G, axis=1) / np.linalg.norm(G, axis=1)
+    assert err.max() <= F_TOL
+    h = 1e-4
+    xd = x.astype(np.float64)
+    for a in atoms[:4]:
+        fd = np.zeros(3)
+        for t in range(3):
+            xp, xm = xd.copy(), xd.copy()
+            xp[a, t] += h
+            xm[a, t] -= h
+            fd[t] = (oracle.atm_atom_energy(xp, a) - oracle.atm_atom_energy(xm, a)) / (2 * h)
+        assert np.linalg.norm(g[a] - fd) / np.linalg.norm(fd) <= F_TOL
+    # the three maps give the same energy (no oracle run of 1.1e10 triples)
+    e = [energy(gpu, x, mp) for mp in ("lambda", "bbox", "linear")]
+    assert e[1] == pytest.approx(e[0], rel=1e-9) and e[2] == pytest.approx(e[0], rel=1e-9)
+
+
+def test_properties_full_size(gpu):
+    """n = 4096: sum of forces ~ 0, total torque ~ 0, and at eps = 0 Euler's
+    theorem for the degree -9 homogeneous energy, sum_i x_i . F_i = 9 E."""
+    x = synth.make_points("atm_n4096")
+    F, E = gpu.atm_forces(to_gpu(x), 1.0, 0.0, "lambda")
+    F = F.cpu().numpy()
+    xd = x.astype(np.float64)
+    scale = np.abs(F).sum()
+    assert np.abs(F.sum(axis=0)).max() <= 1e-6 * scale
+    assert np.abs(np.cross(xd, F).sum(axis=0)).max() <= 1e-6 * scale * 20
+    assert (xd * F).sum() == pytest.approx(9 * E.item(), rel=1e-5)
+
+
+def test_scale_config_n16384(gpu, oracle):
+    """n = 16384 (7.33e11 triples), seed 6: forces on 8 sampled atoms against
+    the oracle, energy equal across lambda and bounding box."""
+    x = synth.make_points("atm_n16384")
+    F, E = gpu.atm_forces(to_gpu(x), 1.0, 1e-4, "lambda")
+    atoms = synth.sample_indices(8, 16384, seed=6 + 10 ** 6)
+    G = oracle.atm_grad_atoms(x, atoms)
+    assert atom_err(F.cpu().numpy()[atoms], G).max() <= F_TOL
+    e_bb = energy(gpu, x, "bbox")
+    assert e_bb == pytest.approx(E.item(), rel=1e-6)

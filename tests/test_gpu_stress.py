@@ -1,0 +1,85 @@
+"""GPU parity of the stress loss over the packed EDM and its gradient
+against the FP64 oracle: loss within 1e-5 relative, gradient within 1e-4
+relative per row (and against FP64 central differences)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import gather, packed_index, rel_err, to_gpu
+
+pytestmark = pytest.mark.gpu
+L_TOL = 1e-5
+G_TOL = 1e-4
+
+
+def row_err(g, G):
+    return np.linalg.norm(g - G, axis=1) / np.linalg.norm(G, axis=1)
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("n,d", [(2, 1), (33, 3), (100, 8), (257, 64), (700, 33)])
+def test_stress_small(gpu, oracle, mp, n, d):
+    x = synth.normal(n, d, seed=400 + n)
+    y = synth.perturbed(x, 0.1, seed=500 + n)
+    xt, yt = to_gpu(x), to_gpu(y)
+    loss, D = gpu.stress_fwd(xt, yt, mp, store_d=True)
+    assert loss.item() == pytest.approx(oracle.stress_loss(x, y), rel=L_TOL)
+    ref_D = oracle.edm_packed(x)
+    off = ref_D > 0
+    assert rel_err(D.cpu().numpy()[off], ref_D[off]).max() <= 1e-5
+    g = gpu.stress_bwd(xt, yt, 1.0, mp).double().cpu().numpy()
+    G = oracle.stress_grad_rows(x, y, range(n))
+    assert row_err(g, G).max() <= G_TOL
+
+
+def test_autograd_and_fd(gpu, oracle):
+    x = synth.normal(150, 6, seed=31)
+    y = synth.perturbed(x, 0.2, seed=32)
+    xt = to_gpu(x).requires_grad_(True)
+    L = gpu.stress_loss(xt, to_gpu(y))
+    (2.5 * L).backward()
+    g = xt.grad.double().cpu().numpy()
+    G = 2.5 * oracle.stress_grad_rows(x, y, range(150))
+    assert row_err(g, G).max() <= G_TOL
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    h = 1e-5
+    for a in (0, 77):
+        for t in range(6):
+            xp, xm = xd.copy(), xd.copy()
+            xp[a, t] += h
+            xm[a, t] -= h
+            fd = 2.5 * (oracle.stress_loss(xp, yd) - oracle.stress_loss(xm, yd)) / (2 * h)
+            assert g[a, t] == pytest.approx(fd, rel=G_TOL, abs=1e-6 * np.abs(G).max())
+
+
+def test_zero_at_reference(gpu):
+    x = to_gpu(synth.normal(300, 5, seed=33))
+    loss, _ = gpu.stress_fwd(x, x)
+    assert loss.item() == 0.0
+    assert bool((gpu.stress_bwd(x, x) == 0).all())
+
+
+def test_scale_config_sampled(gpu, oracle):
+    """n = 65536, d = 64, N(0,1) seed 4, y = x + 0.1 N(0,1) seed 5: gradient
+    rows of 16 sampled atoms and 100k sampled entries of the stored D against
+    the oracle; sum of the gradient ~ 0."""
+    w = synth.WORKLOADS["stress_n65536_d64"]
+    x = synth.normal(w["n"], w["d"], w["seed"])
+    y = synth.perturbed(x, w["sigma"], w["y_seed"])
+    xt, yt = to_gpu(x), to_gpu(y)
+    loss, D = gpu.stress_fwd(xt, yt, "lambda", store_d=True)
+    pr = synth.sample_pairs(100000, w["n"], seed=41)
+    got = gather(D, packed_index(pr[:, 0], pr[:, 1]))
+    ref = oracle.edm_pairs(x, pr)
+    m = pr[:, 0] != pr[:, 1]
+    assert rel_err(got[m], ref[m]).max() <= 1e-5
+    del D
+    torch.cuda.empty_cache()
+    g = gpu.stress_bwd(xt, yt)
+    rows = synth.sample_indices(16, w["n"], seed=42)
+    G = oracle.stress_grad_rows(x, y, rows)
+    assert row_err(g[torch.from_numpy(rows).cuda()].double().cpu().numpy(), G).max() <= G_TOL
+    gs = g.double().sum(0).abs().max().item()
+    assert gs <= 1e-4 * g.double().abs().sum(0).max().item()
+    assert loss.item() > 0

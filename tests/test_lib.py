@@ -1,0 +1,118 @@
+"""Host-side checks of libsimplex (no GPU needed).
+
+* the library builds and exports every entry point ``include/simplex.h``
+  declares;
+* the map decode, compiled for the host from the same header the kernels
+  use, equals the oracle's independent recursive construction bit for bit;
+* argument validation returns status codes before any GPU work.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1610_07394_gb300 as sx
+from paper_1610_07394_gb300 import build as sxbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    sxbuild.build()
+    return sx.lib()
+
+
+def header_symbols():
+    with open(os.path.join(ROOT, "include", "simplex.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(simplex_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = header_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+    assert sorted(sx.EXPORTS) == syms
+
+
+def test_abi_and_strerror(L):
+    assert sx.simplex_abi_version() == 1
+    for st in range(7):
+        assert L.simplex_strerror(st)
+    assert L.simplex_last_cuda_error() == 0
+
+
+def host_table(m, nb, mp):
+    g = sx.simplex_grid_blocks(m, nb, mp)
+    t = torch.empty((g, 2 * m), dtype=torch.int32)
+    sx.simplex_map_blocks_host(m, nb, mp, t)
+    return t.numpy()
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 7, 8, 16, 31, 64, 100, 256, 1024, 4096])
+def test_decode2_host_equals_oracle(oracle, mp, nb):
+    if mp != "lambda" and nb > 1024:
+        pytest.skip("box/linear tables of this size add nothing")
+    assert sx.simplex_grid_blocks(2, nb, mp) == np.prod(oracle.grid2(nb, mp))
+    assert np.array_equal(host_table(2, nb, mp), oracle.table2(nb, mp))
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 6, 8, 9, 16, 20, 32, 64, 128, 256])
+def test_decode3_host_equals_oracle(oracle, mp, nb):
+    if mp != "lambda" and nb > 128:
+        pytest.skip("box/linear tables of this size add nothing")
+    assert sx.simplex_grid_blocks(3, nb, mp) == np.prod(oracle.grid3(nb, mp))
+    assert np.array_equal(host_table(3, nb, mp), oracle.table3(nb, mp))
+
+
+def test_linear_decode_large_indices(oracle):
+    """The root-based inverse with its integer fix-up stays exact where FP32
+    roots alone are off (8l+1 and 6l beyond 2^24): whole tables of a large
+    triangle and tetrahedron against the oracle's enumeration."""
+    nb = 4100
+    assert np.array_equal(host_table(2, nb, "linear"), oracle.table2(nb, "linear"))
+    nb = 300
+    assert np.array_equal(host_table(3, nb, "linear"), oracle.table3(nb, "linear"))
+
+
+def test_grid_and_workspace_sizes(L):
+    assert sx.simplex_grid_blocks(2, 64, "lambda") == 32 * 64
+    assert sx.simplex_grid_blocks(3, 32, "lambda") == 16 * 16 * (16 + 8 + 2)
+    assert sx.simplex_grid_blocks(3, 32, "bbox") == 32 ** 3
+    assert sx.simplex_grid_blocks(3, 32, "linear") == 32 * 33 * 34 // 6
+    assert sx.simplex_grid_blocks(4, 32, "lambda") == -1
+    rho = sx.simplex_block_rho("atm_energy")
+    nb = -(-1024 // rho)
+    assert sx.simplex_workspace_bytes("atm_energy", 1024, 3, "lambda") == 8 * (
+        sx.simplex_grid_blocks(3, nb, "lambda") + 1024)
+    assert sx.simplex_workspace_bytes("map2", 10, 1) == 0
+    assert sx.simplex_workspace_bytes("atm_energy", 0, 3) == -1
+
+
+def test_validation_before_gpu_work(L):
+    """Bad arguments come back as status codes; nothing reaches the GPU."""
+    null = None
+    assert L.simplex_edm_packed(0, 3, 16, 16, 0, 0, null, 0, null) == 1          # n < 1
+    assert L.simplex_edm_packed(4, 3, null, 16, 0, 0, null, 0, null) == 1        # NULL x
+    assert L.simplex_edm_packed(4, 3, 16, 16, 7, 0, null, 0, null) == 1          # bad map
+    assert L.simplex_edm_packed(4, 3, 17, 16, 0, 0, null, 0, null) == 2          # misaligned x
+    assert L.simplex_atm_energy(8, 2, 16, 1.0, 1e-4, 16, 0, null, 0, null) == 4   # d != 3
+    assert L.simplex_atm_energy(8, 3, 16, 1.0, 1e-4, 16, 0, null, 0, null) == 6   # no workspace
+    assert L.simplex_atm_energy(8, 3, 16, 1.0, 1e-4, 16, 0, 256, 16, null) == 6  # too small
+    assert L.simplex_map2(10, 33, 0, 16, 16, null) == 1                          # rho > 32
+    assert L.simplex_map3(10, 11, 0, 16, 16, null) == 1                          # rho^3 > 1024
+    assert L.simplex_stress_bwd(8, 4, 16, 16, 1.0, 20, 0, 0, null, 0, null) == 2  # grad not 16B
+    assert L.simplex_map_blocks_host(2, 4, 0, null) == 1
+
+
+def test_binding_requires_cuda_tensors(L):
+    x = torch.zeros(8, 3)
+    with pytest.raises(TypeError):
+        sx.simplex_atm_energy(x, 1.0, 1e-4, torch.zeros((), dtype=torch.float64))
