@@ -5,24 +5,26 @@
 // linear enumeration with cube roots).
 //
 // Per triple (i, j, k) with edge vectors e_ij = x_j - x_i, e_ik = x_k - x_i,
-// e_jk = x_k - x_j and softened inverse lengths r = (|e|^2 + eps)^{-1/2}:
-//   e = nu R^3 (1 + 3 d_i d_j d_k R^2),  R = r_ij r_ik r_jk,
-// with the vertex dot products d_i = e_ij . e_ik, d_j = -e_ij . e_jk,
-// d_k = e_ik . e_jk (so cos g_i = d_i r_ij r_ik, and R^2 = 1/(s_a s_b s_c)).
-// The dot products are taken from the edge vectors, not from the law of
-// cosines on squared lengths: for a triangle with one short side the latter
-// cancels catastrophically in FP32, and such close triples dominate E.
+// e_jk = x_k - x_j, softened squares s = |e|^2 + eps, r = s^{-1/2} and unit
+// vectors u = e r:
+//   cos g_i = u_ij . u_ik,  cos g_j = -u_ij . u_jk,  cos g_k = u_ik . u_jk,
+//   e = nu r_ij^3 r_ik^3 r_jk^3 (1 + 3 cos g_i cos g_j cos g_k).
+// The cosines are dot products of edge vectors, never the law of cosines on
+// squared lengths: for a triangle with one short side the latter cancels
+// catastrophically in FP32, and such close triples dominate E.  r^3 is
+// formed once per pair as 1/(s sqrt(s)) (two correctly rounded operations),
+// so R^3 = r_ij^3 r_ik^3 r_jk^3 carries few roundings.
 //
 // Tile layout (256 threads): thread (ti, tj), ti, tj in [0, 16), owns the
 // four pairs (i, j) = (ti + 16p, tj + 16q), p, q in {0, 1}, and walks the 32
 // points k of the third tile.  Pair terms are computed once per tile and
-// kept in shared memory: for each (j, k) and (i, k) the edge vector and its
-// r.  The order constraint and the padding past n are folded into r:
-// r_ij = 0 unless i < j < n and r_jk = 0 unless j < k < n, which zeroes every
-// term outside the simplex without a branch.  Per-thread sums are FP32 within
-// a tile and FP64 across tiles; the block sum is FP64 and one FP64 partial
-// per block goes to the workspace, reduced deterministically by a second
-// pass.
+// kept in shared memory: for each (j, k) and (i, k) the unit vector and r^3
+// (energy) or r (forces).  The order constraint and the padding past n are
+// folded into the pair terms: a pair outside i < j < k < n gets u = 0 and
+// r = 0, which zeroes its triples without a branch.  Per-thread sums are
+// FP32 within a tile and FP64 across tiles; the block sum is FP64 and one
+// FP64 partial per block goes to the workspace, reduced deterministically by
+// a second pass.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -32,8 +34,8 @@ constexpr int R_ = kAtmRho;  // 32
 
 struct AtmTables {
     float4 xs[3][R_];        // tiles I, J, K: (x, y, z, 0)
-    float4 tb[R_][2][16];    // [k][q][t]: (e_jk, r_jk) of pair (j = t + 16q, k)
-    float4 tc[R_][2][16];    // [k][p][t]: (e_ik, r_ik) of pair (i = t + 16p, k)
+    float4 tb[R_][2][16];    // [k][q][t]: (u_jk, r_jk^3 or r_jk) of pair (j = t + 16q, k)
+    float4 tc[R_][2][16];    // [k][p][t]: (u_ik, r_ik^3 or r_ik) of pair (i = t + 16p, k)
 };
 
 // Loads the three point tiles (zero past n).
@@ -50,41 +52,44 @@ __device__ __forceinline__ void load_tiles(const float *__restrict__ x, int64_t 
     }
 }
 
-// Pair tables of the (j, k) and (i, k) sides.
+// Pair terms.  CUBE selects r^3 (energy) or r (forces) in the w slot.
 __device__ __forceinline__ float4 edge(float4 from, float4 to) {
     return make_float4(to.x - from.x, to.y - from.y, to.z - from.z, 0.0f);
 }
 
-__device__ __forceinline__ float rinv(float4 e, float eps) {
-    return 1.0f / sqrtf(fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps))));
+template <bool CUBE>
+__device__ __forceinline__ float4 pair_term(float4 from, float4 to, bool valid, float eps) {
+    const float4 e = edge(from, to);
+    if (!valid) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const float s = fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps)));
+    const float q = sqrtf(s);
+    const float r = 1.0f / q;
+    return make_float4(e.x * r, e.y * r, e.z * r, CUBE ? 1.0f / (s * q) : r);
 }
 
+template <bool CUBE>
 __device__ __forceinline__ void build_tables(int64_t n, int I, int J, int K, float eps,
                                              AtmTables &T) {
     for (int e = threadIdx.x; e < R_ * R_; e += 256) {
         const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
-        const int64_t gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
-        float4 b = edge(T.xs[1][o], T.xs[2][k]);
-        b.w = (gj < gk && gk < n) ? rinv(b, eps) : 0.0f;
-        T.tb[k][half][t] = b;
-        float4 c = edge(T.xs[0][o], T.xs[2][k]);
-        c.w = rinv(c, eps);
-        T.tc[k][half][t] = c;
+        const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
+        T.tb[k][half][t] = pair_term<CUBE>(T.xs[1][o], T.xs[2][k], gj < gk && gk < n, eps);
+        T.tc[k][half][t] = pair_term<CUBE>(T.xs[0][o], T.xs[2][k], gi < gk && gk < n, eps);
     }
 }
 
 struct PairConst {
-    float4 e;    // e_ij = x_j - x_i, w = r_ij (0 outside i < j < n)
-    float3 f;    // -3 e_ij
+    float4 u;    // u_ij, w = r_ij^3 (energy) or r_ij (forces); 0 outside i < j < n
+    float3 f;    // -3 u_ij
 };
 
+template <bool CUBE>
 __device__ __forceinline__ PairConst pair_const(int64_t n, int I, int J, int i, int j, float eps,
                                                 const AtmTables &T) {
     PairConst c;
-    c.e = edge(T.xs[0][i], T.xs[1][j]);
     const int64_t gi = (int64_t)I * R_ + i, gj = (int64_t)J * R_ + j;
-    c.e.w = (gi < gj && gj < n) ? rinv(c.e, eps) : 0.0f;
-    c.f = make_float3(-3.0f * c.e.x, -3.0f * c.e.y, -3.0f * c.e.z);
+    c.u = pair_term<CUBE>(T.xs[0][i], T.xs[1][j], gi < gj && gj < n, eps);
+    c.f = make_float3(-3.0f * c.u.x, -3.0f * c.u.y, -3.0f * c.u.z);
     return c;
 }
 
@@ -96,17 +101,15 @@ __device__ __forceinline__ float dot3(float3 a, float4 b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
 }
 
-// One triple's energy without nu: R^3 (1 + 3 d_i d_j d_k R^2) added to acc;
-// B = (e_jk, r_jk), C = (e_ik, r_ik).
+// One triple's energy without nu: R^3 (1 + 3 cos g_i cos g_j cos g_k) added
+// to acc; B = (u_jk, r_jk^3), C = (u_ik, r_ik^3).  15 FP32 operations.
 __device__ __forceinline__ void triple_energy(float4 B, float4 C, const PairConst &c, float &acc) {
-    const float di = dot3(c.e, C);                 // d_i
-    const float dj3 = dot3(c.f, B);                // 3 d_j
-    const float dk = dot3(C, B);                   // d_k
-    const float D3 = (di * dj3) * dk;              // 3 d_i d_j d_k
-    const float R = (c.e.w * C.w) * B.w;
-    const float R2 = R * R;
-    const float R3 = R2 * R;
-    acc = fmaf(R3, fmaf(D3, R2, 1.0f), acc);
+    const float ci = dot3(c.u, C);                 // cos g_i
+    const float cj3 = dot3(c.f, B);                // 3 cos g_j
+    const float ck = dot3(C, B);                   // cos g_k
+    const float C3 = (ci * cj3) * ck;
+    const float R3 = (c.u.w * C.w) * B.w;
+    acc = fmaf(R3, 1.0f + C3, acc);
 }
 
 template <int MAP>
@@ -123,12 +126,12 @@ __global__ void __launch_bounds__(256) k_atm_energy(int64_t n, const float *__re
         if (t) __syncthreads();
         load_tiles(x, n, I, J, K, T);
         __syncthreads();
-        build_tables(n, I, J, K, eps, T);
+        build_tables<true>(n, I, J, K, eps, T);
         PairConst pc[2][2];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const<true>(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
         __syncthreads();
         float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 4
@@ -160,29 +163,35 @@ struct AtmForceSmem {
 
 // One triple: energy into acc and the derivatives of e (without nu) with
 // respect to the squared sides a = |e_ij|^2, b = |e_jk|^2, c = |e_ik|^2.
-// With D = d_i d_j d_k, Q = R^2 = 1/P, G = 1.5 (1 + 5 D Q):
-//   de/da = R^3 (3 Q dD/da - G / s_a), and likewise for b and c, where
-//   dD/da = (d_j d_k + d_i d_k - d_i d_j)/2, dD/db = (d_i d_k + d_i d_j - d_j d_k)/2,
-//   dD/dc = (d_j d_k + d_i d_j - d_i d_k)/2  (from 2 d_i = a + c - b, etc.),
-// and 1/s = r^2.
+// From e = R^3 (1 + 3 D R^2) with D = d_i d_j d_k (vertex dot products,
+// 2 d_i = a + c - b, 2 d_j = a + b - c, 2 d_k = b + c - a) and R^2 = 1/P:
+//   de/da = R^3 (3 R^2 dD/da - 1.5 (1 + 5 D R^2) r_a^2),
+//   dD/da = (d_j d_k + d_i d_k - d_i d_j)/2, and likewise for b, c.
+// In cosines (Cp = cos_i cos_j cos_k = D R^2, d_j d_k R^2 = cos_j cos_k r_a r_c,
+// d_i d_k R^2 = cos_i cos_k r_a r_b, d_i d_j R^2 = cos_i cos_j r_b r_c):
+//   de/da = 1.5 R^3 (X + Y - Z - H r_a^2),  de/db = 1.5 R^3 (Y + Z - X - H r_b^2),
+//   de/dc = 1.5 R^3 (X + Z - Y - H r_c^2),
+// with X = cos_j cos_k r_a r_c, Y = cos_i cos_k r_a r_b, Z = cos_i cos_j r_b r_c,
+// H = 1 + 5 Cp.  B = (u_jk, r_jk), C = (u_ik, r_ik).
 __device__ __forceinline__ void triple_grad(float4 B, float4 C, const PairConst &c, float &acc,
                                             float &ea, float &eb, float &ec) {
-    const float di = dot3(c.e, C);
-    const float dj = -dot3(c.e, B);
-    const float dk = dot3(C, B);
-    const float pij = di * dj, pjk = dj * dk, pik = di * dk;
-    const float D = pij * dk;
-    const float R = (c.e.w * C.w) * B.w;
-    const float Q = R * R;
-    const float R3 = Q * R;
-    const float DQ = D * Q;
-    acc = fmaf(R3, fmaf(3.0f, DQ, 1.0f), acc);
-    const float G = fmaf(7.5f, DQ, 1.5f);
-    const float hS = 0.5f * (pij + pjk + pik);
-    const float Q3 = 3.0f * Q;
-    ea = R3 * fmaf(Q3, hS - pij, -G * (c.e.w * c.e.w));
-    eb = R3 * fmaf(Q3, hS - pjk, -G * (B.w * B.w));
-    ec = R3 * fmaf(Q3, hS - pik, -G * (C.w * C.w));
+    const float ra = c.u.w, rb = B.w, rc = C.w;
+    const float ci = dot3(c.u, C);
+    const float cj = -dot3(c.u, B);
+    const float ck = dot3(C, B);
+    const float cjk = cj * ck, cik = ci * ck, cij = ci * cj;
+    const float Cp = ci * cjk;
+    const float rab = ra * rb;
+    const float X = cjk * (ra * rc), Y = cik * rab, Z = cij * (rb * rc);
+    const float R = rab * rc;
+    const float R3 = (R * R) * R;
+    acc = fmaf(R3, fmaf(3.0f, Cp, 1.0f), acc);
+    const float H = fmaf(5.0f, Cp, 1.0f);
+    const float h = 1.5f * R3;
+    const float S = X + Y + Z;
+    ea = h * fmaf(-H, ra * ra, fmaf(-2.0f, Z, S));
+    eb = h * fmaf(-H, rb * rb, fmaf(-2.0f, X, S));
+    ec = h * fmaf(-H, rc * rc, fmaf(-2.0f, Y, S));
 }
 
 template <int MAP>
@@ -202,12 +211,12 @@ __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__re
         load_tiles(x, n, I, J, K, T);
         for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
         __syncthreads();
-        build_tables(n, I, J, K, eps, T);
+        build_tables<false>(n, I, J, K, eps, T);
         PairConst pc[2][2];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const<false>(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
         __syncthreads();
         float acc = 0.0f;
         float wa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};

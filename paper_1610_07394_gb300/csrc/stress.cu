@@ -5,9 +5,11 @@
 //   L = sum_{i<j} (D_ij - delta_ij)^2,  D_ij = |x_i - x_j|^2,
 //   delta_ij = |y_i - y_j|^2,
 //   dL/dx_i = 4 sum_{j != i} (D_ij - delta_ij)(x_i - x_j).
-// Both passes recompute D and delta from the points (never stored); the
-// forward pass can also write the packed D.  Pair arithmetic is FP32; the
-// loss is reduced in FP64; the gradient accumulates in FP32 global atomics.
+// Both passes recompute the residual r_ij = D_ij - delta_ij from the points
+// (never stored), as a sum of per-coordinate differences of squares (see
+// tile_resid); the forward pass can also write the packed D.  Pair
+// arithmetic is FP32; the loss is reduced in FP64; the gradient accumulates
+// in FP32 global atomics.
 #include "common.cuh"
 #include "kernels.h"
 #include "tile.cuh"
@@ -20,25 +22,23 @@ __global__ void __launch_bounds__(256) k_stress_fwd(int64_t n, int d, const floa
                                                     float *__restrict__ d_out, int nb,
                                                     double *__restrict__ partials) {
     __shared__ TileSmem sm;
+    __shared__ ResidSmem rs;
     __shared__ double red[8];
     const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double total = 0.0;
     for (int t = 0; t < L.cnt; ++t) {
         const int64_t row0 = (int64_t)L.y[t] * kStressRho, col0 = (int64_t)L.x[t] * kStressRho;
-        float D[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-        tile_sqdist(x, n, d, row0, col0, sm, D);
-        tile_sqdist(y, n, d, row0, col0, sm, E);
+        float D[4] = {0.f, 0.f, 0.f, 0.f}, r[4] = {0.f, 0.f, 0.f, 0.f};
+        if (d_out) tile_sqdist(x, n, d, row0, col0, sm, D);
+        tile_resid(x, y, n, d, row0, col0, rs, r);
         const int64_t j = col0 + lane;
         float loc = 0.f;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int64_t i = row0 + w + 8 * m;
-            if (j <= i && i < n) {
-                if (d_out) d_out[i * (i + 1) / 2 + j] = D[m];
-                const float r = D[m] - E[m];
-                loc = fmaf(r, r, loc);
-            }
+            if (j < i && i < n) loc = fmaf(r[m], r[m], loc);
+            if (d_out && j <= i && i < n) d_out[i * (i + 1) / 2 + j] = D[m];
         }
         total += (double)loc;
     }
@@ -51,20 +51,20 @@ __global__ void __launch_bounds__(256) k_stress_bwd(int64_t n, int d, const floa
                                                     const float *__restrict__ y, float scale4,
                                                     int nb, float *__restrict__ grad) {
     __shared__ TileSmem sm;
+    __shared__ ResidSmem rs;
     __shared__ float C[32][33];
     __shared__ float rsum[32], csum[32];
     const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = 0; t < L.cnt; ++t) {
         const int64_t row0 = (int64_t)L.y[t] * kStressRho, col0 = (int64_t)L.x[t] * kStressRho;
-        float D[4] = {0.f, 0.f, 0.f, 0.f}, E[4] = {0.f, 0.f, 0.f, 0.f};
-        tile_sqdist(x, n, d, row0, col0, sm, D);
-        tile_sqdist(y, n, d, row0, col0, sm, E);
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+        tile_resid(x, y, n, d, row0, col0, rs, r);
         const int64_t j = col0 + lane;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int64_t i = row0 + w + 8 * m;
-            C[w + 8 * m][lane] = (j < i && i < n) ? D[m] - E[m] : 0.0f;
+            C[w + 8 * m][lane] = (j < i && i < n) ? r[m] : 0.0f;
         }
         __syncthreads();
         if (threadIdx.x < 32) {

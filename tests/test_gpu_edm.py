@@ -23,7 +23,9 @@ def test_edm_small(gpu, oracle, mp, n, d):
     i = np.arange(n)
     assert (out[packed_index(i, i)] == 0).all()
     off = ref > 0
-    assert rel_err(out[off], ref[off]).max() <= TOL
+    if off.any():
+        assert rel_err(out[off], ref[off]).max() <= TOL
+    assert out.shape == ref.shape
 
 
 @pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
