@@ -41,11 +41,11 @@ import synth  # noqa: E402
 METRIC = "pairs/s and triplets/s, λ-map vs bounding-box on 1 GB300; % of HBM/FP32 roofline"
 WORKLOAD = "atm_n1024"
 NU, EPS = 1.0, 1e-4
-# FP32 operations per triple in the energy kernel's inner loop, pair terms
-# hoisted: three 3-vector dot products (3 FMUL + 6 FFMA), the cosine product
-# (2 FMUL), R = r_ij r_ik r_jk (2 FMUL), R^2 and R^3 (2 FMUL), and two FFMA
-# for the bracket and the sum: 9 FMUL + 8 FFMA = 25 flops (FMA = 2).
-FLOPS_PER_TRIPLE = 25
+# Algorithmic FP32 flops per triple with the pair terms (unit edge vectors
+# and r^3) hoisted: three 3-vector dot products (3 x 5), the cosine product
+# (2), R^3 = r_ij^3 r_ik^3 r_jk^3 (2), the bracket 1 + 3 cos cos cos (2, one
+# FMA) and the running sum (1): 22 flops.
+FLOPS_PER_TRIPLE = 22
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 

@@ -25,6 +25,8 @@
 // FP32 within a tile and FP64 across tiles; the block sum is FP64 and one
 // FP64 partial per block goes to the workspace, reduced deterministically by
 // a second pass.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -112,17 +114,26 @@ __device__ __forceinline__ void triple_energy(float4 B, float4 C, const PairCons
     acc = fmaf(R3, 1.0f + C3, acc);
 }
 
+// The (up to two) data blocks of a grid block, read without dynamic indexing.
+__device__ __forceinline__ void block_of(const List3 &L, int t, int &I, int &J, int &K) {
+    I = t ? L.i[1] : L.i[0];
+    J = t ? L.j[1] : L.j[0];
+    K = t ? L.k[1] : L.k[0];
+}
+
 template <int MAP>
-__global__ void __launch_bounds__(256) k_atm_energy(int64_t n, const float *__restrict__ x,
-                                                    float nu, float eps, int nb, int p,
-                                                    double *__restrict__ partials) {
+__global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *__restrict__ x,
+                                                       float nu, float eps, int nb, int p,
+                                                       double *__restrict__ partials) {
     __shared__ AtmTables T;
-    __shared__ double red[8];
+    __shared__ float red[16];
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
     const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
-    double total = 0.0;
+    float hi = 0.f, lo = 0.f;
+#pragma unroll 1
     for (int t = 0; t < L.cnt; ++t) {
-        const int I = L.i[t], J = L.j[t], K = L.k[t];
+        int I, J, K;
+        block_of(L, t, I, J, K);
         if (t) __syncthreads();
         load_tiles(x, n, I, J, K, T);
         __syncthreads();
@@ -143,9 +154,12 @@ __global__ void __launch_bounds__(256) k_atm_energy(int64_t n, const float *__re
             triple_energy(B0, C1, pc[1][0], acc[1][0]);
             triple_energy(B1, C1, pc[1][1], acc[1][1]);
         }
-        total += ((double)acc[0][0] + (double)acc[0][1]) + ((double)acc[1][0] + (double)acc[1][1]);
+        add_ff(hi, lo, acc[0][0], 0.f);
+        add_ff(hi, lo, acc[0][1], 0.f);
+        add_ff(hi, lo, acc[1][0], 0.f);
+        add_ff(hi, lo, acc[1][1], 0.f);
     }
-    const double s = block_sum_f64<256>(total, red);
+    const double s = block_sum_ff<256>(hi, lo, red);
     if (threadIdx.x == 0) {
         const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
         partials[bid] = (double)nu * s;
@@ -156,6 +170,8 @@ __global__ void __launch_bounds__(256) k_atm_energy(int64_t n, const float *__re
 
 struct AtmForceSmem {
     AtmTables T;
+    float tb3[R_][2][16];    // r_jk^3 of the pairs of T.tb
+    float tc3[R_][2][16];    // r_ik^3 of the pairs of T.tc
     float wjk[R_][R_ + 1];   // [k][j]: sum over i of de/db
     float wik[R_][R_ + 1];   // [k][i]: sum over j of de/dc
     float wij[R_][R_ + 1];   // [i][j]: sum over k of de/da
@@ -172,9 +188,11 @@ struct AtmForceSmem {
 //   de/da = 1.5 R^3 (X + Y - Z - H r_a^2),  de/db = 1.5 R^3 (Y + Z - X - H r_b^2),
 //   de/dc = 1.5 R^3 (X + Z - Y - H r_c^2),
 // with X = cos_j cos_k r_a r_c, Y = cos_i cos_k r_a r_b, Z = cos_i cos_j r_b r_c,
-// H = 1 + 5 Cp.  B = (u_jk, r_jk), C = (u_ik, r_ik).
-__device__ __forceinline__ void triple_grad(float4 B, float4 C, const PairConst &c, float &acc,
-                                            float &ea, float &eb, float &ec) {
+// H = 1 + 5 Cp.  B = (u_jk, r_jk), C = (u_ik, r_ik); R^3 is the product of the
+// three pairs' r^3 = 1/(s sqrt(s)), as in the energy kernel.
+__device__ __forceinline__ void triple_grad(float4 B, float4 C, float rb3, float rc3,
+                                            const PairConst &c, float ra3, float &acc, float &ea,
+                                            float &eb, float &ec) {
     const float ra = c.u.w, rb = B.w, rc = C.w;
     const float ci = dot3(c.u, C);
     const float cj = -dot3(c.u, B);
@@ -183,8 +201,7 @@ __device__ __forceinline__ void triple_grad(float4 B, float4 C, const PairConst 
     const float Cp = ci * cjk;
     const float rab = ra * rb;
     const float X = cjk * (ra * rc), Y = cik * rab, Z = cij * (rb * rc);
-    const float R = rab * rc;
-    const float R3 = (R * R) * R;
+    const float R3 = (ra3 * rc3) * rb3;
     acc = fmaf(R3, fmaf(3.0f, Cp, 1.0f), acc);
     const float H = fmaf(5.0f, Cp, 1.0f);
     const float h = 1.5f * R3;
@@ -194,40 +211,64 @@ __device__ __forceinline__ void triple_grad(float4 B, float4 C, const PairConst 
     ec = h * fmaf(-H, rc * rc, fmaf(-2.0f, Y, S));
 }
 
+// r^3 of every table pair, 1/(s sqrt(s)) from the stored unit vector's s.
+__device__ __forceinline__ float cube_r(float4 from, float4 to, bool valid, float eps) {
+    if (!valid) return 0.0f;
+    const float4 e = edge(from, to);
+    const float s = fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps)));
+    return 1.0f / (s * sqrtf(s));
+}
+
 template <int MAP>
 __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__restrict__ x,
                                                     float nu, float eps, int nb, int p,
                                                     double *__restrict__ partials,
                                                     double *__restrict__ forces) {
-    __shared__ AtmForceSmem S;
-    __shared__ double red[8];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AtmForceSmem &S = *reinterpret_cast<AtmForceSmem *>(smem_raw);
+    __shared__ float red[16];
     AtmTables &T = S.T;
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
     const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4, lane = tid & 31;
-    double total = 0.0;
+    float hi = 0.f, lo = 0.f;
+#pragma unroll 1
     for (int t = 0; t < L.cnt; ++t) {
-        const int I = L.i[t], J = L.j[t], K = L.k[t];
+        int I, J, K;
+        block_of(L, t, I, J, K);
         if (t) __syncthreads();
         load_tiles(x, n, I, J, K, T);
         for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
         __syncthreads();
         build_tables<false>(n, I, J, K, eps, T);
+        for (int e = tid; e < R_ * R_; e += 256) {
+            const int k = e >> 5, o = e & 31, half = o >> 4, tt = o & 15;
+            const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
+            S.tb3[k][half][tt] = cube_r(T.xs[1][o], T.xs[2][k], gj < gk && gk < n, eps);
+            S.tc3[k][half][tt] = cube_r(T.xs[0][o], T.xs[2][k], gi < gk && gk < n, eps);
+        }
         PairConst pc[2][2];
+        float ra3[2][2];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const<false>(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+            for (int b = 0; b < 2; ++b) {
+                pc[a][b] = pair_const<false>(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+                const int64_t gi = (int64_t)I * R_ + ti + 16 * a, gj = (int64_t)J * R_ + tj + 16 * b;
+                ra3[a][b] = cube_r(T.xs[0][ti + 16 * a], T.xs[1][tj + 16 * b], gi < gj && gj < n, eps);
+            }
         __syncthreads();
         float acc = 0.0f;
         float wa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
         for (int k = 0; k < R_; ++k) {
             const float4 B0 = T.tb[k][0][tj], B1 = T.tb[k][1][tj];
             const float4 C0 = T.tc[k][0][ti], C1 = T.tc[k][1][ti];
+            const float b30 = S.tb3[k][0][tj], b31 = S.tb3[k][1][tj];
+            const float c30 = S.tc3[k][0][ti], c31 = S.tc3[k][1][ti];
             float ea, eb[2][2], ec[2][2];
-            triple_grad(B0, C0, pc[0][0], acc, ea, eb[0][0], ec[0][0]); wa[0][0] += ea;
-            triple_grad(B1, C0, pc[0][1], acc, ea, eb[0][1], ec[0][1]); wa[0][1] += ea;
-            triple_grad(B0, C1, pc[1][0], acc, ea, eb[1][0], ec[1][0]); wa[1][0] += ea;
-            triple_grad(B1, C1, pc[1][1], acc, ea, eb[1][1], ec[1][1]); wa[1][1] += ea;
+            triple_grad(B0, C0, b30, c30, pc[0][0], ra3[0][0], acc, ea, eb[0][0], ec[0][0]); wa[0][0] += ea;
+            triple_grad(B1, C0, b31, c30, pc[0][1], ra3[0][1], acc, ea, eb[0][1], ec[0][1]); wa[0][1] += ea;
+            triple_grad(B0, C1, b30, c31, pc[1][0], ra3[1][0], acc, ea, eb[1][0], ec[1][0]); wa[1][0] += ea;
+            triple_grad(B1, C1, b31, c31, pc[1][1], ra3[1][1], acc, ea, eb[1][1], ec[1][1]); wa[1][1] += ea;
             // side (j, k): sum over the 16 i of this half-warp (lanes with the same tj)
             float sb0 = eb[0][0] + eb[1][0], sb1 = eb[0][1] + eb[1][1];
 #pragma unroll
@@ -246,7 +287,7 @@ __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__re
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) S.wij[ti + 16 * a][tj + 16 * b] = wa[a][b];
-        total += (double)acc;
+        add_ff(hi, lo, acc, 0.f);
         __syncthreads();
         // Pair coefficients -> gradient: grad_p += 2 sum_q w_pq (x_p - x_q).
         if (tid < 6 * R_) {
@@ -285,12 +326,32 @@ __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__re
         }
     }
     if (partials) {
-        const double s = block_sum_f64<256>(total, red);
+        const double s = block_sum_ff<256>(hi, lo, red);
         if (tid == 0) {
             const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
             partials[bid] = (double)nu * s;
         }
     }
+}
+
+// The force kernel's shared memory exceeds the 48 KB default of a launch;
+// opt in once per device for each instantiation.
+static int forces_smem_optin(int bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    static std::mutex mu;
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        if ((e = cudaFuncSetAttribute(k_atm_forces<MAP_LAMBDA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_BBOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+            return cuda_status(e);
+        done[dev] = true;
+    }
+    return SIMPLEX_OK;
 }
 
 static int atm_check(int64_t n, int64_t d, const float *x, int map, void *ws, int64_t ws_bytes,
@@ -346,10 +407,12 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
     double *partials = energy ? (double *)workspace : nullptr;
     const int64_t blocks = g.gx * g.gy * g.gz;
     if ((st = cuda_status(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s)))) return st;
+    const int smem = (int)sizeof(AtmForceSmem);
+    if ((st = forces_smem_optin(smem))) return st;
     prof_begin(s);
-    if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
-    else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
-    else k_atm_forces<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    else k_atm_forces<MAP_LINEAR><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;

@@ -67,6 +67,43 @@ __device__ __forceinline__ double block_sum_f64(double v, double *red) {
     return s;
 }
 
+// Compensated FP32 sums: (hi, lo) carries a value and the rounding error of
+// its additions (Knuth's TwoSum), so block sums keep ~2x FP32 precision
+// without FP64 arithmetic, which is slow on this part.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (h2, l2), renormalised.
+__device__ __forceinline__ void add_ff(float &hi, float &lo, float h2, float l2) {
+    float s, e;
+    two_sum(hi, h2, s, e);
+    e += lo + l2;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// Block sum of (hi, lo) pairs over NT threads; the FP64 result is valid in
+// thread 0.  `red` holds 2 * NT/32 floats of shared memory.
+template <int NT>
+__device__ __forceinline__ double block_sum_ff(float hi, float lo, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        add_ff(hi, lo, h2, l2);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[2 * w] = hi; red[2 * w + 1] = lo; }
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int t = 0; t < NT / 32; ++t) s += (double)red[2 * t] + (double)red[2 * t + 1];
+    return s;
+}
+
 // Deterministic FP64 sum of `count` per-block partials into *out (written,
 // not accumulated): pass 1 reduces fixed chunks into tmp[], pass 2 sums tmp.
 // tmp needs kReduceSlots doubles.
