@@ -51,7 +51,9 @@ typedef enum {
     SIMPLEX_EOVERFLOW = 3,    /* size exceeds 64-bit indices or grid limits  */
     SIMPLEX_EUNSUPPORTED = 4, /* valid request this build does not serve     */
     SIMPLEX_ECUDA = 5,        /* a CUDA call failed                          */
-    SIMPLEX_EWORKSPACE = 6    /* workspace missing, too small or misaligned  */
+    SIMPLEX_EWORKSPACE = 6,   /* workspace missing, too small or misaligned  */
+    SIMPLEX_ESCRATCH = 7      /* problem too large for the library's static
+                                 scratch (simplex_atm_energy_noalloc)        */
 } simplex_status;
 
 typedef enum {
@@ -194,6 +196,30 @@ int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
 
 /* Bytes of workspace an operation needs (0 if none, -1 on bad arguments). */
 int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map, int prec);
+
+/*
+ * simplex_atm_energy without any device allocation, for callers that cannot
+ * allocate: a plug-in handed only a stream and its tensors by a host
+ * framework whose caching allocator owns the device memory (a side
+ * cudaMalloc can fail or fragment that pool), or a latency-critical loop
+ * that must not call cudaMalloc/cudaFree because they can synchronise the
+ * device.  The paper has no counterpart; this is a packaging of the same
+ * kernels (identical results to simplex_atm_energy).
+ *
+ * Scratch is a fixed 4 MiB array inside the library (one FP64 per grid block
+ * plus 1024 reduction slots), held by every GPU that loads the library until
+ * the process exits.  Problems whose grid needs more return SIMPLEX_ESCRATCH
+ * before any work: with the lambda map that is n > 4096 points (BBOX:
+ * n > 2048; LINEAR: n > 4096).  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  The array needs no
+ * clearing: every slot a call reads is written earlier in that call.  All
+ * calls share the one array, so calls that can overlap on the GPU (different
+ * streams, or different host threads) race and corrupt each other's result:
+ * order them on one stream.  Arguments as simplex_atm_energy.
+ */
+int simplex_atm_energy_noalloc(int64_t n, int64_t d, const float *x, float nu, float eps,
+                               double *energy, int map, void *stream);
 
 /*
  * Tracing.  simplex_profile(1) clears the counters and starts recording;

@@ -36,7 +36,7 @@ EXPORTS = [
     "simplex_grid_blocks", "simplex_map_blocks", "simplex_map_blocks_host", "simplex_map2",
     "simplex_map3", "simplex_edm_packed", "simplex_atm_energy", "simplex_atm_forces",
     "simplex_stress_fwd", "simplex_stress_bwd", "simplex_workspace_bytes", "simplex_profile",
-    "simplex_profile_read",
+    "simplex_profile_read", "simplex_atm_energy_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ def _signatures(L):
         "simplex_stress_bwd": (_i32, [_i64, _i64, _vp, _vp, _f64, _vp, _i32, _i32, _vp, _i64, _vp]),
         "simplex_workspace_bytes": (_i64, [_i32, _i64, _i64, _i32, _i32]),
         "simplex_profile": (_i32, [_i32]),
+        "simplex_atm_energy_noalloc": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _i32, _vp]),
         "simplex_profile_read": (_i32, [ctypes.POINTER(_f64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     }
     for name, (res, args) in sig.items():
@@ -181,6 +182,14 @@ def simplex_atm_energy(x, nu, eps, energy, map="lambda", workspace=None, stream=
     _check("simplex_atm_energy", lib().simplex_atm_energy(
         n, d, _cuda(x, torch.float32, "x"), nu, eps, _cuda(energy, torch.float64, "energy"),
         _map(map), ws, 0 if workspace is None else workspace.numel(), _stream(stream)))
+
+
+def simplex_atm_energy_noalloc(x, nu, eps, energy, map="lambda", stream=None):
+    """simplex_atm_energy with the library's static scratch (no allocation)."""
+    n, d = x.shape
+    _check("simplex_atm_energy_noalloc", lib().simplex_atm_energy_noalloc(
+        n, d, _cuda(x, torch.float32, "x"), nu, eps, _cuda(energy, torch.float64, "energy"),
+        _map(map), _stream(stream)))
 
 
 def simplex_atm_forces(x, nu, eps, energy, forces, map="lambda", workspace=None, stream=None):

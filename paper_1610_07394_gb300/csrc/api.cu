@@ -130,6 +130,7 @@ extern "C" const char *simplex_strerror(int status) {
         case SIMPLEX_EUNSUPPORTED: return "request not supported by this build";
         case SIMPLEX_ECUDA: return "CUDA call failed (see simplex_last_cuda_error)";
         case SIMPLEX_EWORKSPACE: return "workspace missing, too small or misaligned";
+        case SIMPLEX_ESCRATCH: return "problem too large for the library's static scratch";
         default: return "unknown status";
     }
 }

@@ -419,3 +419,65 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
     if (energy) return reduce_partials(partials, blocks, partials + blocks, energy, s);
     return SIMPLEX_OK;
 }
+
+// ---------------------------------------------------------------- no-alloc entry
+
+namespace sx {
+
+// Scratch of simplex_atm_energy_noalloc: one FP64 partial per grid block plus
+// the reduction's slots, in a fixed array of this library's device image.
+// Every GPU that loads the library holds these 4 MiB until the process exits.
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 19;
+static __device__ __align__(256) double g_atm_noalloc_scratch[kNoAllocScratchDoubles];
+
+// Device address of that array on the current device.  In host code the
+// array's name is a host-side stand-in, not a device address, so the address
+// is looked up with cudaGetSymbolAddress once per device (with that device
+// current, on the first call made there) and cached.
+static int noalloc_scratch(double **out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static double *addr[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (dev < 0 || dev >= kMaxDevices) return SIMPLEX_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_atm_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        addr[dev] = static_cast<double *>(p);
+    }
+    *out = addr[dev];
+    return SIMPLEX_OK;
+}
+
+}  // namespace sx
+
+extern "C" int simplex_atm_energy_noalloc(int64_t n, int64_t d, const float *x, float nu,
+                                          float eps, double *energy, int map, void *stream) {
+    if (!energy) return SIMPLEX_EINVAL;
+    if (n < 1 || d != 3 || !x || map < MAP_LAMBDA || map > MAP_LINEAR)
+        return d != 3 && d > 0 ? SIMPLEX_EUNSUPPORTED : SIMPLEX_EINVAL;
+    if (!aligned(x, 4) || !aligned(energy, 8)) return SIMPLEX_EALIGN;
+    if (n > (1 << 22)) return SIMPLEX_EOVERFLOW;
+    const int64_t nb = (n + R_ - 1) / R_;
+    const Grid g = grid3(nb, map);
+    if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
+    const int64_t blocks = g.gx * g.gy * g.gz;
+    if (blocks + kReduceSlots > kNoAllocScratchDoubles) return SIMPLEX_ESCRATCH;
+    double *scratch = nullptr;
+    int st = noalloc_scratch(&scratch);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *partials = scratch, *tmp = scratch + blocks;
+    prof_begin(s);
+    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    prof_end(s);
+    note_launches(1);
+    if ((st = launch_status())) return st;
+    return reduce_partials(partials, blocks, tmp, energy, s);
+}
