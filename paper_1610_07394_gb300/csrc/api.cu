@@ -73,8 +73,23 @@ __global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__
     if (threadIdx.x == 0) *out = v;
 }
 
+// Small counts: one block of 1024 threads sums the partials directly.
+__global__ void __launch_bounds__(1024) k_reduce_small(const double *__restrict__ partials,
+                                                       int count, double *__restrict__ out) {
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int t = threadIdx.x; t < count; t += 1024) v += partials[t];
+    v = block_sum_f64<1024>(v, red);
+    if (threadIdx.x == 0) *out = v;
+}
+
 int reduce_partials(const double *partials, int64_t count, double *tmp, double *out,
                     cudaStream_t s) {
+    if (count <= 65536) {
+        k_reduce_small<<<1, 1024, 0, s>>>(partials, (int)count, out);
+        note_launches(1);
+        return launch_status();
+    }
     int64_t chunk = (count + kReduceSlots - 1) / kReduceSlots;
     if (chunk < 1) chunk = 1;
     const int slots = (int)((count + chunk - 1) / chunk);

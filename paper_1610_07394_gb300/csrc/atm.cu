@@ -42,7 +42,7 @@ struct AtmTables {
 
 // Loads the three point tiles (zero past n).
 __device__ __forceinline__ void load_tiles(const float *__restrict__ x, int64_t n, int I, int J,
-                                           int K, AtmTables &T) {
+                                           int K, float4 (*xs)[R_]) {
     const int tid = threadIdx.x;
     if (tid < 3 * R_) {
         const int which = tid / R_, o = tid % R_;
@@ -50,7 +50,7 @@ __device__ __forceinline__ void load_tiles(const float *__restrict__ x, int64_t 
         const int64_t g = (int64_t)blk * R_ + o;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (g < n) v = make_float4(__ldg(x + 3 * g), __ldg(x + 3 * g + 1), __ldg(x + 3 * g + 2), 0.f);
-        T.xs[which][o] = v;
+        xs[which][o] = v;
     }
 }
 
@@ -103,15 +103,55 @@ __device__ __forceinline__ float dot3(float3 a, float4 b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
 }
 
-// One triple's energy without nu: R^3 (1 + 3 cos g_i cos g_j cos g_k) added
-// to acc; B = (u_jk, r_jk^3), C = (u_ik, r_ik^3).  15 FP32 operations.
-__device__ __forceinline__ void triple_energy(float4 B, float4 C, const PairConst &c, float &acc) {
-    const float ci = dot3(c.u, C);                 // cos g_i
-    const float cj3 = dot3(c.f, B);                // 3 cos g_j
-    const float ck = dot3(C, B);                   // cos g_k
-    const float C3 = (ci * cj3) * ck;
-    const float R3 = (c.u.w * C.w) * B.w;
-    acc = fmaf(R3, 1.0f + C3, acc);
+// Energy tables, laid out for packed FP32x2 arithmetic over the thread's two
+// i-slots p = 0, 1 (i = ti and ti + 16):
+//   ec[k][0][ti] = (u_ik0.x, u_ik1.x, u_ik0.y, u_ik1.y), ec[k][1][ti] = (u_ik0.z, u_ik1.z, r_ik0^3, r_ik1^3)
+//   eb[k][q][0][tj] = (u.x, u.x, u.y, u.y), eb[k][q][1][tj] = (u.z, u.z, r^3, r^3) of pair (j = tj + 16q, k),
+// each (j, k) value duplicated so one broadcast load feeds both lanes.  A
+// warp's 16 distinct ti read 256 contiguous bytes (two wavefronts, no bank
+// conflict); its two tj read two addresses (one broadcast wavefront).
+struct AtmEnergySmem {
+    float4 xs[3][R_];
+    float4 ec[R_][2][16];
+    float4 eb[R_][2][2][16];
+};
+
+__device__ __forceinline__ void put_pair(float4 &lo, float4 &hi, int lane, float4 v) {
+    float *a = reinterpret_cast<float *>(&lo), *b = reinterpret_cast<float *>(&hi);
+    a[lane] = v.x; a[2 + lane] = v.y; b[lane] = v.z; b[2 + lane] = v.w;
+}
+
+__device__ __forceinline__ void build_energy_tables(int64_t n, int I, int J, int K, float eps,
+                                                    AtmEnergySmem &S) {
+    for (int e = threadIdx.x; e < R_ * R_; e += 256) {
+        const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
+        const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
+        const float4 c = pair_term<true>(S.xs[0][o], S.xs[2][k], gi < gk && gk < n, eps);
+        put_pair(S.ec[k][0][t], S.ec[k][1][t], half, c);
+        const float4 b = pair_term<true>(S.xs[1][o], S.xs[2][k], gj < gk && gk < n, eps);
+        S.eb[k][half][0][t] = make_float4(b.x, b.x, b.y, b.y);
+        S.eb[k][half][1][t] = make_float4(b.z, b.z, b.w, b.w);
+    }
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Two triples (i0, j, k) and (i1, j, k) in the two lanes: with the unit
+// vectors of the pairs and the product w = r_ik^3 r_jk^3,
+//   acc += w (1 - 3 (u_ij.u_ik)(u_ij.u_jk)(u_ik.u_jk)),
+// i.e. the term e / (nu r_ij^3) (cos g_j = -u_ij.u_jk); r_ij^3 multiplies the
+// sum over k afterwards.  14 packed FP32x2 operations.
+__device__ __forceinline__ void triple_energy2(const float2 (&uij)[3], float4 C0, float4 C1,
+                                               float4 B0, float4 B1, float2 &acc) {
+    const float2 cx = lo2(C0), cy = hi2(C0), cz = lo2(C1), cw = hi2(C1);
+    const float2 bx = lo2(B0), by = hi2(B0), bz = lo2(B1), bw = hi2(B1);
+    const float2 ci = __ffma2_rn(uij[0], cx, __ffma2_rn(uij[1], cy, __fmul2_rn(uij[2], cz)));
+    const float2 cj = __ffma2_rn(uij[0], bx, __ffma2_rn(uij[1], by, __fmul2_rn(uij[2], bz)));
+    const float2 ck = __ffma2_rn(cx, bx, __ffma2_rn(cy, by, __fmul2_rn(cz, bz)));
+    const float2 c3 = __fmul2_rn(__fmul2_rn(ci, cj), ck);
+    const float2 t = __ffma2_rn(make_float2(-3.0f, -3.0f), c3, make_float2(1.0f, 1.0f));
+    acc = __ffma2_rn(__fmul2_rn(cw, bw), t, acc);
 }
 
 // The (up to two) data blocks of a grid block, read without dynamic indexing.
@@ -125,7 +165,8 @@ template <int MAP>
 __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *__restrict__ x,
                                                        float nu, float eps, int nb, int p,
                                                        double *__restrict__ partials) {
-    __shared__ AtmTables T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AtmEnergySmem &S = *reinterpret_cast<AtmEnergySmem *>(smem_raw);
     __shared__ float red[16];
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
     const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
@@ -135,29 +176,39 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
         int I, J, K;
         block_of(L, t, I, J, K);
         if (t) __syncthreads();
-        load_tiles(x, n, I, J, K, T);
+        load_tiles(x, n, I, J, K, S.xs);
         __syncthreads();
-        build_tables<true>(n, I, J, K, eps, T);
-        PairConst pc[2][2];
+        build_energy_tables(n, I, J, K, eps, S);
+        // pair constants: u_ij of slots (p, q) packed over p, and r_ij^3
+        float2 uij[2][3];
+        float ra3[2][2];
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) pc[a][b] = pair_const<true>(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
+        for (int q = 0; q < 2; ++q) {
+            const int64_t gj = (int64_t)J * R_ + tj + 16 * q;
+            const float4 u0 = pair_term<true>(S.xs[0][ti], S.xs[1][tj + 16 * q],
+                                              (int64_t)I * R_ + ti < gj && gj < n, eps);
+            const float4 u1 = pair_term<true>(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
+                                              (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
+            uij[q][0] = make_float2(u0.x, u1.x);
+            uij[q][1] = make_float2(u0.y, u1.y);
+            uij[q][2] = make_float2(u0.z, u1.z);
+            ra3[0][q] = u0.w;
+            ra3[1][q] = u1.w;
+        }
         __syncthreads();
-        float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int k = 0; k < R_; ++k) {
-            const float4 B0 = T.tb[k][0][tj], B1 = T.tb[k][1][tj];
-            const float4 C0 = T.tc[k][0][ti], C1 = T.tc[k][1][ti];
-            triple_energy(B0, C0, pc[0][0], acc[0][0]);
-            triple_energy(B1, C0, pc[0][1], acc[0][1]);
-            triple_energy(B0, C1, pc[1][0], acc[1][0]);
-            triple_energy(B1, C1, pc[1][1], acc[1][1]);
+            const float4 C0 = S.ec[k][0][ti], C1 = S.ec[k][1][ti];
+            const float4 B00 = S.eb[k][0][0][tj], B01 = S.eb[k][0][1][tj];
+            const float4 B10 = S.eb[k][1][0][tj], B11 = S.eb[k][1][1][tj];
+            triple_energy2(uij[0], C0, C1, B00, B01, acc0);
+            triple_energy2(uij[1], C0, C1, B10, B11, acc1);
         }
-        add_ff(hi, lo, acc[0][0], 0.f);
-        add_ff(hi, lo, acc[0][1], 0.f);
-        add_ff(hi, lo, acc[1][0], 0.f);
-        add_ff(hi, lo, acc[1][1], 0.f);
+        add_ff(hi, lo, acc0.x * ra3[0][0], 0.f);
+        add_ff(hi, lo, acc0.y * ra3[1][0], 0.f);
+        add_ff(hi, lo, acc1.x * ra3[0][1], 0.f);
+        add_ff(hi, lo, acc1.y * ra3[1][1], 0.f);
     }
     const double s = block_sum_ff<256>(hi, lo, red);
     if (threadIdx.x == 0) {
@@ -236,7 +287,7 @@ __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__re
         int I, J, K;
         block_of(L, t, I, J, K);
         if (t) __syncthreads();
-        load_tiles(x, n, I, J, K, T);
+        load_tiles(x, n, I, J, K, T.xs);
         for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
         __syncthreads();
         build_tables<false>(n, I, J, K, eps, T);
@@ -334,9 +385,11 @@ __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__re
     }
 }
 
-// The force kernel's shared memory exceeds the 48 KB default of a launch;
-// opt in once per device for each instantiation.
-static int forces_smem_optin(int bytes) {
+constexpr int kEnergySmem = (int)sizeof(AtmEnergySmem);
+
+// Both kernels' shared memory exceeds the 48 KB default of a launch; opt in
+// once per device for every instantiation.
+static int smem_optin() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e);
@@ -345,9 +398,14 @@ static int forces_smem_optin(int bytes) {
     if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
-        if ((e = cudaFuncSetAttribute(k_atm_forces<MAP_LAMBDA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_atm_forces<MAP_BBOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        const int fb = (int)sizeof(AtmForceSmem);
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if ((e = cudaFuncSetAttribute(k_atm_forces<MAP_LAMBDA>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_BBOX>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_energy<MAP_LAMBDA>, a, kEnergySmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_energy<MAP_BBOX>, a, kEnergySmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_energy<MAP_LINEAR>, a, kEnergySmem)) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -384,10 +442,11 @@ extern "C" int simplex_atm_energy(int64_t n, int64_t d, const float *x, float nu
     double *partials = (double *)workspace;
     const int64_t blocks = g.gx * g.gy * g.gz;
     double *tmp = partials + blocks;
+    if ((st = smem_optin())) return st;
     prof_begin(s);
-    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
-    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
-    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;
@@ -408,7 +467,7 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
     const int64_t blocks = g.gx * g.gy * g.gz;
     if ((st = cuda_status(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s)))) return st;
     const int smem = (int)sizeof(AtmForceSmem);
-    if ((st = forces_smem_optin(smem))) return st;
+    if ((st = smem_optin())) return st;
     prof_begin(s);
     if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
     else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
@@ -472,10 +531,11 @@ extern "C" int simplex_atm_energy_noalloc(int64_t n, int64_t d, const float *x, 
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
     double *partials = scratch, *tmp = scratch + blocks;
+    if ((st = smem_optin())) return st;
     prof_begin(s);
-    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
-    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
-    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;
