@@ -46,6 +46,8 @@ NU, EPS = 1.0, 1e-4
 # (2), R^3 = r_ij^3 r_ik^3 r_jk^3 (2), the bracket 1 + 3 cos cos cos (2, one
 # FMA) and the running sum (1): 22 flops.
 FLOPS_PER_TRIPLE = 22
+ROWS_NAMES = ("edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
+              "stress_n65536_d64", "edm_n16384_d64")
 FP32_LANES_PER_SM = 128
 L2_FLUSH_BYTES = 512 << 20
 
@@ -57,6 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", choices=["auto", "on", "off"], default="auto")
+    ap.add_argument("--row", choices=sorted(ROWS_NAMES), default=None,
+                    help="time only this row (no headline line)")
     return ap.parse_args()
 
 
@@ -211,105 +215,169 @@ def config_block():
 
 # ------------------------------------------------------------------ our arm
 
-def rows_measure(torch, sx, peaks):
-    """Every other kernel of the path at its own configuration."""
-    out = {}
-    dev = "cuda"
-    hbm = peaks["hbm_gbs"]
+def _median_ms(torch, fn, steps, warmup=1):
+    return statistics.median(time_steps(torch, fn, steps, warmup))
 
-    def t_ms(fn, steps, warmup=1):
-        return statistics.median(time_steps(torch, fn, steps, warmup))
 
-    def kernel_ms(fn, steps=3, warmup=1):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
-        sx.simplex_profile(True)
-        for _ in range(steps):
-            fn()
-        ms, k, _ = sx.simplex_profile_read()
-        sx.simplex_profile(False)
-        return ms / max(k, 1)
+def _kernel_ms(torch, sx, fn, steps=3, warmup=1):
+    """Average duration of the entry point's main kernel (library event pairs)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    sx.simplex_profile(True)
+    for _ in range(steps):
+        fn()
+    ms, k, _ = sx.simplex_profile_read()
+    sx.simplex_profile(False)
+    return ms / max(k, 1)
 
-    # EDM n=1024, d=3: 524,800 FP32 outputs (2.1 MB): one launch is a few
-    # microseconds, so a step is a batch of 100 launches.
-    x = torch.from_numpy(synth.make_points("edm_n1024_d3")).to(dev)
-    o = torch.empty(1024 * 1025 // 2, device=dev)
-    pairs = 1024 * 1025 // 2
-    r = {"unit": "pairs/s", "pairs": pairs, "note": "batch of 100 launches per timed step; output L2-resident"}
+
+def row_edm_n1024_d3(torch, sx, peaks):
+    """EDM n=1024, d=3: 524,800 FP32 outputs (2.1 MB); one launch is a few
+    microseconds, so a step is a batch of 100 launches."""
+    x = torch.from_numpy(synth.make_points("edm_n1024_d3")).cuda()
+    o = torch.empty(1024 * 1025 // 2, device="cuda")
+    pairs = o.numel()
+    r = {"unit": "pairs/s", "pairs": pairs, "prec": "fp32",
+         "note": "batch of 100 launches per timed step; output L2-resident"}
     for mp in ("lambda", "bbox", "linear"):
         f = lambda: [sx.simplex_edm_packed(x, o, mp, "fp32") for _ in range(100)]  # noqa: E731
-        ms = t_ms(f, 5) / 100
+        ms = _median_ms(torch, f, 5) / 100
         r[mp] = pairs / (ms / 1e3)
         r[mp + "_us"] = ms * 1e3
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
-    out["edm_n1024_d3"] = r
+    return r
 
-    # EDM n=32768, d=256 (FP32 SIMT path): 536,887,296 outputs, 2.15 GB written.
-    x = torch.from_numpy(synth.make_points("edm_n32768_d256")).to(dev)
-    o = torch.empty(32768 * 32769 // 2, device=dev)
+
+def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox")):
+    n, d = x.shape
+    o = torch.empty(n * (n + 1) // 2, device="cuda")
     pairs = o.numel()
-    r = {"unit": "pairs/s", "pairs": pairs, "prec": "fp32"}
-    for mp in ("lambda", "bbox"):
-        ms = kernel_ms(lambda: sx.simplex_edm_packed(x, o, mp, "fp32"))
+    ws = {mp: sx.workspace("edm", n, d, mp, prec) for mp in maps}
+    r = {"unit": "pairs/s", "pairs": pairs, "prec": prec}
+    for mp in maps:
+        ms = _kernel_ms(torch, sx, lambda: sx.simplex_edm_packed(x, o, mp, prec, ws[mp]))
         r[mp] = pairs / (ms / 1e3)
         r[mp + "_ms"] = ms
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
-    r["hbm_frac_lambda"] = (4.0 * pairs / (r["lambda_ms"] / 1e3) / 1e9) / hbm
-    out["edm_n32768_d256"] = r
-    del x, o
-    torch.cuda.empty_cache()
+    t = r["lambda_ms"] / 1e3
+    r["hbm_gbs_lambda"] = 4.0 * pairs / t / 1e9          # packed output written
+    r["hbm_frac_lambda"] = r["hbm_gbs_lambda"] / peaks["hbm_gbs"]
+    if prec != "fp32":
+        r["tensor_tflops_lambda"] = 6.0 * d * pairs / t / 1e12   # hi.hi + hi.lo + lo.hi
+        r["tensor_frac_lambda"] = r["tensor_tflops_lambda"] / peaks["bf16_tflops"]
+    sx.simplex_device_errors()
+    return r
 
-    # ATM n=4096 (differentiation config): energy, energy+forces.
-    x = torch.from_numpy(synth.make_points("atm_n4096")).to(dev)
+
+def row_edm_n32768_d256(torch, sx, peaks):
+    """EDM n=32768, d=256 on tensor cores (BF16 hi+lo split): 536,887,296
+    outputs, 2.15 GB written; FP32 SIMT path alongside."""
+    x = torch.from_numpy(synth.make_points("edm_n32768_d256")).cuda()
+    r = _edm_big(torch, sx, peaks, x, "bf16x3")
+    r["fp32_simt_lambda"] = _edm_big(torch, sx, peaks, x, "fp32", ("lambda", "bbox"))["lambda"]
+    return r
+
+
+def row_edm_n65536_d64(torch, sx, peaks):
+    """EDM n=65536, d=64 on tensor cores: 2,147,516,416 outputs, 8.6 GB."""
+    w = synth.WORKLOADS["stress_n65536_d64"]
+    x = torch.from_numpy(synth.normal(w["n"], w["d"], w["seed"])).cuda()
+    return _edm_big(torch, sx, peaks, x, "bf16x3")
+
+
+def row_edm_n16384_d64(torch, sx, peaks):
+    """EDM n=16384, d=64 on tensor cores (134M outputs, 537 MB): a smaller
+    case of the same kernel, sized for profiler captures."""
+    x = torch.from_numpy(synth.normal(16384, 64, seed=4)).cuda()
+    return _edm_big(torch, sx, peaks, x, "bf16x3")
+
+
+def row_atm_n4096(torch, sx, peaks):
+    """ATM n=4096 (differentiation config): energy, energy+forces."""
+    x = torch.from_numpy(synth.make_points("atm_n4096")).cuda()
     n = 4096
     r = {"unit": "triplets/s", "triples": triples(n)}
-    e = torch.empty((), dtype=torch.float64, device=dev)
+    e = torch.empty((), dtype=torch.float64, device="cuda")
     for mp in ("lambda", "bbox", "linear"):
         ws = sx.workspace("atm_energy", n, 3, mp)
-        ms = t_ms(lambda: sx.simplex_atm_energy(x, NU, EPS, e, mp, ws), 3)
+        ms = _median_ms(torch, lambda: sx.simplex_atm_energy(x, NU, EPS, e, mp, ws), 3)
         r["energy_" + mp] = triples(n) / (ms / 1e3)
     r["energy_lambda_vs_bbox"] = r["energy_lambda"] / r["energy_bbox"]
-    f = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     for mp in ("lambda", "bbox"):
         ws = sx.workspace("atm_forces", n, 3, mp)
-        ms = t_ms(lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws), 3)
+        ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws), 3)
         r["energy_forces_" + mp] = triples(n) / (ms / 1e3)
     r["energy_forces_lambda_vs_bbox"] = r["energy_forces_lambda"] / r["energy_forces_bbox"]
-    out["atm_n4096"] = r
+    return r
 
-    # ATM n=16384 (scale config): 7.33e11 triples.
+
+def row_atm_n16384(torch, sx, peaks):
+    """ATM n=16384 (scale config): 7.33e11 triples."""
     n = 16384
-    x = torch.from_numpy(synth.make_points("atm_n16384")).to(dev)
+    x = torch.from_numpy(synth.make_points("atm_n16384")).cuda()
     r = {"unit": "triplets/s", "triples": triples(n)}
+    e = torch.empty((), dtype=torch.float64, device="cuda")
     ws = sx.workspace("atm_forces", n, 3, "lambda")
-    ms = t_ms(lambda: sx.simplex_atm_energy(x, NU, EPS, e, "lambda", ws), 1, 0)
+    ms = _median_ms(torch, lambda: sx.simplex_atm_energy(x, NU, EPS, e, "lambda", ws), 1, 0)
     r["energy_lambda"] = triples(n) / (ms / 1e3)
-    f = torch.empty((n, 3), dtype=torch.float64, device=dev)
-    ms = t_ms(lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, "lambda", ws), 1, 0)
+    f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, "lambda", ws), 1, 0)
     r["energy_forces_lambda"] = triples(n) / (ms / 1e3)
-    out["atm_n16384"] = r
-    del ws
-    torch.cuda.empty_cache()
+    return r
 
-    # Stress loss n=65536, d=64: forward (loss only) and backward.
+
+def row_stress_n65536_d64(torch, sx, peaks):
+    """Stress loss n=65536, d=64: forward (loss only) and backward."""
     w = synth.WORKLOADS["stress_n65536_d64"]
     xn = synth.normal(w["n"], w["d"], w["seed"])
     yn = synth.perturbed(xn, w["sigma"], w["y_seed"])
-    x = torch.from_numpy(xn).to(dev)
-    y = torch.from_numpy(yn).to(dev)
+    x = torch.from_numpy(xn).cuda()
+    y = torch.from_numpy(yn).cuda()
     n = w["n"]
     pairs = n * (n - 1) // 2
     r = {"unit": "pairs/s", "pairs": pairs}
-    loss = torch.empty((), dtype=torch.float64, device=dev)
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
     ws = sx.workspace("stress_fwd", n, w["d"], "lambda")
-    ms = t_ms(lambda: sx.simplex_stress_fwd(x, y, None, loss, "lambda", "fp32", ws), 2)
+    ms = _median_ms(torch, lambda: sx.simplex_stress_fwd(x, y, None, loss, "lambda", "fp32", ws), 2)
     r["fwd_lambda"] = pairs / (ms / 1e3)
     g = torch.empty_like(x)
-    ms = t_ms(lambda: sx.simplex_stress_bwd(x, y, 1.0, g, "lambda", "fp32"), 2)
+    ms = _median_ms(torch, lambda: sx.simplex_stress_bwd(x, y, 1.0, g, "lambda", "fp32"), 2)
     r["bwd_lambda"] = pairs / (ms / 1e3)
-    out["stress_n65536_d64"] = r
+    return r
+
+
+ROWS = {
+    "edm_n1024_d3": row_edm_n1024_d3,
+    "edm_n32768_d256": row_edm_n32768_d256,
+    "edm_n65536_d64": row_edm_n65536_d64,
+    "atm_n4096": row_atm_n4096,
+    "atm_n16384": row_atm_n16384,
+    "stress_n65536_d64": row_stress_n65536_d64,
+}
+# profiling-only cases (not part of the default rows)
+PROFILE_ROWS = {"edm_n16384_d64": row_edm_n16384_d64}
+
+
+def rows_measure(torch, sx, peaks, names=None):
+    """Every other kernel of the path at its own configuration."""
+    out = {}
+    for name, fn in ROWS.items():
+        if names is None or name in names:
+            out[name] = fn(torch, sx, peaks)
+            torch.cuda.empty_cache()
     return out
+
+
+def row_only(args):
+    """--row NAME: just that row (for profiling one kernel)."""
+    import torch
+    import paper_1610_07394_gb300 as sx
+    sx.lib()
+    peaks, _ = measured_peaks()
+    fn = ROWS.get(args.row) or PROFILE_ROWS[args.row]
+    print(json.dumps({"row": args.row, **fn(torch, sx, peaks)}), flush=True)
 
 
 def our_arm(args):
@@ -434,7 +502,9 @@ def our_arm(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.row:
+        row_only(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         our_arm(args)

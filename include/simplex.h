@@ -52,8 +52,9 @@ typedef enum {
     SIMPLEX_EUNSUPPORTED = 4, /* valid request this build does not serve     */
     SIMPLEX_ECUDA = 5,        /* a CUDA call failed                          */
     SIMPLEX_EWORKSPACE = 6,   /* workspace missing, too small or misaligned  */
-    SIMPLEX_ESCRATCH = 7      /* problem too large for the library's static
+    SIMPLEX_ESCRATCH = 7,     /* problem too large for the library's static
                                  scratch (simplex_atm_energy_noalloc)        */
+    SIMPLEX_ETIMEOUT = 8      /* a bounded device-side wait ran out          */
 } simplex_status;
 
 typedef enum {
@@ -143,10 +144,15 @@ int simplex_map3(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
  * 2-simplex problem): out[i(i+1)/2 + j] = |x_i - x_j|^2 (squared distance)
  * for 0 <= j <= i < n; the diagonal is exactly 0.
  * x: device, n*d FP32, 4-byte aligned.  out: device, n(n+1)/2 FP32.
- * prec: SIMPLEX_PREC_FP32 (difference form, any d) or SIMPLEX_PREC_BF16X3
- * (Gram form on tensor cores with a hi+lo BF16 split and an FP32 recompute of
- * near-zero entries; needs d % 16 == 0); AUTO picks BF16X3 when d >= 32 and
- * d % 16 == 0.  Needs workspace for BF16X3 (see simplex_workspace_bytes).
+ * prec: SIMPLEX_PREC_FP32 (difference form, any d, 32 x 32 tiles) or
+ * SIMPLEX_PREC_BF16X3: |x_i|^2 + |x_j|^2 - 2 x_i.x_j with the Gram term on
+ * tensor cores (tcgen05, FP32 accumulation in tensor memory) from a BF16
+ * split x = hi + lo (three products hi.hi + hi.lo + lo.hi), FP32 norms, and
+ * an FP32 recompute of entries below (|x_i|^2 + |x_j|^2)/64; 128 x 128 tiles;
+ * needs d % 64 == 0.  AUTO picks BF16X3 when d >= 64 and d % 64 == 0.
+ * BF16X3 needs workspace (simplex_workspace_bytes; 1024-byte aligned) for
+ * the BF16 copies and the norms.  Its device waits are bounded: check
+ * simplex_device_errors() when a result must be trusted.
  */
 int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *out, int map,
                        int prec, void *workspace, int64_t ws_bytes, void *stream);
@@ -193,6 +199,11 @@ int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const float *y,
 int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
                        double gscale, float *grad, int map, int prec,
                        void *workspace, int64_t ws_bytes, void *stream);
+
+/* Synchronises `stream` and reports whether any bounded device-side wait of
+ * the tensor-core kernels ran out since the last check (SIMPLEX_ETIMEOUT,
+ * flag cleared), else SIMPLEX_OK. */
+int simplex_device_errors(void *stream);
 
 /* Bytes of workspace an operation needs (0 if none, -1 on bad arguments). */
 int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map, int prec);

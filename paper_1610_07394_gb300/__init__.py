@@ -36,7 +36,7 @@ EXPORTS = [
     "simplex_grid_blocks", "simplex_map_blocks", "simplex_map_blocks_host", "simplex_map2",
     "simplex_map3", "simplex_edm_packed", "simplex_atm_energy", "simplex_atm_forces",
     "simplex_stress_fwd", "simplex_stress_bwd", "simplex_workspace_bytes", "simplex_profile",
-    "simplex_profile_read", "simplex_atm_energy_noalloc",
+    "simplex_profile_read", "simplex_atm_energy_noalloc", "simplex_device_errors",
 ]
 
 
@@ -70,6 +70,7 @@ def _signatures(L):
         "simplex_stress_bwd": (_i32, [_i64, _i64, _vp, _vp, _f64, _vp, _i32, _i32, _vp, _i64, _vp]),
         "simplex_workspace_bytes": (_i64, [_i32, _i64, _i64, _i32, _i32]),
         "simplex_profile": (_i32, [_i32]),
+        "simplex_device_errors": (_i32, [_vp]),
         "simplex_atm_energy_noalloc": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _i32, _vp]),
         "simplex_profile_read": (_i32, [ctypes.POINTER(_f64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     }
@@ -217,6 +218,11 @@ def simplex_stress_bwd(x, y, gscale, grad, map="lambda", prec="fp32", workspace=
         n, d, _cuda(x, torch.float32, "x"), _cuda(y, torch.float32, "y"), float(gscale),
         _cuda(grad, torch.float32, "grad"), _map(map), _prec(prec), ws,
         0 if workspace is None else workspace.numel(), _stream(stream)))
+
+
+def simplex_device_errors(stream=None):
+    """Raises if a bounded device-side wait ran out (synchronises the stream)."""
+    _check("simplex_device_errors", lib().simplex_device_errors(_stream(stream)))
 
 
 def simplex_profile(on: bool):

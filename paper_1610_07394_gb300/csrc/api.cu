@@ -146,6 +146,7 @@ extern "C" const char *simplex_strerror(int status) {
         case SIMPLEX_ECUDA: return "CUDA call failed (see simplex_last_cuda_error)";
         case SIMPLEX_EWORKSPACE: return "workspace missing, too small or misaligned";
         case SIMPLEX_ESCRATCH: return "problem too large for the library's static scratch";
+        case SIMPLEX_ETIMEOUT: return "a bounded device-side wait ran out";
         default: return "unknown status";
     }
 }

@@ -28,14 +28,16 @@ __global__ void __launch_bounds__(256) k_edm_simt(int64_t n, int d, const float 
     }
 }
 
-int edm_rho(int64_t d, int prec) {
-    (void)d; (void)prec;
-    return kEdmRho;
+// Whether a request runs on the tensor-core path.
+static bool use_umma(int64_t d, int prec) {
+    return prec == SIMPLEX_PREC_BF16X3 || (prec == SIMPLEX_PREC_AUTO && d >= 64 && d % 64 == 0);
 }
 
+int edm_rho(int64_t d, int prec) { return use_umma(d, prec) ? kEdmUmmaRho : kEdmRho; }
+
 int64_t edm_workspace_bytes(int64_t n, int64_t d, int map, int prec) {
-    (void)n; (void)d; (void)map; (void)prec;
-    return 0;
+    (void)map;
+    return use_umma(d, prec) ? edm_umma_workspace_bytes(n, d) : 0;
 }
 
 }  // namespace sx
@@ -44,12 +46,12 @@ using namespace sx;
 
 extern "C" int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *out, int map,
                                   int prec, void *workspace, int64_t ws_bytes, void *stream) {
-    (void)workspace; (void)ws_bytes;
     if (n < 1 || d < 1 || !x || !out || map < MAP_LAMBDA || map > MAP_LINEAR) return SIMPLEX_EINVAL;
     if (prec < SIMPLEX_PREC_FP32 || prec > SIMPLEX_PREC_AUTO) return SIMPLEX_EINVAL;
-    if (prec == SIMPLEX_PREC_BF16X3) return SIMPLEX_EUNSUPPORTED;
     if (!aligned(x, 4) || !aligned(out, 4)) return SIMPLEX_EALIGN;
     if (d > (1 << 24) || n > ((int64_t)1 << 31) || n * d > ((int64_t)1 << 40)) return SIMPLEX_EOVERFLOW;
+    if (use_umma(d, prec))
+        return edm_umma_run(n, d, x, out, map, workspace, ws_bytes, (cudaStream_t)stream);
     const int64_t nb = (n + kEdmRho - 1) / kEdmRho;
     const Grid g = grid2(nb, map);
     if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;

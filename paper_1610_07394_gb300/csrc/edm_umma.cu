@@ -1,0 +1,618 @@
+// edm_umma.cu -- packed EDM with the Gram term on the 5th-generation tensor
+// cores (tcgen05, TMEM accumulators, TMA-staged operands), for large d.
+//
+// For a 128 x 128 tile of pairs (rows i of block Y, columns j of block X,
+// X <= Y, the block chosen by a block-space map of Sec. III-A):
+//   D_ij = |x_i|^2 + |x_j|^2 - 2 g_ij,   g_ij = x_i . x_j,
+// with g from BF16 operands split as x = hi + lo (hi = bf16(x),
+// lo = bf16(x - hi)):  g ~ hi_i.hi_j + hi_i.lo_j + lo_i.hi_j, accumulated in
+// FP32 in tensor memory.  The norms are FP32 sums of the original FP32
+// coordinates.  Entries with D < |x_i|^2/64 + |x_j|^2/64 (where the Gram
+// form cancels) are recomputed in FP32 from the coordinates; the diagonal is
+// exactly 0.
+//
+// Persistent and warp-specialised: one CTA per SM walks the grid of the
+// chosen block-space map (grid blocks blockIdx.x, blockIdx.x + gridDim.x, ...)
+// and handles the tiles they map to.  Warp 0 issues the TMA loads of the
+// four 128 x 64 BF16 operand tiles of each K-chunk (128-byte swizzle) into a
+// two-stage ring; warp 1 issues the tcgen05.mma instructions (M = N = 128,
+// K = 16, three products per K step) into one of two 128-column TMEM
+// accumulators; eight epilogue warps (two per TMEM lane quarter) read a
+// finished accumulator with tcgen05.ld, form D, stage rows through shared
+// memory and write each packed row segment with coalesced stores, while the
+// MMA warp already fills the other accumulator.  Every mbarrier wait is
+// bounded in time; a wait that runs out sets a device error flag
+// (simplex_device_errors) and the block stops instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstddef>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sx {
+namespace umma {
+
+constexpr int TM = 128;                        // tile rows (i)
+constexpr int TN = 128;                        // tile columns (j)
+constexpr int KC = 64;                         // K chunk: 64 BF16 = one 128-byte swizzle row
+constexpr int TILE_BYTES = TM * KC * 2;        // 16 KB per operand tile
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int TMEM_COLS = 128;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+// Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5),
+// A = B = BF16 (bits 7-9, 10-12), both K-major (bits 15, 16 = 0),
+// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ int g_error;   // set when a bounded wait runs out
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// One potentially blocking test of the phase: the thread may be suspended
+// up to kSuspendNs while the phase is incomplete (instead of spinning).
+constexpr uint32_t kSuspendNs = 200000;
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase), "r"(kSuspendNs)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of parity `phase` to complete, at most kWaitCycles,
+// or until another thread of the block has flagged a failure.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile int *fail) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, phase)) {
+        if (*fail) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *fail = 1;
+            atomicExch(&g_error, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// shared -> global bulk copy (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_store(float *gdst, uint32_t ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(ssrc), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// waits until this thread's committed bulk copies have read their sources
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile with 128-byte
+// swizzle: start address >> 4 (bits 0-13), leading byte offset 16 >> 4
+// (bits 16-29, unused by this layout), stride byte offset 1024 >> 4 between
+// 8-row groups (bits 32-45), descriptor version 1 (bit 46), swizzle mode 2 =
+// 128 B (bits 61-63).  The tile base is 1024-byte aligned, so base offset 0.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+}
+
+// x = hi + lo in BF16 and |x|^2 in FP32, one warp per row.
+__global__ void __launch_bounds__(256) k_split_bf16(const float *__restrict__ x, int64_t n, int d,
+                                                    __nv_bfloat16 *__restrict__ xh,
+                                                    __nv_bfloat16 *__restrict__ xl,
+                                                    float *__restrict__ nrm) {
+    const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const float *xr = x + row * d;
+    float acc = 0.f;
+    for (int t = lane; t < d; t += 32) {
+        const float v = __ldg(xr + t);
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        xh[row * d + t] = h;
+        xl[row * d + t] = __float2bfloat16_rn(v - __bfloat162float(h));
+        acc = fmaf(v, v, acc);
+    }
+    acc = warp_sum_f32(acc);
+    if (lane == 0) nrm[row] = acc;
+}
+
+// |x_i - x_j|^2 in FP32 from the coordinates (kept out of line: it is rare).
+__device__ __noinline__ float exact_sqdist(const float *__restrict__ x, int64_t i, int64_t j, int d) {
+    const float *xi = x + i * d, *xj = x + j * d;
+    float acc = 0.0f;
+    for (int e = 0; e < d; ++e) {
+        const float df = __ldg(xi + e) - __ldg(xj + e);
+        acc = fmaf(df, df, acc);
+    }
+    return acc;
+}
+
+constexpr int kStages = 2;                     // operand pipeline depth
+constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
+constexpr int kAccCols = 2 * TN;               // two accumulators in TMEM
+
+// Epilogue staging of one warp: 32 rows of 64 FP32 columns each, row pitch
+// 68 floats.  A row is written at an offset of (its global address mod 16
+// bytes) / 4 floats, so that the 16-byte-aligned body of the global row
+// segment starts at a 16-byte-aligned shared address and one cp.async.bulk
+// copies it.
+constexpr int kStageCols = 64;
+constexpr int kStagePitch = 68;
+
+struct PCtl {
+    uint64_t full[kStages], empty[kStages];   // operand stages: TMA -> MMA -> TMA
+    uint64_t tfull[2], tempty[2];             // accumulators: MMA -> epilogue -> MMA
+    uint32_t tmem;
+    int fail;
+    alignas(16) float ncol[kEpiWarps][64];    // each epilogue warp's column norms (float4 reads)
+};
+
+constexpr int kCtlBytes = 3072;
+constexpr int PSMEM_BYTES = 1024 + kStages * STAGE_BYTES + kEpiWarps * 32 * kStagePitch * 4 + kCtlBytes;
+static_assert(sizeof(PCtl) <= kCtlBytes, "control block");
+static_assert(offsetof(PCtl, ncol) % 16 == 0, "float4 reads of the column norms");
+static_assert(PSMEM_BYTES <= 227 * 1024, "shared memory per block");
+
+// The tiles of the grid blocks this CTA owns, in order: grid blocks
+// w = blockIdx.x + k gridDim.x of the map's grid (gx x gy), each sent by the
+// map to zero, one or two 128 x 128 tiles (column block X <= row block Y).
+template <int MAP>
+struct TileWalk {
+    int64_t w, total;   // linear grid-block index (x fastest) and grid size
+    int wx, wy, gx, nb;
+    int pend, px, py;   // second tile of a diagonal pair, still to visit
+    __device__ TileWalk(int gx_, int64_t total_, int nb_)
+        : w(blockIdx.x), total(total_), gx(gx_), nb(nb_), pend(0), px(0), py(0) {
+        wy = (int)(blockIdx.x / (unsigned)gx_);
+        wx = (int)(blockIdx.x - (unsigned)wy * (unsigned)gx_);
+    }
+    __device__ bool next(int &X, int &Y) {
+        if (pend) { pend = 0; X = px; Y = py; return true; }
+        while (w < total) {
+            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb)
+                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb);
+            // advance by gridDim.x grid blocks without a division
+            w += gridDim.x;
+            wx += (int)gridDim.x;
+            while (wx >= gx) { wx -= gx; ++wy; }
+            if (L.cnt == 0) continue;
+            X = L.x[0]; Y = L.y[0];
+            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
+            return true;
+        }
+        return false;
+    }
+};
+
+__device__ __forceinline__ void named_bar(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int MAP>
+__global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
+                                                          const __grid_constant__ CUtensorMap map_lo,
+                                                          const float *__restrict__ x,
+                                                          const float *__restrict__ nrm,
+                                                          float *__restrict__ out, int64_t n, int d,
+                                                          int nb, int gx, int64_t total) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *stages = base;   // kStages x 64 KB, 1024-aligned tiles
+    float *stg_all = reinterpret_cast<float *>(base + kStages * STAGE_BYTES);
+    PCtl &ctl = *reinterpret_cast<PCtl *>(base + kStages * STAGE_BYTES + kEpiWarps * 32 * kStagePitch * 4);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t s_stages = smem_u32(stages);
+    volatile int *fail = &ctl.fail;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&ctl.full[s]), 1);
+            mbar_init(smem_u32(&ctl.empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&ctl.tfull[a]), 1);
+            mbar_init(smem_u32(&ctl.tempty[a]), kEpiWarps);
+        }
+        ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&ctl.tmem)),
+                     "r"(kAccCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl.tmem;
+    const int nchunks = (d + KC - 1) / KC;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            TileWalk<MAP> walk(gx, total, nb);
+            int X, Y;
+            uint32_t it = 0;
+            while (!*fail && walk.next(X, Y)) {
+                for (int c = 0; c < nchunks; ++c, ++it) {
+                    const int s = (int)(it % kStages);
+                    const uint32_t ph = (it / kStages) & 1;
+                    if (!mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail)) break;
+                    const uint32_t bar = smem_u32(&ctl.full[s]);
+                    const uint32_t dst = s_stages + s * STAGE_BYTES;
+                    mbar_expect_tx(bar, STAGE_BYTES);
+                    tma_load_2d(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar);
+                    tma_load_2d(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar);
+                    tma_load_2d(dst + 2 * TILE_BYTES, &map_hi, c * KC, X * TN, bar);
+                    tma_load_2d(dst + 3 * TILE_BYTES, &map_lo, c * KC, X * TN, bar);
+                }
+            }
+            // a failed block waits (bounded) for its loads in flight
+            if (*fail && it > 0) {
+                const uint32_t last = it - 1;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(smem_u32(&ctl.full[last % kStages]), (last / kStages) & 1) &&
+                       clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            TileWalk<MAP> walk(gx, total, nb);
+            int X, Y;
+            uint32_t it = 0, tt = 0;
+            while (!*fail && walk.next(X, Y)) {
+                const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
+                if (!mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail)) break;
+                tc_fence_after();
+                const uint32_t dtm = tmem + acc * TN;
+                for (int c = 0; c < nchunks; ++c, ++it) {
+                    const int s = (int)(it % kStages);
+                    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail)) break;
+                    tc_fence_after();
+                    const uint32_t src = s_stages + s * STAGE_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint32_t koff = ks * 32;
+                        const uint64_t ah = sw128_desc(src + 0 * TILE_BYTES + koff);
+                        const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
+                        const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
+                        const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
+                        mma_bf16(dtm, ah, bh, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16(dtm, ah, bl, 1u);
+                        mma_bf16(dtm, al, bh, 1u);
+                    }
+                    mma_commit(smem_u32(&ctl.empty[s]));
+                }
+                mma_commit(smem_u32(&ctl.tfull[acc]));
+                ++tt;
+            }
+        }
+    } else {
+        // ---------------- epilogue: 8 warps, two per TMEM lane quarter
+        const int ew = warp - 2;                 // 0..7
+        const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+        const int half = ew >> 2;                // columns [64*half, 64*half + 64)
+        const int r = 32 * quarter + lane;       // this thread's row in the tile
+        float *stg = stg_all + ew * 32 * kStagePitch;
+        TileWalk<MAP> walk(gx, total, nb);
+        int X, Y;
+        uint32_t tt = 0;
+        while (!*fail && walk.next(X, Y)) {
+            const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
+            const int64_t row0 = (int64_t)Y * TM, col0 = (int64_t)X * TN;
+            // this warp's 64 column norms (its own buffer: no cross-warp sync)
+            float *nc = &ctl.ncol[ew][0];
+            {
+                const int64_t j0 = col0 + 64 * half + lane, j1 = j0 + 32;
+                const float a = j0 < n ? __ldg(nrm + j0) : 0.0f;
+                const float b = j1 < n ? __ldg(nrm + j1) : 0.0f;
+                __syncwarp();   // the previous tile's reads of nc are done
+                nc[lane] = a;
+                nc[lane + 32] = b;
+            }
+            const int64_t i = row0 + r;
+            const float ni = i < n ? __ldg(nrm + i) : 0.0f;
+            const bool diag = (X == Y);
+            // packed index of this row's first column in this warp's half
+            const int64_t gbase = i * (i + 1) / 2 + col0 + 64 * half;
+            // floats from the row start back to the previous 16-byte boundary of out
+            const int shift = (int)((reinterpret_cast<uintptr_t>(out + gbase) >> 2) & 3);
+            float *myrow = stg + lane * kStagePitch + shift;
+            __syncwarp();
+            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail)) break;
+            tc_fence_after();
+            float v0[32], v1[32];
+            const uint32_t taddr = tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * half);
+            tmem_ld32(taddr, v0);
+            tmem_ld32(taddr + 32, v1);
+            // the accumulator is read: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            // D = |x_i|^2 + |x_j|^2 - 2 g; flag entries with D < (|x_i|^2 + |x_j|^2)/64
+            float low = 1.0f;
+#pragma unroll
+            for (int q = 0; q < 32; q += 4) {
+                const float4 a = *reinterpret_cast<const float4 *>(nc + q);
+                const float4 b = *reinterpret_cast<const float4 *>(nc + 32 + q);
+                float sa[4] = {ni + a.x, ni + a.y, ni + a.z, ni + a.w};
+                float sb[4] = {ni + b.x, ni + b.y, ni + b.z, ni + b.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    v0[q + k] = fmaf(-2.0f, v0[q + k], sa[k]);
+                    v1[q + k] = fmaf(-2.0f, v1[q + k], sb[k]);
+                    low = fminf(low, fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
+                                           fmaf(-0.015625f, sb[k], v1[q + k])));
+                }
+            }
+            if (__any_sync(0xffffffffu, low < 0.0f)) {
+#pragma unroll
+                for (int q = 0; q < 64; ++q) {
+                    float &vq = q < 32 ? v0[q] : v1[q - 32];
+                    const int64_t j = col0 + 64 * half + q;
+                    const float sj = ni + nc[q];
+                    if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
+                }
+            }
+            bulk_wait_read();   // the previous tile's copy has left this staging row
+#pragma unroll
+            for (int q = 0; q < 32; ++q) { myrow[q] = v0[q]; myrow[32 + q] = v1[q]; }
+            if (!diag) {
+                // Each lane writes its own 64-float row segment: the 16-byte-
+                // aligned body by one bulk copy, the ragged head and tail (at
+                // most 3 floats each) by plain stores.
+                if (i < n) {
+                    const int h = (4 - shift) & 3;
+                    const int body = (64 - h) & ~3;
+                    fence_proxy_async();
+                    bulk_store(out + gbase + h, smem_u32(myrow + h), (uint32_t)body * 4);
+                    bulk_commit();
+                    for (int e = 0; e < h; ++e) out[gbase + e] = myrow[e];
+                    for (int e = h + body; e < 64; ++e) out[gbase + e] = myrow[e];
+                }
+            } else if (i < n && 64 * half <= r) {
+                // diagonal tile: columns j <= i only, plain stores
+                const int rc = r - 64 * half;             // diagonal column, local
+                const int last = rc < 63 ? rc : 63;
+                if (rc <= 63) myrow[rc] = 0.0f;           // D_ii = 0 exactly
+                for (int e = 0; e <= last; ++e) out[gbase + e] = myrow[e];
+            }
+            ++tt;
+        }
+    }
+    bulk_wait_all();   // staging rows must stay valid until the copies have read them
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kAccCols)
+                     : "memory");
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the CUDA runtime).
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+    static std::once_flag once;
+    static EncodeTiled fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// n x d BF16 row-major, boxes of 128 rows x 64 columns, 128-byte swizzle,
+// zero fill outside the matrix.
+static bool make_map(CUtensorMap *m, void *ptr, int64_t n, int d) {
+    EncodeTiled f = encode_fn();
+    if (!f) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)TM};
+    const cuuint32_t estr[2] = {1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+static int smem_optin() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    static std::mutex mu;
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM_BYTES)) != cudaSuccess)
+            return cuda_status(e);
+        done[dev] = true;
+    }
+    return SIMPLEX_OK;
+}
+
+}  // namespace umma
+
+// BF16 hi and lo copies (1024-byte aligned for the tensor maps) and the FP32
+// norms, plus slack to align the caller's (256-byte aligned) workspace.
+int64_t edm_umma_workspace_bytes(int64_t n, int64_t d) {
+    return 1024 + 2 * umma::align_up(n * d * 2, 1024) + umma::align_up(n * 4, 1024);
+}
+
+int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void *ws,
+                 int64_t ws_bytes, cudaStream_t s) {
+    using namespace umma;
+    if (d % KC != 0) return SIMPLEX_EUNSUPPORTED;
+    if (!ws || ws_bytes < edm_umma_workspace_bytes(n, d) || !aligned(ws, 256))
+        return SIMPLEX_EWORKSPACE;
+    const int64_t nb = (n + TM - 1) / TM;
+    const Grid g = grid2(nb, map);
+    if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
+    unsigned char *w = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    __nv_bfloat16 *xh = reinterpret_cast<__nv_bfloat16 *>(w);
+    __nv_bfloat16 *xl = reinterpret_cast<__nv_bfloat16 *>(w + align_up(n * d * 2, 1024));
+    float *nrm = reinterpret_cast<float *>(w + 2 * align_up(n * d * 2, 1024));
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, xh, n, (int)d) || !make_map(&ml, xl, n, (int)d)) return SIMPLEX_ECUDA;
+    int st = smem_optin();
+    if (st) return st;
+    k_split_bf16<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(x, n, (int)d, xh, xl, nrm);
+    note_launches(1);
+    if ((st = launch_status())) return st;
+    // persistent grid: one CTA per SM walks the map's grid with stride gridDim.x
+    int dev = 0, sms = 0;
+    if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
+    if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
+    const int64_t total = g.gx * g.gy;
+    const unsigned ctas = (unsigned)(total < sms ? total : sms);
+    prof_begin(s);
+    if (map == MAP_LAMBDA)
+        k_edm_umma<MAP_LAMBDA><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)g.gx, total);
+    else if (map == MAP_BBOX)
+        k_edm_umma<MAP_BBOX><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)g.gx, total);
+    else
+        k_edm_umma<MAP_LINEAR><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)g.gx, total);
+    prof_end(s);
+    note_launches(1);
+    return launch_status();
+}
+
+int umma_device_errors(cudaStream_t s) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    if ((e = cudaMemcpyFromSymbol(&h, umma::g_error, sizeof(int))) != cudaSuccess) return cuda_status(e);
+    if (h) {
+        const int zero = 0;
+        if ((e = cudaMemcpyToSymbol(umma::g_error, &zero, sizeof(int))) != cudaSuccess)
+            return cuda_status(e);
+        return SIMPLEX_ETIMEOUT;
+    }
+    return SIMPLEX_OK;
+}
+
+}  // namespace sx
+
+extern "C" int simplex_device_errors(void *stream) {
+    return sx::umma_device_errors((cudaStream_t)stream);
+}

@@ -3,6 +3,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 namespace sx {
 
 constexpr int kEdmRho = 32;      // SIMT EDM tile: 32 x 32 pairs, 256 threads
@@ -11,5 +13,11 @@ constexpr int kStressRho = 32;   // stress tile: 32 x 32 pairs, 256 threads
 
 int edm_rho(int64_t d, int prec);
 int64_t edm_workspace_bytes(int64_t n, int64_t d, int map, int prec);
+
+// Tensor-core EDM (edm_umma.cu): tiles of 128 x 128 pairs, d % 64 == 0.
+constexpr int kEdmUmmaRho = 128;
+int64_t edm_umma_workspace_bytes(int64_t n, int64_t d);
+int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void *ws,
+                 int64_t ws_bytes, cudaStream_t s);
 
 }  // namespace sx

@@ -81,3 +81,68 @@ def test_edm_maps_agree_bitwise(gpu):
     a = gpu.edm_packed(x, "lambda")
     assert torch.equal(a, gpu.edm_packed(x, "bbox"))
     assert torch.equal(a, gpu.edm_packed(x, "linear"))
+
+
+# ---------------------------------------------------------------- tensor cores
+
+BF_TOL = 1e-5
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("n,d", [(1, 64), (128, 64), (129, 64), (200, 128), (300, 256), (1000, 64),
+                                 (700, 192)])
+def test_edm_bf16x3_small(gpu, oracle, mp, n, d):
+    """Gram term on tensor cores (BF16 hi+lo split, FP32 accumulation),
+    every entry against the FP64 oracle."""
+    x = synth.normal(n, d, seed=600 + n + d)
+    out = gpu.edm_packed(to_gpu(x), mp, "bf16x3")
+    gpu.simplex_device_errors()
+    out = out.cpu().numpy()
+    ref = oracle.edm_packed(x)
+    i = np.arange(n)
+    assert (out[packed_index(i, i)] == 0).all()
+    off = ref > 0
+    if off.any():
+        assert rel_err(out[off], ref[off]).max() <= BF_TOL
+
+
+def test_edm_bf16x3_near_duplicates(gpu, oracle):
+    """Points that nearly coincide make the Gram form cancel; those entries
+    are recomputed in FP32 and still meet the tolerance."""
+    base = synth.normal(150, 64, seed=31)
+    x = np.concatenate([base, base + 1e-3 * synth.normal(150, 64, seed=32)]).astype(np.float32)
+    out = gpu.edm_packed(to_gpu(x), "lambda", "bf16x3")
+    gpu.simplex_device_errors()
+    out = out.cpu().numpy()
+    ref = oracle.edm_packed(x)
+    off = ref > 0
+    assert rel_err(out[off], ref[off]).max() <= BF_TOL
+
+
+def test_edm_bf16x3_precision_config(gpu, oracle):
+    """n = 32768, d = 256, N(0,1) seed 2 (536,887,296 entries): sampled pairs
+    plus two whole diagonal tiles against the FP64 oracle."""
+    x = synth.make_points("edm_n32768_d256")
+    out = gpu.edm_packed(to_gpu(x), "lambda", "bf16x3")
+    gpu.simplex_device_errors()
+    assert sampled_check(out, x, oracle, seed=21, nb_rho=128) <= BF_TOL
+
+
+def test_edm_bf16x3_scale_config(gpu, oracle):
+    """n = 65536, d = 64 (2,147,516,416 entries) with the library's choice
+    (AUTO selects the tensor-core path for d = 64)."""
+    w = synth.WORKLOADS["stress_n65536_d64"]
+    x = synth.normal(w["n"], w["d"], w["seed"])
+    out = gpu.edm_packed(to_gpu(x), "lambda", "auto")
+    gpu.simplex_device_errors()
+    assert sampled_check(out, x, oracle, seed=22, nb_rho=128) <= BF_TOL
+    del out
+    torch.cuda.empty_cache()
+
+
+def test_edm_bf16x3_maps_agree(gpu):
+    x = to_gpu(synth.normal(1500, 128, seed=33))
+    a = gpu.edm_packed(x, "lambda", "bf16x3")
+    assert torch.equal(a, gpu.edm_packed(x, "bbox", "bf16x3"))
+    assert torch.equal(a, gpu.edm_packed(x, "linear", "bf16x3"))
+    gpu.simplex_device_errors()
