@@ -496,3 +496,27 @@ def test_synth_recipes():
     g = synth.normal(4096, 4, seed=2).astype(np.float64)
     assert abs(g.mean()) < 0.02 and abs(g.std() - 1) < 0.02
     assert len(set(synth.sample_indices(64, 4096, seed=3).tolist())) == 64
+
+
+def test_stress_moment_identity(oracle):
+    """Squared distances are quadratic in the coordinates, so the stress loss
+    and its gradient have closed forms over moment matrices: with S = x + y,
+    Delta = x - y, a_i = S_i . Delta_i and r_ij = a_i + a_j - S_i.Delta_j -
+    Delta_i.S_j,  sum_j r_ij = n a_i + sum a - S_i.sum(Delta) - Delta_i.sum(S)
+    and sum_j r_ij x_j = a_i sum(x) + a^T x - S_i (Delta^T x) - Delta_i (S^T x);
+    L = (1/2) sum_ij r_ij^2 expands the same way.  None of this is the
+    oracle's pairwise loop."""
+    x = synth.normal(70, 5, seed=51).astype(np.float64)
+    y = synth.perturbed(x.astype(np.float32), 0.2, seed=52).astype(np.float64)
+    n = len(x)
+    S, De = x + y, x - y
+    a = (S * De).sum(1)
+    rs = n * a + a.sum() - S @ De.sum(0) - De @ S.sum(0)
+    rx = np.outer(a, x.sum(0)) + a @ x - S @ (De.T @ x) - De @ (S.T @ x)
+    grad = 4 * (x * rs[:, None] - rx)
+    assert np.allclose(oracle.stress_grad_rows(x, y, range(n)), grad, rtol=1e-9, atol=1e-9 * np.abs(grad).max())
+    # L via the Gram matrices of the stacked factors U = [a, 1, S, Delta], V = [1, a, -Delta, -S]
+    U = np.hstack([a[:, None], np.ones((n, 1)), S, De])
+    V = np.hstack([np.ones((n, 1)), a[:, None], -De, -S])
+    L = 0.5 * np.sum((U.T @ U) * (V.T @ V))   # sum_ij (U_i . V_j)^2
+    assert oracle.stress_loss(x, y) == pytest.approx(L, rel=1e-10)
