@@ -49,6 +49,11 @@ FLOPS_PER_TRIPLE = 22
 ROWS_NAMES = ("edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
               "stress_n65536_d64", "edm_n16384_d64")
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one k_atm_energy<lambda> launch on this
+# workload, from the ncu capture summarised in
+# profiles/k_atm_energy_lambda_n1024.md (set to None whenever the kernel
+# changes and the capture has not been repeated).
+ENERGY_KERNEL_DRAM_BYTES = 1.55008e6
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -232,6 +237,11 @@ def _kernel_ms(torch, sx, fn, steps=3, warmup=1):
     return ms / max(k, 1)
 
 
+def _fp32_peak(torch):
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+
+
 def row_edm_n1024_d3(torch, sx, peaks):
     """EDM n=1024, d=3: 524,800 FP32 outputs (2.1 MB); one launch is a few
     microseconds, so a step is a batch of 100 launches."""
@@ -325,6 +335,7 @@ def row_atm_n16384(torch, sx, peaks):
     f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, "lambda", ws), 1, 0)
     r["energy_forces_lambda"] = triples(n) / (ms / 1e3)
+    r["energy_fp32_frac"] = FLOPS_PER_TRIPLE * r["energy_lambda"] / 1e12 / _fp32_peak(torch)
     return r
 
 
@@ -345,6 +356,14 @@ def row_stress_n65536_d64(torch, sx, peaks):
     g = torch.empty_like(x)
     ms = _median_ms(torch, lambda: sx.simplex_stress_bwd(x, y, 1.0, g, "lambda", "fp32"), 2)
     r["bwd_lambda"] = pairs / (ms / 1e3)
+    # algorithmic FP32 flops per pair: forward 4d (two FMAs per coordinate),
+    # backward 8d (the residual plus the two tile products)
+    d = w["d"]
+    fp32 = _fp32_peak(torch)
+    r["fwd_tflops"] = 4 * d * r["fwd_lambda"] / 1e12
+    r["bwd_tflops"] = 8 * d * r["bwd_lambda"] / 1e12
+    r["fwd_fp32_frac"] = r["fwd_tflops"] / fp32
+    r["bwd_fp32_frac"] = r["bwd_tflops"] / fp32
     return r
 
 
@@ -477,7 +496,8 @@ def our_arm(args):
         "data": "synthetic", "config": config_block(),
         "maps": maps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": ENERGY_KERNEL_DRAM_BYTES,
+                     "algorithmic_bytes": 12 * n + 8 * 6656,
                      "kernel": "k_atm_energy<lambda>", "kernel_ms": k_ms,
                      "flops_per_triple": FLOPS_PER_TRIPLE,
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
