@@ -151,6 +151,20 @@ def triples(n):
     return n * (n - 1) * (n - 2) // 6
 
 
+def job_rate(ms_local: float, units_per_rank: int, world: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processes
+    `units_per_rank`; the job's step time is the slowest rank's (MAX
+    all-reduce, the only collective; it carries a timing, not data).
+    Returns (units per second for the job, job step ms)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 # ------------------------------------------------------------------ oracle arm
 
 def oracle_energy_rate(x, seconds_min=10.0, i_hi=None):
@@ -447,12 +461,7 @@ def our_arm(args):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms_step = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = t.item()
-    value = world * units / (ms_step / 1e3)
+    value, ms_step = job_rate(sum(times) / len(times), units, world, dist, "cuda")
     k_ms = main_ms / max(main_k, 1)
     achieved = FLOPS_PER_TRIPLE * units / (k_ms / 1e3) / 1e12
 
@@ -476,12 +485,8 @@ def our_arm(args):
         ep.copy_(e, non_blocking=True)
 
     te = time_steps(torch, e2e_step, args.steps, 3, flush)
-    e2e_ms = sum(te) / len(te)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
-    e2e = {"value": world * units / (e2e_ms / 1e3), "unit": "triplets/s",
+    e2e_value, e2e_ms = job_rate(sum(te) / len(te), units, world, dist, "cuda")
+    e2e = {"value": e2e_value, "unit": "triplets/s",
            "h2d_bytes_per_step": int(xp.numel() * xp.element_size()),
            "d2h_bytes_per_step": int(ep.numel() * ep.element_size())}
 
