@@ -34,12 +34,6 @@ namespace sx {
 
 constexpr int R_ = kAtmRho;  // 32
 
-struct AtmTables {
-    float4 xs[3][R_];        // tiles I, J, K: (x, y, z, 0)
-    float4 tb[R_][2][16];    // [k][q][t]: (u_jk, r_jk^3 or r_jk) of pair (j = t + 16q, k)
-    float4 tc[R_][2][16];    // [k][p][t]: (u_ik, r_ik^3 or r_ik) of pair (i = t + 16p, k)
-};
-
 // Loads the three point tiles (zero past n).
 __device__ __forceinline__ void load_tiles(const float *__restrict__ x, int64_t n, int I, int J,
                                            int K, float4 (*xs)[R_]) {
@@ -54,52 +48,21 @@ __device__ __forceinline__ void load_tiles(const float *__restrict__ x, int64_t 
     }
 }
 
-// Pair terms.  CUBE selects r^3 (energy) or r (forces) in the w slot.
+// Pair terms: (u, r^3) of the edge from -> to, zero outside the simplex.
 __device__ __forceinline__ float4 edge(float4 from, float4 to) {
     return make_float4(to.x - from.x, to.y - from.y, to.z - from.z, 0.0f);
 }
 
-template <bool CUBE>
 __device__ __forceinline__ float4 pair_term(float4 from, float4 to, bool valid, float eps) {
     const float4 e = edge(from, to);
     if (!valid) return make_float4(0.f, 0.f, 0.f, 0.f);
     const float s = fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps)));
     const float q = sqrtf(s);
     const float r = 1.0f / q;
-    return make_float4(e.x * r, e.y * r, e.z * r, CUBE ? 1.0f / (s * q) : r);
-}
-
-template <bool CUBE>
-__device__ __forceinline__ void build_tables(int64_t n, int I, int J, int K, float eps,
-                                             AtmTables &T) {
-    for (int e = threadIdx.x; e < R_ * R_; e += 256) {
-        const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
-        const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
-        T.tb[k][half][t] = pair_term<CUBE>(T.xs[1][o], T.xs[2][k], gj < gk && gk < n, eps);
-        T.tc[k][half][t] = pair_term<CUBE>(T.xs[0][o], T.xs[2][k], gi < gk && gk < n, eps);
-    }
-}
-
-struct PairConst {
-    float4 u;    // u_ij, w = r_ij^3 (energy) or r_ij (forces); 0 outside i < j < n
-    float3 f;    // -3 u_ij
-};
-
-template <bool CUBE>
-__device__ __forceinline__ PairConst pair_const(int64_t n, int I, int J, int i, int j, float eps,
-                                                const AtmTables &T) {
-    PairConst c;
-    const int64_t gi = (int64_t)I * R_ + i, gj = (int64_t)J * R_ + j;
-    c.u = pair_term<CUBE>(T.xs[0][i], T.xs[1][j], gi < gj && gj < n, eps);
-    c.f = make_float3(-3.0f * c.u.x, -3.0f * c.u.y, -3.0f * c.u.z);
-    return c;
+    return make_float4(e.x * r, e.y * r, e.z * r, 1.0f / (s * q));
 }
 
 __device__ __forceinline__ float dot3(float4 a, float4 b) {
-    return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
-}
-
-__device__ __forceinline__ float dot3(float3 a, float4 b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
 }
 
@@ -126,9 +89,9 @@ __device__ __forceinline__ void build_energy_tables(int64_t n, int I, int J, int
     for (int e = threadIdx.x; e < R_ * R_; e += 256) {
         const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
         const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
-        const float4 c = pair_term<true>(S.xs[0][o], S.xs[2][k], gi < gk && gk < n, eps);
+        const float4 c = pair_term(S.xs[0][o], S.xs[2][k], gi < gk && gk < n, eps);
         put_pair(S.ec[k][0][t], S.ec[k][1][t], half, c);
-        const float4 b = pair_term<true>(S.xs[1][o], S.xs[2][k], gj < gk && gk < n, eps);
+        const float4 b = pair_term(S.xs[1][o], S.xs[2][k], gj < gk && gk < n, eps);
         S.eb[k][half][0][t] = make_float4(b.x, b.x, b.y, b.y);
         S.eb[k][half][1][t] = make_float4(b.z, b.z, b.w, b.w);
     }
@@ -185,9 +148,9 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int64_t gj = (int64_t)J * R_ + tj + 16 * q;
-            const float4 u0 = pair_term<true>(S.xs[0][ti], S.xs[1][tj + 16 * q],
+            const float4 u0 = pair_term(S.xs[0][ti], S.xs[1][tj + 16 * q],
                                               (int64_t)I * R_ + ti < gj && gj < n, eps);
-            const float4 u1 = pair_term<true>(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
+            const float4 u1 = pair_term(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
                                               (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
             uij[q][0] = make_float2(u0.x, u1.x);
             uij[q][1] = make_float2(u0.y, u1.y);
@@ -219,19 +182,67 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
 
 // ---------------------------------------------------------------- forces
 
+// Force tables, laid out like the energy tables for packed FP32x2 arithmetic
+// over the thread's two i-slots p (lanes x, y):
+//   fc[k][0][ti] = (u_ik0.x, u_ik1.x, u_ik0.y, u_ik1.y)
+//   fc[k][1][ti] = (u_ik0.z, u_ik1.z, r_ik0,   r_ik1)
+//   fc[k][2][ti] = (r_ik0^3, r_ik1^3, r_ik0^2, r_ik1^2)
+//   fb[k][q][0..2][tj] = the same three vectors of pair (j = tj + 16q, k),
+//   each value duplicated into both lanes (one broadcast load feeds both).
 struct AtmForceSmem {
-    AtmTables T;
-    float tb3[R_][2][16];    // r_jk^3 of the pairs of T.tb
-    float tc3[R_][2][16];    // r_ik^3 of the pairs of T.tc
+    float4 xs[3][R_];
+    float4 fc[R_][3][16];
+    float4 fb[R_][2][3][16];
     float wjk[R_][R_ + 1];   // [k][j]: sum over i of de/db
     float wik[R_][R_ + 1];   // [k][i]: sum over j of de/dc
     float wij[R_][R_ + 1];   // [i][j]: sum over k of de/da
 };
 
-// One triple: energy into acc and the derivatives of e (without nu) with
-// respect to the squared sides a = |e_ij|^2, b = |e_jk|^2, c = |e_ik|^2.
-// From e = R^3 (1 + 3 D R^2) with D = d_i d_j d_k (vertex dot products,
-// 2 d_i = a + c - b, 2 d_j = a + b - c, 2 d_k = b + c - a) and R^2 = 1/P:
+// (u, r, r^3, r^2) of a pair: r = 1/sqrt(s), r^3 = 1/(s sqrt(s)), all zero
+// outside the simplex.
+struct PairTerms {
+    float ux, uy, uz, r, r3, r2;
+};
+
+__device__ __forceinline__ PairTerms pair_terms(float4 from, float4 to, bool valid, float eps) {
+    PairTerms t;
+    if (!valid) { t.ux = t.uy = t.uz = t.r = t.r3 = t.r2 = 0.0f; return t; }
+    const float4 e = edge(from, to);
+    const float s = fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps)));
+    const float q = sqrtf(s);
+    t.r = 1.0f / q;
+    t.r3 = 1.0f / (s * q);
+    t.r2 = t.r * t.r;
+    t.ux = e.x * t.r; t.uy = e.y * t.r; t.uz = e.z * t.r;
+    return t;
+}
+
+__device__ __forceinline__ void build_force_tables(int64_t n, int I, int J, int K, float eps,
+                                                   AtmForceSmem &S) {
+    for (int e = threadIdx.x; e < R_ * R_; e += 256) {
+        const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
+        const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
+        const PairTerms c = pair_terms(S.xs[0][o], S.xs[2][k], gi < gk && gk < n, eps);
+        put_pair(S.fc[k][0][t], S.fc[k][1][t], half, make_float4(c.ux, c.uy, c.uz, c.r));
+        float *f2 = reinterpret_cast<float *>(&S.fc[k][2][t]);
+        f2[half] = c.r3; f2[2 + half] = c.r2;
+        const PairTerms b = pair_terms(S.xs[1][o], S.xs[2][k], gj < gk && gk < n, eps);
+        S.fb[k][half][0][t] = make_float4(b.ux, b.ux, b.uy, b.uy);
+        S.fb[k][half][1][t] = make_float4(b.uz, b.uz, b.r, b.r);
+        S.fb[k][half][2][t] = make_float4(b.r3, b.r3, b.r2, b.r2);
+    }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Two triples (i0, j, k), (i1, j, k) in the two lanes.  Energy term into acc
+// and the derivatives of e (without nu) with respect to the squared sides
+// a = |e_ij|^2, b = |e_jk|^2, c = |e_ik|^2.  From e = R^3 (1 + 3 D R^2) with
+// D = d_i d_j d_k (vertex dot products, 2 d_i = a + c - b, 2 d_j = a + b - c,
+// 2 d_k = b + c - a) and R^2 = 1/P:
 //   de/da = R^3 (3 R^2 dD/da - 1.5 (1 + 5 D R^2) r_a^2),
 //   dD/da = (d_j d_k + d_i d_k - d_i d_j)/2, and likewise for b, c.
 // In cosines (Cp = cos_i cos_j cos_k = D R^2, d_j d_k R^2 = cos_j cos_k r_a r_c,
@@ -239,46 +250,66 @@ struct AtmForceSmem {
 //   de/da = 1.5 R^3 (X + Y - Z - H r_a^2),  de/db = 1.5 R^3 (Y + Z - X - H r_b^2),
 //   de/dc = 1.5 R^3 (X + Z - Y - H r_c^2),
 // with X = cos_j cos_k r_a r_c, Y = cos_i cos_k r_a r_b, Z = cos_i cos_j r_b r_c,
-// H = 1 + 5 Cp.  B = (u_jk, r_jk), C = (u_ik, r_ik); R^3 is the product of the
-// three pairs' r^3 = 1/(s sqrt(s)), as in the energy kernel.
-__device__ __forceinline__ void triple_grad(float4 B, float4 C, float rb3, float rc3,
-                                            const PairConst &c, float ra3, float &acc, float &ea,
-                                            float &eb, float &ec) {
-    const float ra = c.u.w, rb = B.w, rc = C.w;
-    const float ci = dot3(c.u, C);
-    const float cj = -dot3(c.u, B);
-    const float ck = dot3(C, B);
-    const float cjk = cj * ck, cik = ci * ck, cij = ci * cj;
-    const float Cp = ci * cjk;
-    const float rab = ra * rb;
-    const float X = cjk * (ra * rc), Y = cik * rab, Z = cij * (rb * rc);
-    const float R3 = (ra3 * rc3) * rb3;
-    acc = fmaf(R3, fmaf(3.0f, Cp, 1.0f), acc);
-    const float H = fmaf(5.0f, Cp, 1.0f);
-    const float h = 1.5f * R3;
-    const float S = X + Y + Z;
-    ea = h * fmaf(-H, ra * ra, fmaf(-2.0f, Z, S));
-    eb = h * fmaf(-H, rb * rb, fmaf(-2.0f, X, S));
-    ec = h * fmaf(-H, rc * rc, fmaf(-2.0f, Y, S));
+// H = 1 + 5 Cp, and R^3 the product of the pairs' r^3.  Here cos_j enters
+// negated (cjn = u_ij . u_jk = -cos_j).  36 packed operations.
+struct PairPack {
+    float2 ux, uy, uz;     // u_ij of the two i-slots
+    float2 ra, ra2, ra3;
+};
+
+__device__ __forceinline__ void triple_grad2(const PairPack &c, float4 C0, float4 C1, float4 C2,
+                                             float4 B0, float4 B1, float4 B2, float2 &acc,
+                                             float2 &ea, float2 &eb, float2 &ec) {
+    const float2 cx = f2(C0.x, C0.y), cy = f2(C0.z, C0.w), cz = f2(C1.x, C1.y), rc = f2(C1.z, C1.w);
+    const float2 rc3 = f2(C2.x, C2.y), rc2 = f2(C2.z, C2.w);
+    const float2 bx = f2(B0.x, B0.y), by = f2(B0.z, B0.w), bz = f2(B1.x, B1.y), rb = f2(B1.z, B1.w);
+    const float2 rb3 = f2(B2.x, B2.y), rb2 = f2(B2.z, B2.w);
+    const float2 ci = fma2(c.ux, cx, fma2(c.uy, cy, mul2(c.uz, cz)));
+    const float2 cjn = fma2(c.ux, bx, fma2(c.uy, by, mul2(c.uz, bz)));
+    const float2 ck = fma2(cx, bx, fma2(cy, by, mul2(cz, bz)));
+    const float2 p1 = mul2(cjn, ck);            // -cos_j cos_k
+    const float2 p2 = mul2(ci, cjn);            // -cos_i cos_j
+    const float2 cik = mul2(ci, ck);            //  cos_i cos_k
+    const float2 cpn = mul2(ci, p1);            // -Cp
+    const float2 xn = mul2(p1, mul2(c.ra, rc)); // -X
+    const float2 zn = mul2(p2, mul2(rb, rc));   // -Z
+    const float2 y = mul2(cik, mul2(c.ra, rb)); //  Y
+    const float2 R3 = mul2(mul2(c.ra3, rc3), rb3);
+    acc = fma2(R3, fma2(f2(-3.0f, -3.0f), cpn, f2(1.0f, 1.0f)), acc);
+    const float2 H = fma2(f2(-5.0f, -5.0f), cpn, f2(1.0f, 1.0f));
+    const float2 h = mul2(f2(1.5f, 1.5f), R3);
+    const float2 S = add2(y, f2(-(xn.x + zn.x), -(xn.y + zn.y)));
+    const float2 nH = f2(-H.x, -H.y);
+    ea = mul2(h, fma2(nH, c.ra2, fma2(f2(2.0f, 2.0f), zn, S)));
+    eb = mul2(h, fma2(nH, rb2, fma2(f2(2.0f, 2.0f), xn, S)));
+    ec = mul2(h, fma2(nH, rc2, fma2(f2(-2.0f, -2.0f), y, S)));
 }
 
-// r^3 of every table pair, 1/(s sqrt(s)) from the stored unit vector's s.
-__device__ __forceinline__ float cube_r(float4 from, float4 to, bool valid, float eps) {
-    if (!valid) return 0.0f;
-    const float4 e = edge(from, to);
-    const float s = fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps)));
-    return 1.0f / (s * sqrtf(s));
+// Sum over the 16 lanes of a half-warp (xor 8, 4, 2, 1) of 16 values per
+// lane, scattered: lane l ends with the total of value l & 15.  30 shuffles
+// and adds instead of 16 full reductions.
+__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int m = 0; m < w; ++m) {
+            const float send = up ? v[m] : v[m + w];
+            const float keep = up ? v[m + w] : v[m];
+            v[m] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+    }
+    return v[0];
 }
 
 template <int MAP>
-__global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__restrict__ x,
-                                                    float nu, float eps, int nb, int p,
-                                                    double *__restrict__ partials,
-                                                    double *__restrict__ forces) {
+__global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *__restrict__ x,
+                                                       float nu, float eps, int nb, int p,
+                                                       double *__restrict__ partials,
+                                                       double *__restrict__ forces) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AtmForceSmem &S = *reinterpret_cast<AtmForceSmem *>(smem_raw);
     __shared__ float red[16];
-    AtmTables &T = S.T;
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
     const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4, lane = tid & 31;
     float hi = 0.f, lo = 0.f;
@@ -287,77 +318,87 @@ __global__ void __launch_bounds__(256) k_atm_forces(int64_t n, const float *__re
         int I, J, K;
         block_of(L, t, I, J, K);
         if (t) __syncthreads();
-        load_tiles(x, n, I, J, K, T.xs);
+        load_tiles(x, n, I, J, K, S.xs);
         for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
         __syncthreads();
-        build_tables<false>(n, I, J, K, eps, T);
-        for (int e = tid; e < R_ * R_; e += 256) {
-            const int k = e >> 5, o = e & 31, half = o >> 4, tt = o & 15;
-            const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
-            S.tb3[k][half][tt] = cube_r(T.xs[1][o], T.xs[2][k], gj < gk && gk < n, eps);
-            S.tc3[k][half][tt] = cube_r(T.xs[0][o], T.xs[2][k], gi < gk && gk < n, eps);
+        build_force_tables(n, I, J, K, eps, S);
+        PairPack pc[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int64_t gj = (int64_t)J * R_ + tj + 16 * q;
+            const PairTerms a0 = pair_terms(S.xs[0][ti], S.xs[1][tj + 16 * q],
+                                            (int64_t)I * R_ + ti < gj && gj < n, eps);
+            const PairTerms a1 = pair_terms(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
+                                            (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
+            pc[q].ux = f2(a0.ux, a1.ux); pc[q].uy = f2(a0.uy, a1.uy); pc[q].uz = f2(a0.uz, a1.uz);
+            pc[q].ra = f2(a0.r, a1.r); pc[q].ra2 = f2(a0.r2, a1.r2); pc[q].ra3 = f2(a0.r3, a1.r3);
         }
-        PairConst pc[2][2];
-        float ra3[2][2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                pc[a][b] = pair_const<false>(n, I, J, ti + 16 * a, tj + 16 * b, eps, T);
-                const int64_t gi = (int64_t)I * R_ + ti + 16 * a, gj = (int64_t)J * R_ + tj + 16 * b;
-                ra3[a][b] = cube_r(T.xs[0][ti + 16 * a], T.xs[1][tj + 16 * b], gi < gj && gj < n, eps);
-            }
         __syncthreads();
-        float acc = 0.0f;
-        float wa[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
-        for (int k = 0; k < R_; ++k) {
-            const float4 B0 = T.tb[k][0][tj], B1 = T.tb[k][1][tj];
-            const float4 C0 = T.tc[k][0][ti], C1 = T.tc[k][1][ti];
-            const float b30 = S.tb3[k][0][tj], b31 = S.tb3[k][1][tj];
-            const float c30 = S.tc3[k][0][ti], c31 = S.tc3[k][1][ti];
-            float ea, eb[2][2], ec[2][2];
-            triple_grad(B0, C0, b30, c30, pc[0][0], ra3[0][0], acc, ea, eb[0][0], ec[0][0]); wa[0][0] += ea;
-            triple_grad(B1, C0, b31, c30, pc[0][1], ra3[0][1], acc, ea, eb[0][1], ec[0][1]); wa[0][1] += ea;
-            triple_grad(B0, C1, b30, c31, pc[1][0], ra3[1][0], acc, ea, eb[1][0], ec[1][0]); wa[1][0] += ea;
-            triple_grad(B1, C1, b31, c31, pc[1][1], ra3[1][1], acc, ea, eb[1][1], ec[1][1]); wa[1][1] += ea;
-            // side (j, k): sum over the 16 i of this half-warp (lanes with the same tj)
-            float sb0 = eb[0][0] + eb[1][0], sb1 = eb[0][1] + eb[1][1];
+        float2 acc = f2(0.f, 0.f);
+        float2 wa[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll 1
+        for (int k0 = 0; k0 < R_; k0 += 8) {
+            float vb[16], vc[16];   // vb[8q + kk]: side (j_q, k); vc[8p + kk]: side (i_p, k)
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                sb0 += __shfl_xor_sync(0xffffffffu, sb0, o);
-                sb1 += __shfl_xor_sync(0xffffffffu, sb1, o);
+            for (int kk = 0; kk < 8; ++kk) {
+                const int k = k0 + kk;
+                const float4 C0 = S.fc[k][0][ti], C1 = S.fc[k][1][ti], C2 = S.fc[k][2][ti];
+                float2 ecs = f2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float4 B0 = S.fb[k][q][0][tj], B1 = S.fb[k][q][1][tj], B2 = S.fb[k][q][2][tj];
+                    float2 ea, eb, ec;
+                    triple_grad2(pc[q], C0, C1, C2, B0, B1, B2, acc, ea, eb, ec);
+                    wa[q] = add2(wa[q], ea);
+                    vb[8 * q + kk] = eb.x + eb.y;          // sum over the two i of this thread
+                    ecs = add2(ecs, ec);                   // sum over the two j of this thread
+                }
+                vc[kk] = ecs.x;
+                vc[8 + kk] = ecs.y;
             }
-            if (ti == 0) { S.wjk[k][tj] = sb0; S.wjk[k][tj + 16] = sb1; }
-            // side (i, k): sum over the two tj of this warp, then across warps
-            float sc0 = ec[0][0] + ec[0][1], sc1 = ec[1][0] + ec[1][1];
-            sc0 += __shfl_xor_sync(0xffffffffu, sc0, 16);
-            sc1 += __shfl_xor_sync(0xffffffffu, sc1, 16);
-            if (lane < 16) { atomicAdd(&S.wik[k][ti], sc0); atomicAdd(&S.wik[k][ti + 16], sc1); }
+            // (j, k) sides: sum over the 16 i of this half-warp; lane ti ends
+            // with j = tj + 16 (ti >> 3), k = k0 + (ti & 7)
+            const float sb = reduce_scatter16(vb, lane);
+            S.wjk[k0 + (ti & 7)][tj + 16 * (ti >> 3)] = sb;
+            // (i, k) sides: sum over the two tj of this warp (lanes l, l ^ 16),
+            // then over the warps by shared atomics
+            const bool up = (lane & 16) != 0;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float send = up ? vc[m] : vc[m + 8];
+                const float keep = up ? vc[m + 8] : vc[m];
+                vc[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+            const int ip = ti + 16 * (up ? 1 : 0);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) atomicAdd(&S.wik[k0 + m][ip], vc[m]);
         }
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) S.wij[ti + 16 * a][tj + 16 * b] = wa[a][b];
-        add_ff(hi, lo, acc, 0.f);
+        for (int q = 0; q < 2; ++q) {
+            S.wij[ti][tj + 16 * q] = wa[q].x;
+            S.wij[ti + 16][tj + 16 * q] = wa[q].y;
+        }
+        add_ff(hi, lo, acc.x, 0.f);
+        add_ff(hi, lo, acc.y, 0.f);
         __syncthreads();
         // Pair coefficients -> gradient: grad_p += 2 sum_q w_pq (x_p - x_q).
         if (tid < 6 * R_) {
             const int atom = tid >> 1, half = tid & 1;
             float gx = 0.f, gy = 0.f, gz = 0.f;
             const int which = atom / R_, o = atom % R_;
-            const float4 xp = T.xs[which][o];
+            const float4 xp = S.xs[which][o];
             for (int q = 0; q < R_; ++q) {
                 float w;
                 float4 xq;
                 if (which == 0) {
-                    if (half == 0) { w = S.wij[o][q]; xq = T.xs[1][q]; }
-                    else { w = S.wik[q][o]; xq = T.xs[2][q]; }
+                    if (half == 0) { w = S.wij[o][q]; xq = S.xs[1][q]; }
+                    else { w = S.wik[q][o]; xq = S.xs[2][q]; }
                 } else if (which == 1) {
-                    if (half == 0) { w = S.wij[q][o]; xq = T.xs[0][q]; }
-                    else { w = S.wjk[q][o]; xq = T.xs[2][q]; }
+                    if (half == 0) { w = S.wij[q][o]; xq = S.xs[0][q]; }
+                    else { w = S.wjk[q][o]; xq = S.xs[2][q]; }
                 } else {
-                    if (half == 0) { w = S.wjk[o][q]; xq = T.xs[1][q]; }
-                    else { w = S.wik[o][q]; xq = T.xs[0][q]; }
+                    if (half == 0) { w = S.wjk[o][q]; xq = S.xs[1][q]; }
+                    else { w = S.wik[o][q]; xq = S.xs[0][q]; }
                 }
                 gx = fmaf(w, xp.x - xq.x, gx);
                 gy = fmaf(w, xp.y - xq.y, gy);
