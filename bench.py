@@ -378,7 +378,53 @@ def row_stress_n65536_d64(torch, sx, peaks):
     r["bwd_tflops"] = 8 * d * r["bwd_lambda"] / 1e12
     r["fwd_fp32_frac"] = r["fwd_tflops"] / fp32
     r["bwd_fp32_frac"] = r["bwd_tflops"] / fp32
+    r.update(_stress_tensor(torch, sx, peaks, x, y, ("lambda", "bbox", "linear")))
     return r
+
+
+def _stress_tensor(torch, sx, peaks, x, y, maps):
+    """Tensor-core stress forward and backward (BF16 hi+lo products): pairs/s
+    per map and the issued MMA rate of the lambda map against the measured
+    BF16 peak.  Per 128 x 128 tile the forward issues three K = 2d products,
+    the backward adds three K = 128 products of N = d + 16 for each side."""
+    n, d = x.shape
+    pairs = n * (n - 1) // 2
+    nb = -(-n // 128)
+    tiles = nb * (nb + 1) // 2
+    f_mma = tiles * 128 * 128 * 2 * (2 * d) * 3
+    b_mma = f_mma + tiles * 2 * 128 * (d + 16) * 2 * 128 * 3
+    r = {}
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    g = torch.empty_like(x)
+    for mp in maps:
+        wf = sx.workspace("stress_fwd", n, d, mp, "bf16x3")
+        ms = _median_ms(torch, lambda: sx.simplex_stress_fwd(x, y, None, loss, mp, "bf16x3", wf), 3)
+        r["tc_fwd_" + mp] = pairs / (ms / 1e3)
+        if mp == "lambda":
+            r["tc_fwd_ms"] = ms
+            r["tc_fwd_mma_tflops"] = f_mma / (ms / 1e3) / 1e12
+        del wf
+        wb = sx.workspace("stress_bwd", n, d, mp, "bf16x3")
+        ms = _median_ms(torch, lambda: sx.simplex_stress_bwd(x, y, 1.0, g, mp, "bf16x3", wb), 3)
+        r["tc_bwd_" + mp] = pairs / (ms / 1e3)
+        if mp == "lambda":
+            r["tc_bwd_ms"] = ms
+            r["tc_bwd_mma_tflops"] = b_mma / (ms / 1e3) / 1e12
+        del wb
+    bf16 = peaks.get("bf16_tflops") if peaks else None
+    if bf16:
+        r["tc_fwd_bf16_frac"] = r["tc_fwd_mma_tflops"] / bf16
+        r["tc_bwd_bf16_frac"] = r["tc_bwd_mma_tflops"] / bf16
+    return r
+
+
+def row_stress_n16384_d64(torch, sx, peaks):
+    """Stress loss n=16384, d=64 on tensor cores: a smaller case of the same
+    kernels, sized for profiler captures."""
+    xn = synth.normal(16384, 64, seed=4)
+    x = torch.from_numpy(xn).cuda()
+    y = torch.from_numpy(synth.perturbed(xn, 0.1, seed=5)).cuda()
+    return _stress_tensor(torch, sx, peaks, x, y, ("lambda",))
 
 
 ROWS = {
@@ -390,7 +436,7 @@ ROWS = {
     "stress_n65536_d64": row_stress_n65536_d64,
 }
 # profiling-only cases (not part of the default rows)
-PROFILE_ROWS = {"edm_n16384_d64": row_edm_n16384_d64}
+PROFILE_ROWS = {"edm_n16384_d64": row_edm_n16384_d64, "stress_n16384_d64": row_stress_n16384_d64}
 
 
 def rows_measure(torch, sx, peaks, names=None):

@@ -328,8 +328,9 @@ def stress_fwd(x, y, map="lambda", prec="fp32", store_d=False):
 
 
 def stress_bwd(x, y, gscale=1.0, map="lambda", prec="fp32"):
+    n, d = x.shape
     grad = torch.empty_like(x)
-    simplex_stress_bwd(x, y, gscale, grad, map, prec)
+    simplex_stress_bwd(x, y, gscale, grad, map, prec, workspace("stress_bwd", n, d, map, prec))
     return grad
 
 

@@ -161,7 +161,7 @@ extern "C" int simplex_block_rho(int op, int64_t d, int prec) {
         case SIMPLEX_OP_ATM_ENERGY:
         case SIMPLEX_OP_ATM_FORCES: return kAtmRho;
         case SIMPLEX_OP_STRESS_FWD:
-        case SIMPLEX_OP_STRESS_BWD: return kStressRho;
+        case SIMPLEX_OP_STRESS_BWD: return stress_use_umma(d, prec) ? kStressUmmaRho : kStressRho;
         default: return -1;
     }
 }
@@ -179,11 +179,13 @@ extern "C" int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map
             return 8 * (g.gx * g.gy * g.gz + kReduceSlots);
         }
         case SIMPLEX_OP_STRESS_FWD: {
+            if (stress_use_umma(d, prec)) return stress_umma_workspace_bytes(n, d, false);
             const int64_t nb = (n + kStressRho - 1) / kStressRho;
             const Grid g = grid2(nb, map);
             return 8 * (g.gx * g.gy * g.gz + kReduceSlots);
         }
-        case SIMPLEX_OP_STRESS_BWD: return 0;
+        case SIMPLEX_OP_STRESS_BWD:
+            return stress_use_umma(d, prec) ? stress_umma_workspace_bytes(n, d, true) : 0;
         default: return -1;
     }
 }

@@ -23,14 +23,12 @@
 // MMA warp already fills the other accumulator.  Every mbarrier wait is
 // bounded in time; a wait that runs out sets a device error flag
 // (simplex_device_errors) and the block stops instead of hanging.
-#include <cuda.h>
-#include <cuda_bf16.h>
-
 #include <cstddef>
 #include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "umma.cuh"
 
 namespace sx {
 namespace umma {
@@ -40,150 +38,10 @@ constexpr int TN = 128;                        // tile columns (j)
 constexpr int KC = 64;                         // K chunk: 64 BF16 = one 128-byte swizzle row
 constexpr int TILE_BYTES = TM * KC * 2;        // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
-constexpr int TMEM_COLS = 128;
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
-
-// Instruction descriptor of tcgen05.mma kind::f16: D = F32 (bits 4-5),
-// A = B = BF16 (bits 7-9, 10-12), both K-major (bits 15, 16 = 0),
-// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// K-major BF16 operands, M = TM, N = TN.
+constexpr uint32_t kIdesc = idesc_bf16(TM, TN, false, false);
 
 __device__ int g_error;   // set when a bounded wait runs out
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-// One potentially blocking test of the phase: the thread may be suspended
-// up to kSuspendNs while the phase is incomplete (instead of spinning).
-constexpr uint32_t kSuspendNs = 200000;
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(phase), "r"(kSuspendNs)
-        : "memory");
-    return ok != 0;
-}
-
-// Waits for the phase of parity `phase` to complete, at most kWaitCycles,
-// or until another thread of the block has flagged a failure.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, volatile int *fail) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, phase)) {
-        if (*fail) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            *fail = 1;
-            atomicExch(&g_error, 1);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// shared -> global bulk copy (addresses 16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void bulk_store(float *gdst, uint32_t ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                 "r"(ssrc), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() {
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-
-// waits until this thread's committed bulk copies have read their sources
-__device__ __forceinline__ void bulk_wait_read() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void bulk_wait_all() {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile with 128-byte
-// swizzle: start address >> 4 (bits 0-13), leading byte offset 16 >> 4
-// (bits 16-29, unused by this layout), stride byte offset 1024 >> 4 between
-// 8-row groups (bits 32-45), descriptor version 1 (bit 46), swizzle mode 2 =
-// 128 B (bits 61-63).  The tile base is 1024-byte aligned, so base offset 0.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
-}
 
 // x = hi + lo in BF16 and |x|^2 in FP32, one warp per row.
 __global__ void __launch_bounds__(256) k_split_bf16(const float *__restrict__ x, int64_t n, int d,
@@ -227,7 +85,6 @@ constexpr int kAccCols = 2 * TN;               // two accumulators in TMEM
 // bytes) / 4 floats, so that the 16-byte-aligned body of the global row
 // segment starts at a 16-byte-aligned shared address and one cp.async.bulk
 // copies it.
-constexpr int kStageCols = 64;
 constexpr int kStagePitch = 68;
 
 struct PCtl {
@@ -275,14 +132,6 @@ struct TileWalk {
     }
 };
 
-__device__ __forceinline__ void named_bar(int id, int threads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
                                                           const __grid_constant__ CUtensorMap map_lo,
@@ -312,15 +161,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         }
         ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
+        prefetch_map(&map_hi);
+        prefetch_map(&map_lo);
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&ctl.tmem)),
-                     "r"(kAccCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tmem_alloc(smem_u32(&ctl.tmem), kAccCols);
     }
     tc_fence_before();
     __syncthreads();
@@ -338,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 for (int c = 0; c < nchunks; ++c, ++it) {
                     const int s = (int)(it % kStages);
                     const uint32_t ph = (it / kStages) & 1;
-                    if (!mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail)) break;
+                    if (!mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error)) break;
                     const uint32_t bar = smem_u32(&ctl.full[s]);
                     const uint32_t dst = s_stages + s * STAGE_BYTES;
                     mbar_expect_tx(bar, STAGE_BYTES);
@@ -351,10 +196,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
             // a failed block waits (bounded) for its loads in flight
             if (*fail && it > 0) {
                 const uint32_t last = it - 1;
-                const long long t0 = clock64();
-                while (!mbar_try_wait(smem_u32(&ctl.full[last % kStages]), (last / kStages) & 1) &&
-                       clock64() - t0 < kWaitCycles) {
-                }
+                mbar_drain(smem_u32(&ctl.full[last % kStages]), (last / kStages) & 1);
             }
         }
     } else if (warp == 1) {
@@ -365,12 +207,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
             uint32_t it = 0, tt = 0;
             while (!*fail && walk.next(X, Y)) {
                 const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
-                if (!mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail)) break;
+                if (!mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error)) break;
                 tc_fence_after();
                 const uint32_t dtm = tmem + acc * TN;
                 for (int c = 0; c < nchunks; ++c, ++it) {
                     const int s = (int)(it % kStages);
-                    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail)) break;
+                    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail, &g_error)) break;
                     tc_fence_after();
                     const uint32_t src = s_stages + s * STAGE_BYTES;
 #pragma unroll
@@ -380,9 +222,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                         const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
                         const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
                         const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
-                        mma_bf16(dtm, ah, bh, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16(dtm, ah, bl, 1u);
-                        mma_bf16(dtm, al, bh, 1u);
+                        mma_bf16(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16(dtm, ah, bl, kIdesc, 1u);
+                        mma_bf16(dtm, al, bh, kIdesc, 1u);
                     }
                     mma_commit(smem_u32(&ctl.empty[s]));
                 }
@@ -422,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
             const int shift = (int)((reinterpret_cast<uintptr_t>(out + gbase) >> 2) & 3);
             float *myrow = stg + lane * kStagePitch + shift;
             __syncwarp();
-            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail)) break;
+            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail, &g_error)) break;
             tc_fence_after();
             float v0[32], v1[32];
             const uint32_t taddr = tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * half);
@@ -488,48 +330,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kAccCols)
-                     : "memory");
+        tmem_dealloc(tmem, kAccCols);
     }
 }
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (the
-// library links only the CUDA runtime).
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                 const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                 const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiled encode_fn() {
-    static std::once_flag once;
-    static EncodeTiled fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    });
-    return fn;
-}
-
-// n x d BF16 row-major, boxes of 128 rows x 64 columns, 128-byte swizzle,
-// zero fill outside the matrix.
-static bool make_map(CUtensorMap *m, void *ptr, int64_t n, int d) {
-    EncodeTiled f = encode_fn();
-    if (!f) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)d * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)TM};
-    const cuuint32_t estr[2] = {1, 1};
-    return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
 static int smem_optin() {
     int dev = 0;
@@ -573,7 +376,7 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
     __nv_bfloat16 *xl = reinterpret_cast<__nv_bfloat16 *>(w + align_up(n * d * 2, 1024));
     float *nrm = reinterpret_cast<float *>(w + 2 * align_up(n * d * 2, 1024));
     CUtensorMap mh, ml;
-    if (!make_map(&mh, xh, n, (int)d) || !make_map(&ml, xl, n, (int)d)) return SIMPLEX_ECUDA;
+    if (!make_map_bf16(&mh, xh, n, d, d, TM) || !make_map_bf16(&ml, xl, n, d, d, TM)) return SIMPLEX_ECUDA;
     int st = smem_optin();
     if (st) return st;
     k_split_bf16<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(x, n, (int)d, xh, xl, nrm);
@@ -614,5 +417,7 @@ int umma_device_errors(cudaStream_t s) {
 }  // namespace sx
 
 extern "C" int simplex_device_errors(void *stream) {
-    return sx::umma_device_errors((cudaStream_t)stream);
+    const int a = sx::umma_device_errors((cudaStream_t)stream);
+    const int b = sx::stress_umma_errors((cudaStream_t)stream);
+    return a != SIMPLEX_OK ? a : b;
 }

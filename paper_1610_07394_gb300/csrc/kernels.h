@@ -19,5 +19,17 @@ constexpr int kEdmUmmaRho = 128;
 int64_t edm_umma_workspace_bytes(int64_t n, int64_t d);
 int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void *ws,
                  int64_t ws_bytes, cudaStream_t s);
+int umma_device_errors(cudaStream_t s);
+
+// Tensor-core stress loss and gradient (stress_umma.cu): tiles of 128 x 128
+// pairs, d % 32 == 0 and d <= 96.
+constexpr int kStressUmmaRho = 128;
+bool stress_umma_ok(int64_t d);
+bool stress_use_umma(int64_t d, int prec);
+int64_t stress_umma_workspace_bytes(int64_t n, int64_t d, bool bwd);
+int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float *y, float *d_out,
+                    double *loss, double gscale, float *grad, int map, void *ws, int64_t ws_bytes,
+                    cudaStream_t s);
+int stress_umma_errors(cudaStream_t s);
 
 }  // namespace sx

@@ -270,7 +270,7 @@ static int stress_check(int64_t n, int64_t d, const float *x, const float *y, in
                         Grid &g, int64_t &nb) {
     if (n < 1 || d < 1 || !x || !y || map < MAP_LAMBDA || map > MAP_LINEAR) return SIMPLEX_EINVAL;
     if (prec < SIMPLEX_PREC_FP32 || prec > SIMPLEX_PREC_AUTO) return SIMPLEX_EINVAL;
-    if (prec == SIMPLEX_PREC_BF16X3) return SIMPLEX_EUNSUPPORTED;
+    if (prec == SIMPLEX_PREC_BF16X3 && !stress_umma_ok(d)) return SIMPLEX_EUNSUPPORTED;
     if (!aligned(x, 4) || !aligned(y, 4)) return SIMPLEX_EALIGN;
     if (d > (1 << 24) || n > ((int64_t)1 << 31) || n * d > ((int64_t)1 << 40)) return SIMPLEX_EOVERFLOW;
     nb = (n + SR - 1) / SR;
@@ -316,6 +316,9 @@ extern "C" int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const fl
     int st = stress_check(n, d, x, y, map, prec, g, nb);
     if (st) return st;
     if (!aligned(loss, 8) || (d_out && !aligned(d_out, 4))) return SIMPLEX_EALIGN;
+    if (stress_use_umma(d, prec))
+        return stress_umma_run(false, n, d, x, y, d_out, loss, 0.0, nullptr, map, workspace, ws_bytes,
+                               (cudaStream_t)stream);
     const int64_t blocks = g.gx * g.gy;
     if (!workspace || ws_bytes < 8 * (blocks + kReduceSlots) || !aligned(workspace, 256))
         return SIMPLEX_EWORKSPACE;
@@ -335,13 +338,15 @@ extern "C" int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const fl
 extern "C" int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
                                   double gscale, float *grad, int map, int prec, void *workspace,
                                   int64_t ws_bytes, void *stream) {
-    (void)workspace; (void)ws_bytes;
     if (!grad) return SIMPLEX_EINVAL;
     Grid g;
     int64_t nb;
     int st = stress_check(n, d, x, y, map, prec, g, nb);
     if (st) return st;
     if (!aligned(grad, 16)) return SIMPLEX_EALIGN;
+    if (stress_use_umma(d, prec))
+        return stress_umma_run(true, n, d, x, y, nullptr, nullptr, gscale, grad, map, workspace,
+                               ws_bytes, (cudaStream_t)stream);
     if ((st = stress_optin())) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;

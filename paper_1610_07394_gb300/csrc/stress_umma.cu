@@ -1,0 +1,663 @@
+// stress_umma.cu -- stress loss and its gradient with every pair product on
+// the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA-staged
+// operands), for d % 32 == 0 and d <= 96.  Tiles of 128 x 128 pairs (rows i
+// of block Y, columns j of block X, X <= Y) of the 2-simplex {j < i}, chosen
+// by a block-space map (Sec. III-A); the EDM is the paper's 2-simplex example
+// (Sec. I).
+//
+// With S = x + y, Delta = x - y and a_i = S_i . Delta_i, the residual is
+//   r_ij = D_ij - delta_ij = a_i + a_j - M_ij,  M_ij = S_i . Delta_j + Delta_i . S_j,
+// so M is one product of K = 2d: P = [S | Delta] (rows i) times Q = [Delta | S]
+// (rows j).  P and Q are split into BF16 hi + lo and M accumulates
+// hi.hi + hi.lo + lo.hi in FP32 in tensor memory (GEMM1).
+//
+// Forward: L = sum_{j<i} r_ij^2, from the accumulator in the epilogue.
+//
+// Backward: dL/dx_i = 4 sum_{j != i} r_ij (x_i - x_j).  The epilogue writes
+// the masked residual tile C (C_ij = r_ij for valid j < i, else 0) to shared
+// memory as BF16 hi + lo, and GEMM2 forms both sides of the tile:
+//   rows    G_Y = C   [X_X | 1],   grad_i += 4 (G_Y[i][d] x_i - G_Y[i][0:d])
+//   columns G_X = C^T [X_Y | 1],   grad_j += 4 (G_X[j][d] x_j - G_X[j][0:d])
+// with X^T stored transposed (d rows of coordinates, a row of ones giving the
+// row / column sums of C in column d of the accumulator, zero rows up to
+// d + 16).  The C tile serves as the K-major A operand of the row side and,
+// read M-major through its descriptor, as C^T for the column side.  Each
+// CTA walks a contiguous range of the map's grid, along which the row block
+// Y stays fixed for runs of tiles (with the lambda map for 2^floor(log2 wy)
+// consecutive grid blocks of row wy), so G_Y accumulates in TMEM over a run
+// and is flushed once per run; G_X is flushed per tile.  Flushes are FP32
+// vector atomics into grad.
+//
+// Persistent and warp-specialised, one CTA per SM: warp 0 issues TMA loads
+// into a two-stage ring of 64 KB stages (GEMM1 chunks, then GEMM2 coordinate
+// tiles), warp 1 issues the MMAs (GEMM1 of tile t+1 runs while the epilogue
+// drains tile t), eight epilogue warps (two per TMEM lane quarter) read the
+// accumulators.  Every wait is bounded (simplex_device_errors).
+#include <cstddef>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "umma.cuh"
+
+namespace sx {
+namespace summa {
+
+using namespace umma;
+
+constexpr int TM = 128;                        // tile rows (i)
+constexpr int TN = 128;                        // tile columns (j)
+constexpr int KC = 64;                         // K chunk: 64 BF16 = one 128-byte swizzle row
+constexpr int TILE_BYTES = TM * KC * 2;        // 16 KB: 128 rows x 64 BF16
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // 64 KB
+constexpr int kStages = 2;
+constexpr int C_BYTES = 4 * TILE_BYTES;        // C hi, lo for column halves 0, 1
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kTmemCols = 512;
+constexpr int kGY = 256;                       // TMEM column of G_Y (after two GEMM1 accumulators)
+constexpr int kGX = 384;                       // TMEM column of G_X
+constexpr int kMaxCtas = 1024;
+
+__device__ int g_error;   // set when a bounded wait runs out
+
+struct Ctl {
+    uint64_t full[kStages], empty[kStages];   // ring: TMA -> MMA -> TMA
+    uint64_t tfull[2], tempty[2];             // GEMM1 accumulators: MMA -> epilogue -> MMA
+    uint64_t cready;                          // C tile written (epilogue -> MMA)
+    uint64_t g2done;                          // GEMM2 of a tile complete (MMA -> epilogue)
+    uint64_t gfree;                           // G accumulators read out (epilogue -> MMA)
+    uint64_t done;                            // every MMA of the block complete
+    uint32_t tmem;
+    int fail;
+    alignas(16) float acol[kEpiWarps][64];    // a_j of each epilogue warp's 64 columns
+    float red[2 * (kThreads / 32)];
+};
+
+constexpr int kCtlBytes = 4096;
+constexpr int SMEM_BYTES = 1024 + kStages * STAGE_BYTES + C_BYTES + kCtlBytes;
+static_assert(sizeof(Ctl) <= kCtlBytes, "control block");
+static_assert(offsetof(Ctl, acol) % 16 == 0, "float4 reads of a_j");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
+
+// The tiles of a contiguous range of the map's grid (gx x gy, x fastest),
+// split evenly over the CTAs; each grid block maps to zero, one or two tiles.
+template <int MAP>
+struct RangeWalk {
+    int64_t w, end;
+    int wx, wy, gx, nb;
+    int pend, px, py;
+    __device__ RangeWalk(int64_t total, int gx_, int nb_) : gx(gx_), nb(nb_), pend(0), px(0), py(0) {
+        const int64_t G = gridDim.x, b = blockIdx.x;
+        const int64_t per = total / G, rem = total % G;
+        w = b * per + (b < rem ? b : rem);
+        end = w + per + (b < rem ? 1 : 0);
+        wy = (int)(w / gx_);
+        wx = (int)(w - (int64_t)wy * gx_);
+    }
+    __device__ bool next(int &X, int &Y) {
+        if (pend) { pend = 0; X = px; Y = py; return true; }
+        while (w < end) {
+            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb)
+                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb);
+            ++w;
+            if (++wx == gx) { wx = 0; ++wy; }
+            if (L.cnt == 0) continue;
+            X = L.x[0]; Y = L.y[0];
+            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
+            return true;
+        }
+        return false;
+    }
+};
+
+// Next ring stage for the producer: waits until it is free and arms it for
+// `bytes` of TMA data.
+__device__ __forceinline__ bool ring_acquire(Ctl &ctl, uint32_t s_stages, uint32_t &it,
+                                             uint32_t bytes, uint32_t &dst, uint32_t &bar,
+                                             volatile int *fail) {
+    const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+    if (!mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error)) return false;
+    bar = smem_u32(&ctl.full[s]);
+    dst = s_stages + s * STAGE_BYTES;
+    mbar_expect_tx(bar, bytes);
+    ++it;
+    return true;
+}
+
+// Next ring stage for the MMA issuer: waits until its data has landed.
+__device__ __forceinline__ bool ring_take(Ctl &ctl, uint32_t s_stages, uint32_t it, uint32_t &src,
+                                          volatile int *fail) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail, &g_error)) return false;
+    tc_fence_after();
+    src = s_stages + s * STAGE_BYTES;
+    return true;
+}
+
+// Coordinates of block B as X^T tiles: rows t = 0 .. NG-1, columns
+// B*128 .. B*128 + 127 as two 64-column boxes, hi then lo.
+__device__ __forceinline__ void load_xt(const CUtensorMap *mh, const CUtensorMap *ml, int B,
+                                        uint32_t dst, uint32_t box, uint32_t bar) {
+    tma_load_2d(dst, mh, B * TN, 0, bar);
+    tma_load_2d(dst + box, mh, B * TN + 64, 0, bar);
+    tma_load_2d(dst + 2 * box, ml, B * TN, 0, bar);
+    tma_load_2d(dst + 3 * box, ml, B * TN + 64, 0, bar);
+}
+
+// grad rows of block B += scale4 (G[row][d] x_row - G[row][0:d]) from the
+// accumulator at TMEM column gcol: this thread's lane quarter row, its half
+// of the d coordinates.  All lanes execute the TMEM loads.
+__device__ __forceinline__ void flush_g(uint32_t tmem, uint32_t gcol, int B, int quarter, int half,
+                                        int lane, int d, int64_t n, float scale4,
+                                        const float *__restrict__ x, float *__restrict__ grad) {
+    const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + gcol;
+    const float s = tmem_ld1(tl + (uint32_t)d);
+    const int64_t row = (int64_t)B * TM + 32 * quarter + lane;
+    const int hw = d >> 1;
+    for (int c = 0; c < hw; c += 16) {
+        float v[16];
+        tmem_ld16(tl + (uint32_t)(half * hw + c), v);
+        if (row < n) {
+            const float *xr = x + row * d + half * hw + c;
+            float *gr = grad + row * d + half * hw + c;
+#pragma unroll
+            for (int q = 0; q < 16; q += 4) {
+                const float4 xv = __ldg(reinterpret_cast<const float4 *>(xr + q));
+                const float4 o = make_float4(scale4 * fmaf(s, xv.x, -v[q]), scale4 * fmaf(s, xv.y, -v[q + 1]),
+                                             scale4 * fmaf(s, xv.z, -v[q + 2]), scale4 * fmaf(s, xv.w, -v[q + 3]));
+                atomicAdd(reinterpret_cast<float4 *>(gr + q), o);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+template <int MAP, bool BWD>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_stress_umma(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
+                  const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
+                  const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
+                  const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
+                  int gx, int64_t total, float scale4, float *__restrict__ grad,
+                  double *__restrict__ partials) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *cbuf = base + kStages * STAGE_BYTES;
+    Ctl &ctl = *reinterpret_cast<Ctl *>(cbuf + C_BYTES);
+    const uint32_t s_stages = smem_u32(base), s_c = smem_u32(cbuf);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int *fail = &ctl.fail;
+    const int NG = d + 16;                       // GEMM2 N: d coordinates, the ones row, zero rows
+    const int nc1 = (2 * d) / KC;                // GEMM1 K chunks
+    const uint32_t xt_box = (uint32_t)NG * 128;  // bytes of one 64-column X^T box
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&ctl.full[s]), 1);
+            mbar_init(smem_u32(&ctl.empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&ctl.tfull[b]), 1);
+            mbar_init(smem_u32(&ctl.tempty[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(&ctl.cready), kEpiWarps);
+        mbar_init(smem_u32(&ctl.g2done), 1);
+        mbar_init(smem_u32(&ctl.gfree), kEpiWarps);
+        mbar_init(smem_u32(&ctl.done), 1);
+        ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&mPh);
+        prefetch_map(&mPl);
+        prefetch_map(&mQh);
+        prefetch_map(&mQl);
+        if (BWD) {
+            prefetch_map(&mTh);
+            prefetch_map(&mTl);
+        }
+    }
+    if (warp == 1) tmem_alloc(smem_u32(&ctl.tmem), kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl.tmem;
+    float lhi = 0.f, llo = 0.f;   // loss partial (forward)
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            RangeWalk<MAP> walk(total, gx, nb);
+            uint32_t it = 0, dst, bar;
+            int X, Y, pX = 0, pY = 0;
+            bool ok = true, have = false;
+            while (ok && !*fail && walk.next(X, Y)) {
+                for (int c = 0; c < nc1; ++c) {
+                    if (!(ok = ring_acquire(ctl, s_stages, it, STAGE_BYTES, dst, bar, fail))) break;
+                    tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
+                    tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
+                    tma_load_2d(dst + 2 * TILE_BYTES, &mQh, c * KC, X * TN, bar);
+                    tma_load_2d(dst + 3 * TILE_BYTES, &mQl, c * KC, X * TN, bar);
+                }
+                if (BWD && ok && have) {
+                    // GEMM2 operands of the previous tile: X^T of its columns, then of its rows
+                    if ((ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                        load_xt(&mTh, &mTl, pX, dst, xt_box, bar);
+                    if (ok && (ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                        load_xt(&mTh, &mTl, pY, dst, xt_box, bar);
+                }
+                pX = X; pY = Y; have = true;
+            }
+            if (BWD && ok && !*fail && have) {
+                if ((ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                    load_xt(&mTh, &mTl, pX, dst, xt_box, bar);
+                if (ok && (ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                    load_xt(&mTh, &mTl, pY, dst, xt_box, bar);
+            }
+            // a failed block waits (bounded) for the loads it may have in flight
+            if (*fail)
+                for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0; k < it; ++k)
+                    mbar_drain(smem_u32(&ctl.full[k % kStages]), (k / kStages) & 1);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id1 = idesc_bf16(TM, TN, false, false);
+            const uint32_t id_row = idesc_bf16(TM, NG, false, false);
+            const uint32_t id_col = idesc_bf16(TM, NG, true, false);
+            RangeWalk<MAP> walk(total, gx, nb);
+            uint32_t it = 0, t = 0, src;
+            int X, Y, prevY = -1, prev2Y = -1;
+            bool ok = true;
+            // GEMM2 of tile u (its row block continues the previous tile's run if sameY)
+            auto gemm2 = [&](uint32_t u, bool sameY) -> bool {
+                if (!mbar_wait(smem_u32(&ctl.cready), u & 1, fail, &g_error)) return false;
+                if (u >= 1 && !mbar_wait(smem_u32(&ctl.gfree), (u - 1) & 1, fail, &g_error)) return false;
+                tc_fence_after();
+                // rows: G_Y (+)= C [X_X | 1], K = j over the two column halves of C
+                if (!ring_take(ctl, s_stages, it, src, fail)) return false;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint64_t ah = sw128_desc(s_c + h * TILE_BYTES + ks * 32);
+                        const uint64_t al = sw128_desc(s_c + (2 + h) * TILE_BYTES + ks * 32);
+                        const uint64_t bh = sw128_desc(src + h * xt_box + ks * 32);
+                        const uint64_t bl = sw128_desc(src + (2 + h) * xt_box + ks * 32);
+                        const uint32_t acc = (h == 0 && ks == 0 && !sameY) ? 0u : 1u;
+                        mma_bf16(tmem + kGY, ah, bh, id_row, acc);
+                        mma_bf16(tmem + kGY, ah, bl, id_row, 1u);
+                        mma_bf16(tmem + kGY, al, bh, id_row, 1u);
+                    }
+                mma_commit(smem_u32(&ctl.empty[it % kStages]));
+                ++it;
+                // columns: G_X = C^T [X_Y | 1], K = i; A is C read M-major (M = j
+                // over the two 64-column halves, LBO = one half tile apart)
+                if (!ring_take(ctl, s_stages, it, src, fail)) return false;
+#pragma unroll
+                for (int ks = 0; ks < TM / 16; ++ks) {
+                    const uint64_t ah = sw128_desc(s_c + ks * 2048, TILE_BYTES, 1024);
+                    const uint64_t al = sw128_desc(s_c + 2 * TILE_BYTES + ks * 2048, TILE_BYTES, 1024);
+                    const uint32_t hb = (uint32_t)(ks >> 2), kb = (uint32_t)(ks & 3) * 32;
+                    const uint64_t bh = sw128_desc(src + hb * xt_box + kb);
+                    const uint64_t bl = sw128_desc(src + (2 + hb) * xt_box + kb);
+                    mma_bf16(tmem + kGX, ah, bh, id_col, ks ? 1u : 0u);
+                    mma_bf16(tmem + kGX, ah, bl, id_col, 1u);
+                    mma_bf16(tmem + kGX, al, bh, id_col, 1u);
+                }
+                mma_commit(smem_u32(&ctl.empty[it % kStages]));
+                ++it;
+                mma_commit(smem_u32(&ctl.g2done));
+                return true;
+            };
+            while (ok && !*fail && walk.next(X, Y)) {
+                const uint32_t acc = t & 1, aph = (t >> 1) & 1;
+                if (!(ok = mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error))) break;
+                tc_fence_after();
+                const uint32_t dtm = tmem + acc * TN;
+                for (int c = 0; c < nc1; ++c) {
+                    if (!(ok = ring_take(ctl, s_stages, it, src, fail))) break;
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint32_t ko = ks * 32;
+                        const uint64_t ah = sw128_desc(src + ko);
+                        const uint64_t al = sw128_desc(src + TILE_BYTES + ko);
+                        const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + ko);
+                        const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + ko);
+                        mma_bf16(dtm, ah, bh, id1, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16(dtm, ah, bl, id1, 1u);
+                        mma_bf16(dtm, al, bh, id1, 1u);
+                    }
+                    mma_commit(smem_u32(&ctl.empty[it % kStages]));
+                    ++it;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&ctl.tfull[acc]));
+                if (BWD && t >= 1 && !(ok = gemm2(t - 1, t >= 2 && prevY == prev2Y))) break;
+                prev2Y = prevY;
+                prevY = Y;
+                ++t;
+            }
+            if (BWD && ok && !*fail && t >= 1) gemm2(t - 1, t >= 2 && prevY == prev2Y);
+            // everything issued has completed before the block releases TMEM
+            mma_commit(smem_u32(&ctl.done));
+            mbar_drain(smem_u32(&ctl.done), 0);
+        }
+    } else {
+        // ---------------- epilogue: 8 warps, two per TMEM lane quarter
+        const int ew = warp - 2;                 // 0..7
+        const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+        const int half = ew >> 2;                // columns [64*half, 64*half + 64)
+        const int r = 32 * quarter + lane;       // this thread's row in the tile
+        float *ac = &ctl.acol[ew][0];
+        unsigned char *rowh = cbuf + half * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128;
+        unsigned char *rowl = rowh + 2 * TILE_BYTES;
+        RangeWalk<MAP> walk(total, gx, nb);
+        uint32_t t = 0;
+        int X, Y, pX = 0, pY = 0;
+        while (!*fail && walk.next(X, Y)) {
+            const uint32_t acc = t & 1, aph = (t >> 1) & 1;
+            const int64_t row0 = (int64_t)Y * TM, jb = (int64_t)X * TN + 64 * half;
+            {
+                const int64_t j0 = jb + lane, j1 = j0 + 32;
+                const float va = j0 < n ? __ldg(a + j0) : 0.0f;
+                const float vb = j1 < n ? __ldg(a + j1) : 0.0f;
+                __syncwarp();   // the previous tile's reads of ac are done
+                ac[lane] = va;
+                ac[lane + 32] = vb;
+            }
+            const int64_t i = row0 + r;
+            const float ai = i < n ? __ldg(a + i) : 0.0f;
+            // valid columns q < lim: j < n, and j < i on a diagonal tile
+            int64_t lim64 = i < n ? n - jb : 0;
+            if (X == Y && i - jb < lim64) lim64 = i - jb;
+            const int lim = lim64 < 0 ? 0 : (lim64 > 64 ? 64 : (int)lim64);
+            __syncwarp();
+            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail, &g_error)) break;
+            tc_fence_after();
+            float v[64];
+            {
+                float v0[32], v1[32];
+                const uint32_t taddr = tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * half);
+                tmem_ld32(taddr, v0);
+                tmem_ld32(taddr + 32, v1);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) { v[q] = v0[q]; v[32 + q] = v1[q]; }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            float sq = 0.f;
+#pragma unroll
+            for (int q = 0; q < 64; q += 4) {
+                const float4 aj = *reinterpret_cast<const float4 *>(ac + q);
+                const float al4[4] = {aj.x, aj.y, aj.z, aj.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float rq = (ai + al4[k]) - v[q + k];
+                    v[q + k] = q + k < lim ? rq : 0.0f;
+                    sq = fmaf(v[q + k], v[q + k], sq);
+                }
+            }
+            if (!BWD) {
+                add_ff(lhi, llo, sq, 0.f);
+            } else {
+                // the C buffer is free once GEMM2 of the previous tile has completed
+                if (t >= 1 && !mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) break;
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    uint32_t ph[4], pl[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float f0 = v[8 * c + 2 * k], f1 = v[8 * c + 2 * k + 1];
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+                        const __nv_bfloat162 hh = __halves2bfloat162(h0, h1);
+                        ph[k] = *reinterpret_cast<const uint32_t *>(&hh);
+                        pl[k] = pack_bf16(f0 - __bfloat162float(h0), f1 - __bfloat162float(h1));
+                    }
+                    const int off = (c ^ (r & 7)) << 4;
+                    *reinterpret_cast<uint4 *>(rowh + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                    *reinterpret_cast<uint4 *>(rowl + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.cready));
+                if (t >= 1) {
+                    // the previous tile's sides: its columns always, its rows at the end of a run
+                    flush_g(tmem, kGX, pX, quarter, half, lane, d, n, scale4, x, grad);
+                    if (Y != pY) flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl.gfree));
+                }
+            }
+            pX = X;
+            pY = Y;
+            ++t;
+        }
+        if (BWD && !*fail && t >= 1 &&
+            mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) {
+            tc_fence_after();
+            flush_g(tmem, kGX, pX, quarter, half, lane, d, n, scale4, x, grad);
+            flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+    if (!BWD) {
+        const double s = block_sum_ff<kThreads>(lhi, llo, ctl.red);
+        if (tid == 0) partials[blockIdx.x] = s;
+    }
+}
+
+// P = [S | Delta], Q = [Delta | S] (BF16 hi, lo; rows of 2d), a = S . Delta in
+// FP32, and for the backward pass X^T hi, lo (rows t < d: coordinates; row d:
+// ones; rows d+1 .. NG-1: zeros; row pitch `pitch`).  32 points per block.
+__global__ void __launch_bounds__(256) k_stress_prep(const float *__restrict__ x,
+                                                     const float *__restrict__ y, int64_t n, int d,
+                                                     int NG, int64_t pitch,
+                                                     __nv_bfloat16 *__restrict__ Ph,
+                                                     __nv_bfloat16 *__restrict__ Pl,
+                                                     __nv_bfloat16 *__restrict__ Qh,
+                                                     __nv_bfloat16 *__restrict__ Ql,
+                                                     __nv_bfloat16 *__restrict__ Th,
+                                                     __nv_bfloat16 *__restrict__ Tl,
+                                                     float *__restrict__ a) {
+    __shared__ float xs[32][97];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    for (int p = warp; p < 32; p += 8) {
+        const int64_t i = i0 + p;
+        if (i >= n) break;
+        float acc = 0.f;
+        for (int t = lane; t < d; t += 32) {
+            const float xv = __ldg(x + i * d + t), yv = __ldg(y + i * d + t);
+            const float S = xv + yv, D = xv - yv;
+            const __nv_bfloat16 sh = __float2bfloat16_rn(S), dh = __float2bfloat16_rn(D);
+            const __nv_bfloat16 sl = __float2bfloat16_rn(S - __bfloat162float(sh));
+            const __nv_bfloat16 dl = __float2bfloat16_rn(D - __bfloat162float(dh));
+            const int64_t o = i * 2 * d + t;
+            Ph[o] = sh; Pl[o] = sl; Ph[o + d] = dh; Pl[o + d] = dl;
+            Qh[o] = dh; Ql[o] = dl; Qh[o + d] = sh; Ql[o + d] = sl;
+            acc = fmaf(S, D, acc);
+            xs[p][t] = xv;
+        }
+        acc = warp_sum_f32(acc);
+        if (lane == 0) a[i] = acc;
+    }
+    if (Th) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < NG * 32; e += 256) {
+            const int t = e >> 5, p = e & 31;
+            const int64_t i = i0 + p;
+            if (i >= n) continue;
+            const float v = t < d ? xs[p][t] : (t == d ? 1.0f : 0.0f);
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            Th[t * pitch + i] = h;
+            Tl[t * pitch + i] = __float2bfloat16_rn(v - __bfloat162float(h));
+        }
+    }
+}
+
+struct Layout {
+    int64_t Ph, Pl, Qh, Ql, Th, Tl, a, part, edm, total, pitch;
+};
+
+static Layout layout_of(int64_t n, int64_t d, bool bwd) {
+    Layout L;
+    const int64_t pq = align_up(n * 2 * d * 2, 1024);
+    L.pitch = align_up(n, 8);
+    const int64_t xt = bwd ? align_up((d + 16) * L.pitch * 2, 1024) : 0;
+    L.Ph = 0; L.Pl = pq; L.Qh = 2 * pq; L.Ql = 3 * pq;
+    L.Th = 4 * pq; L.Tl = L.Th + xt;
+    L.a = L.Tl + xt;
+    L.part = L.a + align_up(n * 4, 1024);
+    L.edm = L.part + align_up(8 * (kMaxCtas + kReduceSlots), 1024);
+    L.total = L.edm + ((!bwd && d % 64 == 0) ? edm_umma_workspace_bytes(n, d) : 0);
+    return L;
+}
+
+template <bool BWD>
+static cudaError_t optin_one() {
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_stress_umma<MAP_LAMBDA, BWD>, a, SMEM_BYTES)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_stress_umma<MAP_BBOX, BWD>, a, SMEM_BYTES)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_stress_umma<MAP_LINEAR, BWD>, a, SMEM_BYTES);
+}
+
+static int smem_optin() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    static std::mutex mu;
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        if ((e = optin_one<false>()) != cudaSuccess || (e = optin_one<true>()) != cudaSuccess)
+            return cuda_status(e);
+        done[dev] = true;
+    }
+    return SIMPLEX_OK;
+}
+
+template <bool BWD>
+static void launch(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
+                   const float *a, int64_t n, int d, int nb, int gx, int64_t total, float scale4,
+                   float *grad, double *partials) {
+    if (map == MAP_LAMBDA)
+        k_stress_umma<MAP_LAMBDA, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, scale4, grad, partials);
+    else if (map == MAP_BBOX)
+        k_stress_umma<MAP_BBOX, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, scale4, grad, partials);
+    else
+        k_stress_umma<MAP_LINEAR, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, scale4, grad, partials);
+}
+
+}  // namespace summa
+
+bool stress_umma_ok(int64_t d) { return d >= 32 && d <= 96 && d % 32 == 0; }
+
+bool stress_use_umma(int64_t d, int prec) {
+    return (prec == SIMPLEX_PREC_BF16X3 || prec == SIMPLEX_PREC_AUTO) && stress_umma_ok(d);
+}
+
+int64_t stress_umma_workspace_bytes(int64_t n, int64_t d, bool bwd) {
+    return 1024 + summa::layout_of(n, d, bwd).total;
+}
+
+int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float *y, float *d_out,
+                    double *loss, double gscale, float *grad, int map, void *ws, int64_t ws_bytes,
+                    cudaStream_t s) {
+    using namespace summa;
+    if (!stress_umma_ok(d)) return SIMPLEX_EUNSUPPORTED;
+    if (!aligned(x, 16)) return SIMPLEX_EALIGN;
+    if (!ws || ws_bytes < stress_umma_workspace_bytes(n, d, bwd) || !aligned(ws, 256))
+        return SIMPLEX_EWORKSPACE;
+    const int64_t nb = (n + TM - 1) / TM;
+    const Grid g = grid2(nb, map);
+    if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
+    const Layout L = layout_of(n, d, bwd);
+    unsigned char *w = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    auto bf = [&](int64_t off) { return reinterpret_cast<__nv_bfloat16 *>(w + off); };
+    float *a = reinterpret_cast<float *>(w + L.a);
+    double *partials = reinterpret_cast<double *>(w + L.part);
+    const int NG = (int)d + 16;
+    CUtensorMap m[6];
+    if (!make_map_bf16(&m[0], bf(L.Ph), n, 2 * d, 2 * d, TM) ||
+        !make_map_bf16(&m[1], bf(L.Pl), n, 2 * d, 2 * d, TM) ||
+        !make_map_bf16(&m[2], bf(L.Qh), n, 2 * d, 2 * d, TM) ||
+        !make_map_bf16(&m[3], bf(L.Ql), n, 2 * d, 2 * d, TM))
+        return SIMPLEX_ECUDA;
+    if (bwd) {
+        if (!make_map_bf16(&m[4], bf(L.Th), NG, n, L.pitch, NG) ||
+            !make_map_bf16(&m[5], bf(L.Tl), NG, n, L.pitch, NG))
+            return SIMPLEX_ECUDA;
+    } else {
+        m[4] = m[0];   // unused by the forward kernel
+        m[5] = m[1];
+    }
+    int st = smem_optin();
+    if (st) return st;
+    k_stress_prep<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(
+        x, y, n, (int)d, NG, L.pitch, bf(L.Ph), bf(L.Pl), bf(L.Qh), bf(L.Ql),
+        bwd ? bf(L.Th) : nullptr, bwd ? bf(L.Tl) : nullptr, a);
+    note_launches(1);
+    if ((st = launch_status())) return st;
+    int dev = 0, sms = 0;
+    if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
+    if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
+    const int64_t total = g.gx * g.gy;
+    int64_t ctas = total < sms ? total : sms;
+    if (ctas > kMaxCtas) ctas = kMaxCtas;
+    if (bwd && (st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s))))
+        return st;
+    prof_begin(s);
+    if (bwd)
+        launch<true>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total,
+                     (float)(4.0 * gscale), grad, nullptr);
+    else
+        launch<false>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, 0.f,
+                      nullptr, partials);
+    prof_end(s);
+    note_launches(1);
+    if ((st = launch_status())) return st;
+    if (bwd) return SIMPLEX_OK;
+    if ((st = reduce_partials(partials, ctas, partials + kMaxCtas, loss, s))) return st;
+    if (!d_out) return SIMPLEX_OK;
+    // the packed D itself: tensor-core EDM where it applies, else FP32
+    if (d % 64 == 0)
+        return simplex_edm_packed(n, d, x, d_out, map, SIMPLEX_PREC_BF16X3, w + L.edm,
+                                  edm_umma_workspace_bytes(n, d), s);
+    return simplex_edm_packed(n, d, x, d_out, map, SIMPLEX_PREC_FP32, nullptr, 0, s);
+}
+
+int stress_umma_errors(cudaStream_t s) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    if ((e = cudaMemcpyFromSymbol(&h, summa::g_error, sizeof(int))) != cudaSuccess) return cuda_status(e);
+    if (h) {
+        const int zero = 0;
+        if ((e = cudaMemcpyToSymbol(summa::g_error, &zero, sizeof(int))) != cudaSuccess)
+            return cuda_status(e);
+        return SIMPLEX_ETIMEOUT;
+    }
+    return SIMPLEX_OK;
+}
+
+}  // namespace sx

@@ -24,3 +24,24 @@ def to_gpu(a):
 def gather(t: torch.Tensor, idx) -> np.ndarray:
     """t[idx] computed on the device, returned as NumPy."""
     return t[torch.from_numpy(np.asarray(idx, dtype=np.int64)).to(t.device)].cpu().numpy()
+
+
+def stress_moments(x, y):
+    """Stress loss and its full gradient in FP64 from moment matrices,
+    O(n d^2): with S = x + y, Delta = x - y, a_i = S_i . Delta_i, the residual
+    r_ij = a_i + a_j - S_i.Delta_j - Delta_i.S_j = U_i . V_j for
+    U = [a, 1, S, Delta], V = [1, a, -Delta, -S], so
+    L = (1/2) sum_ij (U_i . V_j)^2 = (1/2) <U^T U, V^T V>, and
+    dL/dx_i = 4 (x_i sum_j r_ij - sum_j r_ij x_j) with both sums linear in the
+    moments.  Pinned against the oracle's pairwise loops in test_oracle.py."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n = len(x)
+    S, De = x + y, x - y
+    a = (S * De).sum(1)
+    U = np.hstack([a[:, None], np.ones((n, 1)), S, De])
+    V = np.hstack([np.ones((n, 1)), a[:, None], -De, -S])
+    L = 0.5 * np.sum((U.T @ U) * (V.T @ V))
+    rs = n * a + a.sum() - S @ De.sum(0) - De @ S.sum(0)
+    rx = np.outer(a, x.sum(0)) + a @ x - S @ (De.T @ x) - De @ (S.T @ x)
+    return L, 4 * (x * rs[:, None] - rx)

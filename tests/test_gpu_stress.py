@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import synth
-from helpers import gather, packed_index, rel_err, to_gpu
+from helpers import gather, packed_index, rel_err, stress_moments, to_gpu
 
 pytestmark = pytest.mark.gpu
 L_TOL = 1e-5
@@ -103,4 +103,98 @@ def test_scale_config_sampled(gpu, oracle):
     assert row_err(g[torch.from_numpy(rows).cuda()].double().cpu().numpy(), G).max() <= G_TOL
     gs = g.double().sum(0).abs().max().item()
     assert gs <= 1e-4 * g.double().abs().sum(0).max().item()
-    assert loss.item() > 0
+    L_ref, G_all = stress_moments(x, y)
+    assert abs(loss.item() - L_ref) <= L_TOL * L_ref
+    assert row_err(g.double().cpu().numpy(), G_all).max() <= G_TOL
+
+
+# ---------------------------------------------------------------- tensor cores
+#
+# prec="bf16x3": every pair product on the tensor cores from BF16 hi + lo
+# splits (|v - hi - lo| <= 2^-16 |v|, products hi.hi + hi.lo + lo.hi, FP32
+# accumulation).  Per residual that is a relative error of a few 2^-16 of
+# sum_t |S_it Delta_jt| + |Delta_it S_jt| in the worst case and ~1e-6 of r
+# typically; the loss, a sum of 2e9 squares with independent errors, and the
+# gradient rows keep the FP32 path's tolerances.
+TC_L_TOL = 1e-5
+TC_G_TOL = 1e-4
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("n,d", [(1, 32), (2, 64), (129, 32), (300, 64), (513, 96), (1000, 64)])
+def test_stress_tensor_small(gpu, oracle, mp, n, d):
+    x = synth.normal(n, d, seed=600 + n)
+    y = synth.perturbed(x, 0.1, seed=700 + n)
+    xt, yt = to_gpu(x), to_gpu(y)
+    loss, D = gpu.stress_fwd(xt, yt, mp, "bf16x3", store_d=True)
+    ref = oracle.stress_loss(x, y)
+    assert abs(loss.item() - ref) <= TC_L_TOL * ref
+    ref_D = oracle.edm_packed(x)
+    off = ref_D > 0
+    if off.any():
+        assert rel_err(D.cpu().numpy()[off], ref_D[off]).max() <= 1e-5
+    g = gpu.stress_bwd(xt, yt, 1.0, mp, "bf16x3").double().cpu().numpy()
+    G = oracle.stress_grad_rows(x, y, range(n))
+    if n == 1:
+        assert (g == 0).all()
+    else:
+        assert row_err(g, G).max() <= TC_G_TOL
+
+
+def test_stress_tensor_maps_agree(gpu):
+    """The three maps visit the same tiles: identical loss, gradient equal up
+    to the order of the FP32 atomic flushes."""
+    x = synth.normal(1100, 64, seed=81)
+    y = synth.perturbed(x, 0.1, seed=82)
+    xt, yt = to_gpu(x), to_gpu(y)
+    L = [gpu.stress_fwd(xt, yt, mp, "bf16x3")[0].item() for mp in ("lambda", "bbox", "linear")]
+    assert L[1] == pytest.approx(L[0], rel=1e-12) and L[2] == pytest.approx(L[0], rel=1e-12)
+    g = [gpu.stress_bwd(xt, yt, 1.0, mp, "bf16x3").double() for mp in ("lambda", "bbox", "linear")]
+    for h in g[1:]:
+        assert (h - g[0]).abs().max().item() <= 1e-5 * g[0].abs().max().item()
+
+
+def test_stress_tensor_zero_autograd_fd(gpu, oracle):
+    x = synth.normal(260, 32, seed=83)
+    xt = to_gpu(x)
+    loss, _ = gpu.stress_fwd(xt, xt, "lambda", "bf16x3")
+    assert loss.item() == 0.0
+    assert bool((gpu.stress_bwd(xt, xt, 1.0, "lambda", "bf16x3") == 0).all())
+    y = synth.perturbed(x, 0.2, seed=84)
+    xg = to_gpu(x).requires_grad_(True)
+    (1.5 * gpu.stress_loss(xg, to_gpu(y), "lambda", "bf16x3")).backward()
+    g = xg.grad.double().cpu().numpy()
+    G = 1.5 * oracle.stress_grad_rows(x, y, range(260))
+    assert row_err(g, G).max() <= TC_G_TOL
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    h = 1e-5
+    for a, t in ((0, 0), (131, 17), (259, 31)):
+        xp, xm = xd.copy(), xd.copy()
+        xp[a, t] += h
+        xm[a, t] -= h
+        fd = 1.5 * (oracle.stress_loss(xp, yd) - oracle.stress_loss(xm, yd)) / (2 * h)
+        assert g[a, t] == pytest.approx(fd, rel=TC_G_TOL, abs=1e-6 * np.abs(G).max())
+
+
+def test_stress_tensor_scale_config(gpu, oracle):
+    """n = 65536, d = 64 (the benchmark configuration and launch): the loss
+    and every gradient row against the FP64 moment identity, 16 rows against
+    the oracle's pairwise sums, 100k entries of the stored D."""
+    w = synth.WORKLOADS["stress_n65536_d64"]
+    x = synth.normal(w["n"], w["d"], w["seed"])
+    y = synth.perturbed(x, w["sigma"], w["y_seed"])
+    xt, yt = to_gpu(x), to_gpu(y)
+    loss, D = gpu.stress_fwd(xt, yt, "lambda", "bf16x3", store_d=True)
+    pr = synth.sample_pairs(100000, w["n"], seed=43)
+    got = gather(D, packed_index(pr[:, 0], pr[:, 1]))
+    ref = oracle.edm_pairs(x, pr)
+    m = pr[:, 0] != pr[:, 1]
+    assert rel_err(got[m], ref[m]).max() <= 1e-5
+    del D
+    torch.cuda.empty_cache()
+    L_ref, G_all = stress_moments(x, y)
+    assert abs(loss.item() - L_ref) <= TC_L_TOL * L_ref
+    g = gpu.stress_bwd(xt, yt, 1.0, "lambda", "bf16x3").double().cpu().numpy()
+    assert row_err(g, G_all).max() <= TC_G_TOL
+    rows = synth.sample_indices(16, w["n"], seed=44)
+    assert row_err(g[rows], oracle.stress_grad_rows(x, y, rows)).max() <= TC_G_TOL

@@ -520,3 +520,8 @@ def test_stress_moment_identity(oracle):
     V = np.hstack([np.ones((n, 1)), a[:, None], -De, -S])
     L = 0.5 * np.sum((U.T @ U) * (V.T @ V))   # sum_ij (U_i . V_j)^2
     assert oracle.stress_loss(x, y) == pytest.approx(L, rel=1e-10)
+    # the helper the GPU tests use at full size is this same identity
+    from helpers import stress_moments
+    Lh, gh = stress_moments(x, y)
+    assert Lh == pytest.approx(L, rel=1e-12)
+    assert np.allclose(gh, grad, rtol=1e-12, atol=1e-12 * np.abs(grad).max())
