@@ -47,7 +47,7 @@ NU, EPS = 1.0, 1e-4
 # FMA) and the running sum (1): 22 flops.
 FLOPS_PER_TRIPLE = 22
 ROWS_NAMES = ("edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
-              "stress_n65536_d64", "edm_n16384_d64")
+              "stress_n65536_d64", "edm_n16384_d64", "stress_n16384_d64")
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one k_atm_energy<lambda> launch on this
 # workload, from the ncu capture summarised in
