@@ -153,6 +153,14 @@ extern "C" const char *simplex_strerror(int status) {
 
 extern "C" int simplex_last_cuda_error(void) { return g_last_cuda_error; }
 
+extern "C" int simplex_device_errors(void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int a = umma_device_errors(s);
+    const int b = stress_umma_errors(s);
+    const int c = atm_device_errors(s);
+    return a != SIMPLEX_OK ? a : (b != SIMPLEX_OK ? b : c);
+}
+
 extern "C" int simplex_block_rho(int op, int64_t d, int prec) {
     switch (op) {
         case SIMPLEX_OP_MAP2: return 16;
@@ -172,7 +180,7 @@ extern "C" int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map
         case SIMPLEX_OP_MAP2:
         case SIMPLEX_OP_MAP3: return 0;
         case SIMPLEX_OP_EDM: return edm_workspace_bytes(n, d, map, prec);
-        case SIMPLEX_OP_ATM_ENERGY:
+        case SIMPLEX_OP_ATM_ENERGY: return atm_energy_workspace_bytes(n, map);
         case SIMPLEX_OP_ATM_FORCES: {
             const int64_t nb = (n + kAtmRho - 1) / kAtmRho;
             const Grid g = grid3(nb, map);

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "umma.cuh"
 
 namespace sx {
 
@@ -177,6 +178,155 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
     if (threadIdx.x == 0) {
         const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
         partials[bid] = (double)nu * s;
+    }
+}
+
+// ---------------------------------------------------------------- pair tables
+
+// The energy tables of every block pair (B1 <= B2) of the 2-simplex of
+// blocks, computed once per call instead of once per tile: for the pairs
+// (a in B1, b in B2), in the layout of AtmEnergySmem so that a tile copies
+// them into shared memory as they are (one bulk copy each),
+//   ec form [b][0][t] = (u0.x, u1.x, u0.y, u1.y), [b][1][t] = (u0.z, u1.z, r0^3, r1^3)
+//           with pairs (a = t, b) -> 0 and (a = t + 16, b) -> 1;
+//   eb form [b][h][0][t] = (u.x, u.x, u.y, u.y), [b][h][1][t] = (u.z, u.z, r^3, r^3)
+//           of the pair (a = t + 16h, b);
+// u the unit vector from x_a to x_b, r^3 = (|x_b - x_a|^2 + eps)^-3/2, all
+// zero unless a < b < n.  A tile (I, J, K) takes the ec form of (I, K), the
+// eb form of (J, K) and its pair constants from the ec form of (I, J).
+constexpr int kTabEc = R_ * 2 * 16;                // float4 of the ec form (16 KB)
+constexpr int kTabEb = R_ * 2 * 2 * 16;            // float4 of the eb form (32 KB)
+constexpr int kTabPair = kTabEc + kTabEb;          // float4 per block pair (48 KB)
+constexpr int64_t kTabMaxBytes = int64_t(8) << 30; // larger tables: per-tile tables instead
+
+__host__ __device__ inline int64_t pair_slot(int B1, int B2) {
+    return (int64_t)B2 * (B2 + 1) / 2 + B1;
+}
+
+inline int64_t atm_table_bytes(int64_t nb) { return nb * (nb + 1) / 2 * kTabPair * 16; }
+
+template <int MAP>
+__global__ void __launch_bounds__(256) k_atm_pairtab(int64_t n, const float *__restrict__ x,
+                                                     float eps, int nb, float4 *__restrict__ tab) {
+    __shared__ float4 xs[2][R_];
+    const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int t = 0; t < L.cnt; ++t) {
+        const int B1 = t ? L.x[1] : L.x[0], B2 = t ? L.y[1] : L.y[0];
+        if (t) __syncthreads();
+        if (tid < 2 * R_) {
+            const int which = tid / R_, o = tid % R_;
+            const int64_t g = (int64_t)(which ? B2 : B1) * R_ + o;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < n) v = make_float4(__ldg(x + 3 * g), __ldg(x + 3 * g + 1), __ldg(x + 3 * g + 2), 0.f);
+            xs[which][o] = v;
+        }
+        __syncthreads();
+        float4 *ec = tab + pair_slot(B1, B2) * kTabPair;
+        float4 *eb = ec + kTabEc;
+        for (int e = tid; e < R_ * 16; e += 256) {
+            const int b = e >> 4, a = e & 15;
+            const int64_t gb = (int64_t)B2 * R_ + b, ga = (int64_t)B1 * R_ + a;
+            const float4 u0 = pair_term(xs[0][a], xs[1][b], ga < gb && gb < n, eps);
+            const float4 u1 = pair_term(xs[0][a + 16], xs[1][b], ga + 16 < gb && gb < n, eps);
+            ec[(2 * b) * 16 + a] = make_float4(u0.x, u1.x, u0.y, u1.y);
+            ec[(2 * b + 1) * 16 + a] = make_float4(u0.z, u1.z, u0.w, u1.w);
+            eb[(4 * b + 0) * 16 + a] = make_float4(u0.x, u0.x, u0.y, u0.y);
+            eb[(4 * b + 1) * 16 + a] = make_float4(u0.z, u0.z, u0.w, u0.w);
+            eb[(4 * b + 2) * 16 + a] = make_float4(u1.x, u1.x, u1.y, u1.y);
+            eb[(4 * b + 3) * 16 + a] = make_float4(u1.z, u1.z, u1.w, u1.w);
+        }
+    }
+}
+
+__device__ int g_atm_error;   // set when a bounded wait of the energy kernel runs out
+
+struct AtmEnergyTabSmem {
+    float4 ec[R_][2][16];
+    float4 eb[R_][2][2][16];
+    uint64_t bar;
+};
+
+// The energy kernel fed by the pair tables: per tile, one thread starts two
+// bulk copies (48 KB) into shared memory, every thread reads its pair
+// constants from the (I, J) table meanwhile, then the packed triple loop of
+// k_atm_energy runs unchanged.
+template <int MAP>
+__global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
+                                                           int nb, int p,
+                                                           double *__restrict__ partials) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AtmEnergyTabSmem &S = *reinterpret_cast<AtmEnergyTabSmem *>(smem_raw);
+    __shared__ float red[16];
+    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+    const uint32_t bar = umma::smem_u32(&S.bar);
+    if (threadIdx.x == 0) {
+        umma::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    float hi = 0.f, lo = 0.f;
+    bool bad = false;   // a wait of this thread ran out (the block's result is then NaN)
+#pragma unroll 1
+    for (int t = 0; t < L.cnt; ++t) {
+        int I, J, K;
+        block_of(L, t, I, J, K);
+        if (t) __syncthreads();   // every thread is done with the previous tile's tables
+        if (threadIdx.x == 0 && !bad) {
+            umma::mbar_expect_tx(bar, (uint32_t)(kTabPair * 16));
+            umma::bulk_load(umma::smem_u32(&S.ec[0][0][0]), tab + pair_slot(I, K) * kTabPair,
+                            kTabEc * 16, bar);
+            umma::bulk_load(umma::smem_u32(&S.eb[0][0][0][0]), tab + pair_slot(J, K) * kTabPair + kTabEc,
+                            kTabEb * 16, bar);
+        }
+        // pair constants of (i, j): the ec form of (I, J) at b = j
+        const float4 *pij = tab + pair_slot(I, J) * kTabPair;
+        float2 uij[2][3];
+        float ra3[2][2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = tj + 16 * q;
+            const float4 a = __ldg(pij + (2 * j) * 16 + ti), b = __ldg(pij + (2 * j + 1) * 16 + ti);
+            uij[q][0] = make_float2(a.x, a.y);
+            uij[q][1] = make_float2(a.z, a.w);
+            uij[q][2] = make_float2(b.x, b.y);
+            ra3[0][q] = b.z;
+            ra3[1][q] = b.w;
+        }
+        // bounded wait for the tables; a timeout flags the error, drains
+        // (bounded) and lets the block finish with a NaN result
+        if (!bad) {
+            const long long t0 = clock64();
+            while (!umma::mbar_try_wait(bar, (uint32_t)t & 1)) {
+                if (clock64() - t0 > umma::kWaitCycles) {
+                    atomicExch(&g_atm_error, 1);
+                    umma::mbar_drain(bar, (uint32_t)t & 1);
+                    bad = true;
+                    break;
+                }
+            }
+        }
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int k = 0; k < R_; ++k) {
+            const float4 C0 = S.ec[k][0][ti], C1 = S.ec[k][1][ti];
+            const float4 B00 = S.eb[k][0][0][tj], B01 = S.eb[k][0][1][tj];
+            const float4 B10 = S.eb[k][1][0][tj], B11 = S.eb[k][1][1][tj];
+            triple_energy2(uij[0], C0, C1, B00, B01, acc0);
+            triple_energy2(uij[1], C0, C1, B10, B11, acc1);
+        }
+        add_ff(hi, lo, acc0.x * ra3[0][0], 0.f);
+        add_ff(hi, lo, acc0.y * ra3[1][0], 0.f);
+        add_ff(hi, lo, acc1.x * ra3[0][1], 0.f);
+        add_ff(hi, lo, acc1.y * ra3[1][1], 0.f);
+    }
+    const bool any_bad = __syncthreads_or(bad) != 0;
+    const double s = block_sum_ff<256>(hi, lo, red);
+    if (threadIdx.x == 0) {
+        const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+        partials[bid] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)nu * s;
     }
 }
 
@@ -427,6 +577,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
 }
 
 constexpr int kEnergySmem = (int)sizeof(AtmEnergySmem);
+constexpr int kEnergyTabSmem = (int)sizeof(AtmEnergyTabSmem);
 
 // Both kernels' shared memory exceeds the 48 KB default of a launch; opt in
 // once per device for every instantiation.
@@ -446,7 +597,10 @@ static int smem_optin() {
             (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR>, a, fb)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_atm_energy<MAP_LAMBDA>, a, kEnergySmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_atm_energy<MAP_BBOX>, a, kEnergySmem)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_atm_energy<MAP_LINEAR>, a, kEnergySmem)) != cudaSuccess)
+            (e = cudaFuncSetAttribute(k_atm_energy<MAP_LINEAR>, a, kEnergySmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_energy_tab<MAP_LAMBDA>, a, kEnergyTabSmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_energy_tab<MAP_BBOX>, a, kEnergyTabSmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_energy_tab<MAP_LINEAR>, a, kEnergyTabSmem)) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -454,15 +608,41 @@ static int smem_optin() {
 }
 
 static int atm_check(int64_t n, int64_t d, const float *x, int map, void *ws, int64_t ws_bytes,
-                     Grid &g, int64_t &nb) {
+                     Grid &g, int64_t &nb, int64_t extra = 0) {
     if (n < 1 || d != 3 || !x || map < MAP_LAMBDA || map > MAP_LINEAR) return d != 3 && d > 0 ? SIMPLEX_EUNSUPPORTED : SIMPLEX_EINVAL;
     if (!aligned(x, 4)) return SIMPLEX_EALIGN;
     if (n > (1 << 22)) return SIMPLEX_EOVERFLOW;
     nb = (n + R_ - 1) / R_;
     g = grid3(nb, map);
     if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
-    const int64_t need = 8 * (g.gx * g.gy * g.gz + kReduceSlots);
+    const int64_t need = extra + 8 * (g.gx * g.gy * g.gz + kReduceSlots);
     if (!ws || ws_bytes < need || !aligned(ws, 256)) return SIMPLEX_EWORKSPACE;
+    return SIMPLEX_OK;
+}
+
+// Bytes of the pair tables of simplex_atm_energy (0 where they would exceed
+// kTabMaxBytes and the per-tile tables are used instead).
+static int64_t energy_table_bytes(int64_t nb) {
+    const int64_t t = atm_table_bytes(nb);
+    return t <= kTabMaxBytes ? t : 0;
+}
+
+int64_t atm_energy_workspace_bytes(int64_t n, int map) {
+    const int64_t nb = (n + R_ - 1) / R_;
+    const Grid g = grid3(nb, map);
+    return energy_table_bytes(nb) + 8 * (g.gx * g.gy * g.gz + kReduceSlots);
+}
+
+int atm_device_errors(cudaStream_t s) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    int h = 0;
+    if ((e = cudaMemcpyFromSymbol(&h, g_atm_error, sizeof(int))) != cudaSuccess) return cuda_status(e);
+    if (h) {
+        const int zero = 0;
+        if ((e = cudaMemcpyToSymbol(g_atm_error, &zero, sizeof(int))) != cudaSuccess) return cuda_status(e);
+        return SIMPLEX_ETIMEOUT;
+    }
     return SIMPLEX_OK;
 }
 
@@ -474,20 +654,39 @@ extern "C" int simplex_atm_energy(int64_t n, int64_t d, const float *x, float nu
                                   double *energy, int map, void *workspace, int64_t ws_bytes,
                                   void *stream) {
     if (!energy) return SIMPLEX_EINVAL;
+    if (n < 1 || n > (1 << 22)) return n < 1 ? SIMPLEX_EINVAL : SIMPLEX_EOVERFLOW;
+    const int64_t tab_bytes = energy_table_bytes((n + R_ - 1) / R_);
     Grid g;
     int64_t nb;
-    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb);
+    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb, tab_bytes);
     if (st) return st;
     if (!aligned(energy, 8)) return SIMPLEX_EALIGN;
     cudaStream_t s = (cudaStream_t)stream;
-    double *partials = (double *)workspace;
+    // workspace: [pair tables][one FP64 partial per grid block][reduction slots]
+    float4 *tab = (float4 *)workspace;
+    double *partials = (double *)((char *)workspace + tab_bytes);
     const int64_t blocks = g.gx * g.gy * g.gz;
     double *tmp = partials + blocks;
     if ((st = smem_optin())) return st;
+    if (tab_bytes) {
+        const Grid g2 = grid2(nb, map);
+        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
+        if (map == MAP_LAMBDA) k_atm_pairtab<MAP_LAMBDA><<<dim_of(g2), 256, 0, s>>>(n, x, eps, (int)nb, tab);
+        else if (map == MAP_BBOX) k_atm_pairtab<MAP_BBOX><<<dim_of(g2), 256, 0, s>>>(n, x, eps, (int)nb, tab);
+        else k_atm_pairtab<MAP_LINEAR><<<dim_of(g2), 256, 0, s>>>(n, x, eps, (int)nb, tab);
+        note_launches(1);
+        if ((st = launch_status())) return st;
+    }
     prof_begin(s);
-    if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
-    else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
-    else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    if (tab_bytes) {
+        if (map == MAP_LAMBDA) k_atm_energy_tab<MAP_LAMBDA><<<dim_of(g), 256, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
+        else if (map == MAP_BBOX) k_atm_energy_tab<MAP_BBOX><<<dim_of(g), 256, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
+        else k_atm_energy_tab<MAP_LINEAR><<<dim_of(g), 256, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
+    } else {
+        if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+        else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+        else k_atm_energy<MAP_LINEAR><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
+    }
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;

@@ -416,8 +416,4 @@ int umma_device_errors(cudaStream_t s) {
 
 }  // namespace sx
 
-extern "C" int simplex_device_errors(void *stream) {
-    const int a = sx::umma_device_errors((cudaStream_t)stream);
-    const int b = sx::stress_umma_errors((cudaStream_t)stream);
-    return a != SIMPLEX_OK ? a : b;
-}
+

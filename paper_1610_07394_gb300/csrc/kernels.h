@@ -12,6 +12,8 @@ constexpr int kAtmRho = 32;      // ATM tile: 32 x 32 x 32 triples, 256 threads
 constexpr int kStressRho = 64;   // stress tile: 64 x 64 pairs, 256 threads
 
 int edm_rho(int64_t d, int prec);
+int64_t atm_energy_workspace_bytes(int64_t n, int map);
+int atm_device_errors(cudaStream_t s);
 int64_t edm_workspace_bytes(int64_t n, int64_t d, int map, int prec);
 
 // Tensor-core EDM (edm_umma.cu): tiles of 128 x 128 pairs, d % 64 == 0.
