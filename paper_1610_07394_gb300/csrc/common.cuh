@@ -99,8 +99,12 @@ __device__ __forceinline__ double block_sum_ff(float hi, float lo, float *red) {
     if (lane == 0) { red[2 * w] = hi; red[2 * w + 1] = lo; }
     __syncthreads();
     double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int t = 0; t < NT / 32; ++t) s += (double)red[2 * t] + (double)red[2 * t + 1];
+    if (threadIdx.x == 0) {
+        // the warps' pairs combined in FP32 (FP64 is slow on this part), one conversion
+        float h = red[0], l = red[1];
+        for (int t = 1; t < NT / 32; ++t) add_ff(h, l, red[2 * t], red[2 * t + 1]);
+        s = (double)h + (double)l;
+    }
     return s;
 }
 
