@@ -80,23 +80,25 @@ constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 constexpr int kAccCols = 2 * TN;               // two accumulators in TMEM
 
-// Epilogue staging of one warp: 32 rows of 64 FP32 columns each, row pitch
-// 68 floats.  A row is written at an offset of (its global address mod 16
-// bytes) / 4 floats, so that the 16-byte-aligned body of the global row
-// segment starts at a 16-byte-aligned shared address and one cp.async.bulk
-// copies it.
-constexpr int kStagePitch = 68;
+// Epilogue staging of one TMEM lane quarter (the two warps that read it):
+// 32 rows of the tile's 128 columns, row pitch 132 floats.  A row is written
+// at an offset of (its global address mod 16 bytes) / 4 floats, so that the
+// 16-byte-aligned body of the global row segment starts at a 16-byte-aligned
+// shared address and one cp.async.bulk of up to 512 bytes copies it.
+constexpr int kRowPitch = 132;
 
 struct PCtl {
     uint64_t full[kStages], empty[kStages];   // operand stages: TMA -> MMA -> TMA
     uint64_t tfull[2], tempty[2];             // accumulators: MMA -> epilogue -> MMA
     uint32_t tmem;
     int fail;
+    uint64_t sfull[4], sfree[4];              // per lane quarter: staging written / copied out
     alignas(16) float ncol[kEpiWarps][64];    // each epilogue warp's column norms (float4 reads)
 };
 
 constexpr int kCtlBytes = 3072;
-constexpr int PSMEM_BYTES = 1024 + kStages * STAGE_BYTES + kEpiWarps * 32 * kStagePitch * 4 + kCtlBytes;
+constexpr int kStageBytes = 4 * 32 * kRowPitch * 4;   // four lane quarters
+constexpr int PSMEM_BYTES = 1024 + kStages * STAGE_BYTES + kStageBytes + kCtlBytes;
 static_assert(sizeof(PCtl) <= kCtlBytes, "control block");
 static_assert(offsetof(PCtl, ncol) % 16 == 0, "float4 reads of the column norms");
 static_assert(PSMEM_BYTES <= 227 * 1024, "shared memory per block");
@@ -132,6 +134,50 @@ struct TileWalk {
     }
 };
 
+// Norms of a tile's rows and columns for one epilogue thread: columns
+// col0 + 64 half + lane and + 32 (a, b) and its row row0 + r (ni); 0 past n.
+__device__ __forceinline__ void load_norms(const float *__restrict__ nrm, int64_t n, int X, int Y,
+                                           int half, int r, int lane, float &a, float &b,
+                                           float &ni) {
+    const int64_t j0 = (int64_t)X * TN + 64 * half + lane, j1 = j0 + 32, i = (int64_t)Y * TM + r;
+    a = j0 < n ? __ldg(nrm + j0) : 0.0f;
+    b = j1 < n ? __ldg(nrm + j1) : 0.0f;
+    ni = i < n ? __ldg(nrm + i) : 0.0f;
+}
+
+// 64 consecutive FP32 columns of this thread's TMEM lane: two loads, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v0)[32], float (&v1)[32]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
+          "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]),
+          "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+          "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]),
+          "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr + 32));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        v0[t] = __uint_as_float(r[t]);
+        v1[t] = __uint_as_float(r[32 + t]);
+    }
+}
+
 template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
                                                           const __grid_constant__ CUtensorMap map_lo,
@@ -144,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *stages = base;   // kStages x 64 KB, 1024-aligned tiles
     float *stg_all = reinterpret_cast<float *>(base + kStages * STAGE_BYTES);
-    PCtl &ctl = *reinterpret_cast<PCtl *>(base + kStages * STAGE_BYTES + kEpiWarps * 32 * kStagePitch * 4);
+    PCtl &ctl = *reinterpret_cast<PCtl *>(base + kStages * STAGE_BYTES + kStageBytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t s_stages = smem_u32(stages);
@@ -158,6 +204,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl.tfull[a]), 1);
             mbar_init(smem_u32(&ctl.tempty[a]), kEpiWarps);
+        }
+        for (int q = 0; q < 4; ++q) {
+            mbar_init(smem_u32(&ctl.sfull[q]), 2);
+            mbar_init(smem_u32(&ctl.sfree[q]), 2);
         }
         ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -238,44 +288,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
         const int half = ew >> 2;                // columns [64*half, 64*half + 64)
         const int r = 32 * quarter + lane;       // this thread's row in the tile
-        float *stg = stg_all + ew * 32 * kStagePitch;
+        float *stg = stg_all + quarter * 32 * kRowPitch;   // shared with the other half's warp
+        // this warp's 64 column norms (its own buffer: no cross-warp sync)
+        float *nc = &ctl.ncol[ew][0];
         TileWalk<MAP> walk(gx, total, nb);
         int X, Y;
+        bool have = walk.next(X, Y);
+        // norms of the current tile, loaded one tile ahead
+        float pa = 0.f, pb = 0.f, pni = 0.f;
+        if (have) load_norms(nrm, n, X, Y, half, r, lane, pa, pb, pni);
         uint32_t tt = 0;
-        while (!*fail && walk.next(X, Y)) {
+        while (have && !*fail) {
+            int Xn, Yn;
+            const bool hn = walk.next(Xn, Yn);
+            float na = 0.f, nbv = 0.f, nni = 0.f;
+            if (hn) load_norms(nrm, n, Xn, Yn, half, r, lane, na, nbv, nni);
             const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
             const int64_t row0 = (int64_t)Y * TM, col0 = (int64_t)X * TN;
-            // this warp's 64 column norms (its own buffer: no cross-warp sync)
-            float *nc = &ctl.ncol[ew][0];
-            {
-                const int64_t j0 = col0 + 64 * half + lane, j1 = j0 + 32;
-                const float a = j0 < n ? __ldg(nrm + j0) : 0.0f;
-                const float b = j1 < n ? __ldg(nrm + j1) : 0.0f;
-                __syncwarp();   // the previous tile's reads of nc are done
-                nc[lane] = a;
-                nc[lane + 32] = b;
-            }
+            __syncwarp();   // the previous tile's reads of nc are done
+            nc[lane] = pa;
+            nc[lane + 32] = pb;
             const int64_t i = row0 + r;
-            const float ni = i < n ? __ldg(nrm + i) : 0.0f;
+            const float ni = pni;
             const bool diag = (X == Y);
-            // packed index of this row's first column in this warp's half
-            const int64_t gbase = i * (i + 1) / 2 + col0 + 64 * half;
-            // floats from the row start back to the previous 16-byte boundary of out
-            const int shift = (int)((reinterpret_cast<uintptr_t>(out + gbase) >> 2) & 3);
-            float *myrow = stg + lane * kStagePitch + shift;
+            // packed index of this row's first column in the tile and in this
+            // warp's half; floats from the row start back to the previous
+            // 16-byte boundary of out
+            const int64_t grow = i * (i + 1) / 2 + col0, gbase = grow + 64 * half;
+            const int shift = (int)((reinterpret_cast<uintptr_t>(out + grow) >> 2) & 3);
+            float *myrow = stg + lane * kRowPitch + shift + 64 * half;
             __syncwarp();
             if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail, &g_error)) break;
             tc_fence_after();
             float v0[32], v1[32];
             const uint32_t taddr = tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * half);
-            tmem_ld32(taddr, v0);
-            tmem_ld32(taddr + 32, v1);
+            tmem_ld64(taddr, v0, v1);
             // the accumulator is read: hand it back to the MMA warp
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
             // D = |x_i|^2 + |x_j|^2 - 2 g; flag entries with D < (|x_i|^2 + |x_j|^2)/64
-            float low = 1.0f;
+            float lows[4] = {1.0f, 1.0f, 1.0f, 1.0f};   // independent chains
 #pragma unroll
             for (int q = 0; q < 32; q += 4) {
                 const float4 a = *reinterpret_cast<const float4 *>(nc + q);
@@ -286,10 +339,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 for (int k = 0; k < 4; ++k) {
                     v0[q + k] = fmaf(-2.0f, v0[q + k], sa[k]);
                     v1[q + k] = fmaf(-2.0f, v1[q + k], sb[k]);
-                    low = fminf(low, fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
-                                           fmaf(-0.015625f, sb[k], v1[q + k])));
+                    lows[k] = fminf(lows[k], fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
+                                                   fmaf(-0.015625f, sb[k], v1[q + k])));
                 }
             }
+            const float low = fminf(fminf(lows[0], lows[1]), fminf(lows[2], lows[3]));
             if (__any_sync(0xffffffffu, low < 0.0f)) {
 #pragma unroll
                 for (int q = 0; q < 64; ++q) {
@@ -299,21 +353,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                     if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
                 }
             }
-            bulk_wait_read();   // the previous tile's copy has left this staging row
+            // the staging is free once both warps' copies of the previous tile have read it
+            if (tt > 0) {
+                bulk_wait_read();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.sfree[quarter]));
+                if (!mbar_wait(smem_u32(&ctl.sfree[quarter]), (tt - 1) & 1, fail, &g_error)) break;
+            }
 #pragma unroll
             for (int q = 0; q < 32; ++q) { myrow[q] = v0[q]; myrow[32 + q] = v1[q]; }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.sfull[quarter]));
+            if (!mbar_wait(smem_u32(&ctl.sfull[quarter]), tt & 1, fail, &g_error)) break;
             if (!diag) {
-                // Each lane writes its own 64-float row segment: the 16-byte-
-                // aligned body by one bulk copy, the ragged head and tail (at
-                // most 3 floats each) by plain stores.
-                if (i < n) {
-                    const int h = (4 - shift) & 3;
-                    const int body = (64 - h) & ~3;
-                    fence_proxy_async();
-                    bulk_store(out + gbase + h, smem_u32(myrow + h), (uint32_t)body * 4);
+                // One bulk copy per row segment of the tile (128 columns, both
+                // halves): lanes 0-15 of this warp take rows 16 half .. +15; the
+                // ragged head and tail (at most 3 floats each) by plain stores.
+                const int rr = 16 * half + lane;
+                const int64_t ir = row0 + 32 * quarter + rr;
+                if (lane < 16 && ir < n) {
+                    const int64_t gb = ir * (ir + 1) / 2 + col0;
+                    const int sh = (int)((reinterpret_cast<uintptr_t>(out + gb) >> 2) & 3);
+                    const float *sr = stg + rr * kRowPitch + sh;   // column c at sr[c]
+                    const int h = (4 - sh) & 3;
+                    const int body = (128 - h) & ~3;
+                    bulk_store(out + gb + h, smem_u32(sr + h), (uint32_t)body * 4);
                     bulk_commit();
-                    for (int e = 0; e < h; ++e) out[gbase + e] = myrow[e];
-                    for (int e = h + body; e < 64; ++e) out[gbase + e] = myrow[e];
+                    for (int e = 0; e < h; ++e) out[gb + e] = sr[e];
+                    for (int e = h + body; e < 128; ++e) out[gb + e] = sr[e];
                 }
             } else if (i < n && 64 * half <= r) {
                 // diagonal tile: columns j <= i only, plain stores
@@ -322,6 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 if (rc <= 63) myrow[rc] = 0.0f;           // D_ii = 0 exactly
                 for (int e = 0; e <= last; ++e) out[gbase + e] = myrow[e];
             }
+            X = Xn; Y = Yn; have = hn;
+            pa = na; pb = nbv; pni = nni;
             ++tt;
         }
     }
