@@ -22,11 +22,12 @@
 // row / column sums of C in column d of the accumulator, zero rows up to
 // d + 16).  The C tile serves as the K-major A operand of the row side and,
 // read M-major through its descriptor, as C^T for the column side.  Each
-// CTA walks a contiguous range of the map's grid, along which the row block
-// Y stays fixed for runs of tiles (with the lambda map for 2^floor(log2 wy)
-// consecutive grid blocks of row wy), so G_Y accumulates in TMEM over a run
-// and is flushed once per run; G_X is flushed per tile.  Flushes are FP32
-// vector atomics into grad.
+// CTA walks interleaved chunks of 32 consecutive grid blocks of the map's
+// grid, along which the row block Y stays fixed for runs of tiles (with the
+// lambda map for 2^floor(log2 wy) consecutive grid blocks of row wy), so G_Y
+// accumulates in TMEM over a run and is flushed once per run; G_X (two
+// buffers where TMEM has room) is flushed per tile.  Flushes are FP32 vector
+// atomics into grad.
 //
 // Persistent and warp-specialised, one CTA per SM: warp 0 issues TMA loads
 // into a two-stage ring of 64 KB stages (GEMM1 chunks, then GEMM2 coordinate
@@ -50,23 +51,29 @@ constexpr int TN = 128;                        // tile columns (j)
 constexpr int KC = 64;                         // K chunk: 64 BF16 = one 128-byte swizzle row
 constexpr int TILE_BYTES = TM * KC * 2;        // 16 KB: 128 rows x 64 BF16
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // 64 KB
-constexpr int kStages = 2;
+constexpr int kStages = 2;                     // ring depth of the backward kernel
+constexpr int kMaxStages = 3;                  // the forward kernel also uses the C area as a stage
+template <bool BWD>
+__host__ __device__ constexpr int stages_of() { return BWD ? kStages : kMaxStages; }
 constexpr int C_BYTES = 4 * TILE_BYTES;        // C hi, lo for column halves 0, 1
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTmemCols = 512;
 constexpr int kGY = 256;                       // TMEM column of G_Y (after two GEMM1 accumulators)
-constexpr int kGX = 384;                       // TMEM column of G_X
+// G_X buffer b sits at kGY + NG (1 + b): two buffers when they fit (NG <= 80,
+// d <= 64), so that GEMM2 of a tile does not wait for the previous tile's flush
+__host__ __device__ inline int gx_buffers(int NG) { return kGY + 3 * NG <= kTmemCols ? 2 : 1; }
 constexpr int kMaxCtas = 1024;
 
 __device__ int g_error;   // set when a bounded wait runs out
 
 struct Ctl {
-    uint64_t full[kStages], empty[kStages];   // ring: TMA -> MMA -> TMA
+    uint64_t full[kMaxStages], empty[kMaxStages];   // ring: TMA -> MMA -> TMA
     uint64_t tfull[2], tempty[2];             // GEMM1 accumulators: MMA -> epilogue -> MMA
     uint64_t cready;                          // C tile written (epilogue -> MMA)
     uint64_t g2done;                          // GEMM2 of a tile complete (MMA -> epilogue)
-    uint64_t gfree;                           // G accumulators read out (epilogue -> MMA)
+    uint64_t gxfree[2];                       // a G_X buffer read out (epilogue -> MMA)
+    uint64_t gyfree;                          // G_Y read out at the end of a run (epilogue -> MMA)
     uint64_t done;                            // every MMA of the block complete
     uint32_t tmem;
     int fail;
@@ -79,25 +86,42 @@ constexpr int SMEM_BYTES = 1024 + kStages * STAGE_BYTES + C_BYTES + kCtlBytes;
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block");
 static_assert(offsetof(Ctl, acol) % 16 == 0, "float4 reads of a_j");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
+static_assert(kMaxStages * STAGE_BYTES <= kStages * STAGE_BYTES + C_BYTES, "forward ring fits");
 
-// The tiles of a contiguous range of the map's grid (gx x gy, x fastest),
-// split evenly over the CTAs; each grid block maps to zero, one or two tiles.
+// The tiles a CTA handles: the map's grid (gx x gy, x fastest) cut into
+// chunks of kChunk consecutive grid blocks, chunk c to CTA c mod gridDim.x;
+// each grid block maps to zero, one or two tiles.  Along a grid row the row
+// block Y stays fixed for runs of tiles (with the lambda map for
+// 2^floor(log2 wy) consecutive grid blocks of row wy), so within a chunk
+// G_Y accumulates over runs of up to kChunk tiles, while interleaving the
+// chunks spreads the map's uneven parts (the diagonal-pair row of lambda,
+// the empty upper half of the bounding box) evenly over the CTAs.
+constexpr int kChunk = 32;
+
 template <int MAP>
-struct RangeWalk {
-    int64_t w, end;
+struct ChunkWalk {
+    int64_t c, w, end, total;
     int wx, wy, gx, nb;
     int pend, px, py;
-    __device__ RangeWalk(int64_t total, int gx_, int nb_) : gx(gx_), nb(nb_), pend(0), px(0), py(0) {
-        const int64_t G = gridDim.x, b = blockIdx.x;
-        const int64_t per = total / G, rem = total % G;
-        w = b * per + (b < rem ? b : rem);
-        end = w + per + (b < rem ? 1 : 0);
-        wy = (int)(w / gx_);
-        wx = (int)(w - (int64_t)wy * gx_);
+    __device__ ChunkWalk(int64_t total_, int gx_, int nb_)
+        : c(blockIdx.x), total(total_), gx(gx_), nb(nb_), pend(0), px(0), py(0) {
+        open();
+    }
+    __device__ void open() {
+        w = c * kChunk;
+        end = w + kChunk < total ? w + kChunk : total;
+        wy = (int)(w / gx);
+        wx = (int)(w - (int64_t)wy * gx);
     }
     __device__ bool next(int &X, int &Y) {
         if (pend) { pend = 0; X = px; Y = py; return true; }
-        while (w < end) {
+        for (;;) {
+            if (w >= end) {
+                c += gridDim.x;
+                if (c * kChunk >= total) return false;
+                open();
+                continue;
+            }
             const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb)
                                               : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb);
             ++w;
@@ -107,16 +131,16 @@ struct RangeWalk {
             if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
             return true;
         }
-        return false;
     }
 };
 
 // Next ring stage for the producer: waits until it is free and arms it for
 // `bytes` of TMA data.
+template <int S>
 __device__ __forceinline__ bool ring_acquire(Ctl &ctl, uint32_t s_stages, uint32_t &it,
                                              uint32_t bytes, uint32_t &dst, uint32_t &bar,
                                              volatile int *fail) {
-    const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+    const uint32_t s = it % S, ph = (it / S) & 1;
     if (!mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error)) return false;
     bar = smem_u32(&ctl.full[s]);
     dst = s_stages + s * STAGE_BYTES;
@@ -126,10 +150,11 @@ __device__ __forceinline__ bool ring_acquire(Ctl &ctl, uint32_t s_stages, uint32
 }
 
 // Next ring stage for the MMA issuer: waits until its data has landed.
+template <int S>
 __device__ __forceinline__ bool ring_take(Ctl &ctl, uint32_t s_stages, uint32_t it, uint32_t &src,
                                           volatile int *fail) {
-    const uint32_t s = it % kStages;
-    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail, &g_error)) return false;
+    const uint32_t s = it % S;
+    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / S) & 1, fail, &g_error)) return false;
     tc_fence_after();
     src = s_stages + s * STAGE_BYTES;
     return true;
@@ -188,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *cbuf = base + kStages * STAGE_BYTES;
+    constexpr int NS = stages_of<BWD>();
+    unsigned char *cbuf = base + kStages * STAGE_BYTES;   // backward only (the forward's third stage)
     Ctl &ctl = *reinterpret_cast<Ctl *>(cbuf + C_BYTES);
     const uint32_t s_stages = smem_u32(base), s_c = smem_u32(cbuf);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -198,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t xt_box = (uint32_t)NG * 128;  // bytes of one 64-column X^T box
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&ctl.full[s]), 1);
             mbar_init(smem_u32(&ctl.empty[s]), 1);
         }
@@ -208,7 +234,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_init(smem_u32(&ctl.cready), kEpiWarps);
         mbar_init(smem_u32(&ctl.g2done), 1);
-        mbar_init(smem_u32(&ctl.gfree), kEpiWarps);
+        mbar_init(smem_u32(&ctl.gxfree[0]), kEpiWarps);
+        mbar_init(smem_u32(&ctl.gxfree[1]), kEpiWarps);
+        mbar_init(smem_u32(&ctl.gyfree), kEpiWarps);
         mbar_init(smem_u32(&ctl.done), 1);
         ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -231,13 +259,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            RangeWalk<MAP> walk(total, gx, nb);
+            ChunkWalk<MAP> walk(total, gx, nb);
             uint32_t it = 0, dst, bar;
             int X, Y, pX = 0, pY = 0;
             bool ok = true, have = false;
             while (ok && !*fail && walk.next(X, Y)) {
                 for (int c = 0; c < nc1; ++c) {
-                    if (!(ok = ring_acquire(ctl, s_stages, it, STAGE_BYTES, dst, bar, fail))) break;
+                    if (!(ok = ring_acquire<NS>(ctl, s_stages, it, STAGE_BYTES, dst, bar, fail))) break;
                     tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
                     tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
                     tma_load_2d(dst + 2 * TILE_BYTES, &mQh, c * KC, X * TN, bar);
@@ -245,23 +273,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (BWD && ok && have) {
                     // GEMM2 operands of the previous tile: X^T of its columns, then of its rows
-                    if ((ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                    if ((ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
                         load_xt(&mTh, &mTl, pX, dst, xt_box, bar);
-                    if (ok && (ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                    if (ok && (ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
                         load_xt(&mTh, &mTl, pY, dst, xt_box, bar);
                 }
                 pX = X; pY = Y; have = true;
             }
             if (BWD && ok && !*fail && have) {
-                if ((ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                if ((ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
                     load_xt(&mTh, &mTl, pX, dst, xt_box, bar);
-                if (ok && (ok = ring_acquire(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
+                if (ok && (ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
                     load_xt(&mTh, &mTl, pY, dst, xt_box, bar);
             }
             // a failed block waits (bounded) for the loads it may have in flight
             if (*fail)
-                for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0; k < it; ++k)
-                    mbar_drain(smem_u32(&ctl.full[k % kStages]), (k / kStages) & 1);
+                for (uint32_t k = it > (uint32_t)NS ? it - NS : 0; k < it; ++k)
+                    mbar_drain(smem_u32(&ctl.full[k % NS]), (k / NS) & 1);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
@@ -269,17 +297,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
-            RangeWalk<MAP> walk(total, gx, nb);
+            ChunkWalk<MAP> walk(total, gx, nb);
             uint32_t it = 0, t = 0, src;
             int X, Y, prevY = -1, prev2Y = -1;
             bool ok = true;
-            // GEMM2 of tile u (its row block continues the previous tile's run if sameY)
+            const int ngx = gx_buffers(NG);
+            uint32_t runs = 0;   // run changes after the first tile
+            // GEMM2 of tile u (its row block continues the previous tile's run if
+            // sameY).  Waits: C tile written; this tile's G_X buffer read out (the
+            // flush of tile u - ngx); G_Y read out when a new run starts.
             auto gemm2 = [&](uint32_t u, bool sameY) -> bool {
                 if (!mbar_wait(smem_u32(&ctl.cready), u & 1, fail, &g_error)) return false;
-                if (u >= 1 && !mbar_wait(smem_u32(&ctl.gfree), (u - 1) & 1, fail, &g_error)) return false;
+                const uint32_t b = u % (uint32_t)ngx;
+                if (u >= (uint32_t)ngx &&
+                    !mbar_wait(smem_u32(&ctl.gxfree[b]), (u / (uint32_t)ngx - 1) & 1, fail, &g_error))
+                    return false;
+                if (u >= 1 && !sameY) {
+                    ++runs;
+                    if (!mbar_wait(smem_u32(&ctl.gyfree), (runs - 1) & 1, fail, &g_error)) return false;
+                }
                 tc_fence_after();
+                const uint32_t tgx = tmem + kGY + (uint32_t)NG * (1 + b);
                 // rows: G_Y (+)= C [X_X | 1], K = j over the two column halves of C
-                if (!ring_take(ctl, s_stages, it, src, fail)) return false;
+                if (!ring_take<NS>(ctl, s_stages, it, src, fail)) return false;
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -293,11 +333,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mma_bf16(tmem + kGY, ah, bl, id_row, 1u);
                         mma_bf16(tmem + kGY, al, bh, id_row, 1u);
                     }
-                mma_commit(smem_u32(&ctl.empty[it % kStages]));
+                mma_commit(smem_u32(&ctl.empty[it % NS]));
                 ++it;
                 // columns: G_X = C^T [X_Y | 1], K = i; A is C read M-major (M = j
                 // over the two 64-column halves, LBO = one half tile apart)
-                if (!ring_take(ctl, s_stages, it, src, fail)) return false;
+                if (!ring_take<NS>(ctl, s_stages, it, src, fail)) return false;
 #pragma unroll
                 for (int ks = 0; ks < TM / 16; ++ks) {
                     const uint64_t ah = sw128_desc(s_c + ks * 2048, TILE_BYTES, 1024);
@@ -305,11 +345,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t hb = (uint32_t)(ks >> 2), kb = (uint32_t)(ks & 3) * 32;
                     const uint64_t bh = sw128_desc(src + hb * xt_box + kb);
                     const uint64_t bl = sw128_desc(src + (2 + hb) * xt_box + kb);
-                    mma_bf16(tmem + kGX, ah, bh, id_col, ks ? 1u : 0u);
-                    mma_bf16(tmem + kGX, ah, bl, id_col, 1u);
-                    mma_bf16(tmem + kGX, al, bh, id_col, 1u);
+                    mma_bf16(tgx, ah, bh, id_col, ks ? 1u : 0u);
+                    mma_bf16(tgx, ah, bl, id_col, 1u);
+                    mma_bf16(tgx, al, bh, id_col, 1u);
                 }
-                mma_commit(smem_u32(&ctl.empty[it % kStages]));
+                mma_commit(smem_u32(&ctl.empty[it % NS]));
                 ++it;
                 mma_commit(smem_u32(&ctl.g2done));
                 return true;
@@ -320,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t dtm = tmem + acc * TN;
                 for (int c = 0; c < nc1; ++c) {
-                    if (!(ok = ring_take(ctl, s_stages, it, src, fail))) break;
+                    if (!(ok = ring_take<NS>(ctl, s_stages, it, src, fail))) break;
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ++ks) {
                         const uint32_t ko = ks * 32;
@@ -332,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mma_bf16(dtm, ah, bl, id1, 1u);
                         mma_bf16(dtm, al, bh, id1, 1u);
                     }
-                    mma_commit(smem_u32(&ctl.empty[it % kStages]));
+                    mma_commit(smem_u32(&ctl.empty[it % NS]));
                     ++it;
                 }
                 if (!ok) break;
@@ -354,9 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = ew >> 2;                // columns [64*half, 64*half + 64)
         const int r = 32 * quarter + lane;       // this thread's row in the tile
         float *ac = &ctl.acol[ew][0];
+        const int ngx = gx_buffers(NG);
         unsigned char *rowh = cbuf + half * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128;
         unsigned char *rowl = rowh + 2 * TILE_BYTES;
-        RangeWalk<MAP> walk(total, gx, nb);
+        ChunkWalk<MAP> walk(total, gx, nb);
         uint32_t t = 0;
         int X, Y, pX = 0, pY = 0;
         while (!*fail && walk.next(X, Y)) {
@@ -429,11 +470,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive(smem_u32(&ctl.cready));
                 if (t >= 1) {
                     // the previous tile's sides: its columns always, its rows at the end of a run
-                    flush_g(tmem, kGX, pX, quarter, half, lane, d, n, scale4, x, grad);
-                    if (Y != pY) flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
+                    const uint32_t pb = (t - 1) % (uint32_t)ngx;
+                    flush_g(tmem, kGY + NG * (1 + pb), pX, quarter, half, lane, d, n, scale4, x, grad);
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&ctl.gfree));
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl.gxfree[pb]));
+                    if (Y != pY) {
+                        flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&ctl.gyfree));
+                    }
                 }
             }
             pX = X;
@@ -443,7 +490,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (BWD && !*fail && t >= 1 &&
             mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) {
             tc_fence_after();
-            flush_g(tmem, kGX, pX, quarter, half, lane, d, n, scale4, x, grad);
+            flush_g(tmem, kGY + NG * (1 + (t - 1) % (uint32_t)ngx), pX, quarter, half, lane, d, n, scale4,
+                    x, grad);
             flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
         }
     }
@@ -622,7 +670,8 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
     const int64_t total = g.gx * g.gy;
-    int64_t ctas = total < sms ? total : sms;
+    const int64_t chunks = (total + kChunk - 1) / kChunk;
+    int64_t ctas = chunks < sms ? chunks : sms;
     if (ctas > kMaxCtas) ctas = kMaxCtas;
     if (bwd && (st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s))))
         return st;
