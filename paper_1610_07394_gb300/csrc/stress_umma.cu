@@ -88,27 +88,54 @@ static_assert(offsetof(Ctl, acol) % 16 == 0, "float4 reads of a_j");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
 static_assert(kMaxStages * STAGE_BYTES <= kStages * STAGE_BYTES + C_BYTES, "forward ring fits");
 
-// The tiles a CTA handles: the map's grid (gx x gy, x fastest) cut into
-// chunks of kChunk consecutive grid blocks, chunk c to CTA c mod gridDim.x;
-// each grid block maps to zero, one or two tiles.  Along a grid row the row
+// The tiles a CTA handles: the map's grid (gx x gy, x fastest) cut into C
+// chunks of kChunk consecutive grid blocks; CTA b takes the chunks pi(c) for
+// c = b, b + gridDim.x, ..., with pi a fixed pseudo-random permutation of
+// [0, C) (chunk_perm), so that no CTA keeps drawing the same position within
+// the map's rows; each grid block maps to zero, one or two tiles.  Along a grid row the row
 // block Y stays fixed for runs of tiles (with the lambda map for
 // 2^floor(log2 wy) consecutive grid blocks of row wy), so within a chunk
 // G_Y accumulates over runs of up to kChunk tiles, while interleaving the
-// chunks spreads the map's uneven parts (the diagonal-pair row of lambda,
-// the empty upper half of the bounding box) evenly over the CTAs.
+// scattered chunks spreads the map's uneven parts (the diagonal-pair row of
+// lambda, the empty upper half of the bounding box) evenly over the CTAs.
 constexpr int kChunk = 32;
+
+// A permutation of [0, C): a three-round Feistel network on 2h bits
+// (2^(2h) >= C), applied again while the value is >= C (cycle walking, at
+// most a few rounds since 2^(2h) < 4C).
+__device__ __forceinline__ uint32_t feistel(uint32_t v, int h) {
+    const uint32_t mask = (1u << h) - 1u;
+    uint32_t L = v >> h, R = v & mask;
+#pragma unroll
+    for (uint32_t r = 0; r < 3; ++r) {
+        const uint32_t f = ((R + r * 0x632BE5ABu) * 0x9E3779B1u) >> 11;
+        const uint32_t t = L ^ (f & mask);
+        L = R;
+        R = t;
+    }
+    return (L << h) | R;
+}
+
+__device__ __forceinline__ int64_t chunk_perm(int64_t c, int64_t C) {
+    int h = 1;
+    while ((int64_t(1) << (2 * h)) < C) ++h;
+    uint32_t v = feistel((uint32_t)c, h);
+    while ((int64_t)v >= C) v = feistel(v, h);
+    return v;
+}
 
 template <int MAP>
 struct ChunkWalk {
-    int64_t c, w, end, total;
+    int64_t c, w, end, total, nchunks;
     int wx, wy, gx, nb;
     int pend, px, py;
     __device__ ChunkWalk(int64_t total_, int gx_, int nb_)
-        : c(blockIdx.x), total(total_), gx(gx_), nb(nb_), pend(0), px(0), py(0) {
+        : c(blockIdx.x), total(total_), nchunks((total_ + kChunk - 1) / kChunk), gx(gx_), nb(nb_),
+          pend(0), px(0), py(0) {
         open();
     }
     __device__ void open() {
-        w = c * kChunk;
+        w = c < nchunks ? chunk_perm(c, nchunks) * kChunk : total;
         end = w + kChunk < total ? w + kChunk : total;
         wy = (int)(w / gx);
         wx = (int)(w - (int64_t)wy * gx);
@@ -118,7 +145,7 @@ struct ChunkWalk {
         for (;;) {
             if (w >= end) {
                 c += gridDim.x;
-                if (c * kChunk >= total) return false;
+                if (c >= nchunks) return false;
                 open();
                 continue;
             }
