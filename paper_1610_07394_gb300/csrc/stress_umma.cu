@@ -224,6 +224,16 @@ __device__ __forceinline__ void flush_g(uint32_t tmem, uint32_t gcol, int B, int
     }
 }
 
+// a = S . Delta of a tile's columns col0 + 64 half + lane and + 32 (ca, cb)
+// and of its row row0 + r (ri), for one epilogue thread; 0 past n.
+__device__ __forceinline__ void load_a(const float *__restrict__ a, int64_t n, int X, int Y, int half,
+                                       int r, int lane, float &ca, float &cb, float &ri) {
+    const int64_t j0 = (int64_t)X * TN + 64 * half + lane, j1 = j0 + 32, i = (int64_t)Y * TM + r;
+    ca = j0 < n ? __ldg(a + j0) : 0.0f;
+    cb = j1 < n ? __ldg(a + j1) : 0.0f;
+    ri = i < n ? __ldg(a + i) : 0.0f;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t *>(&h);
@@ -427,19 +437,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         ChunkWalk<MAP> walk(total, gx, nb);
         uint32_t t = 0;
         int X, Y, pX = 0, pY = 0;
-        while (!*fail && walk.next(X, Y)) {
+        bool have = walk.next(X, Y);
+        // a of the current tile's columns (va, vb) and row (vi), loaded a tile ahead
+        float va = 0.f, vb = 0.f, vi = 0.f;
+        if (have) load_a(a, n, X, Y, half, r, lane, va, vb, vi);
+        while (have && !*fail) {
+            int Xn, Yn;
+            const bool hn = walk.next(Xn, Yn);
+            float na = 0.f, nbv = 0.f, ni = 0.f;
+            if (hn) load_a(a, n, Xn, Yn, half, r, lane, na, nbv, ni);
             const uint32_t acc = t & 1, aph = (t >> 1) & 1;
             const int64_t row0 = (int64_t)Y * TM, jb = (int64_t)X * TN + 64 * half;
-            {
-                const int64_t j0 = jb + lane, j1 = j0 + 32;
-                const float va = j0 < n ? __ldg(a + j0) : 0.0f;
-                const float vb = j1 < n ? __ldg(a + j1) : 0.0f;
-                __syncwarp();   // the previous tile's reads of ac are done
-                ac[lane] = va;
-                ac[lane + 32] = vb;
-            }
+            __syncwarp();   // the previous tile's reads of ac are done
+            ac[lane] = va;
+            ac[lane + 32] = vb;
             const int64_t i = row0 + r;
-            const float ai = i < n ? __ldg(a + i) : 0.0f;
+            const float ai = vi;
             // valid columns q < lim: j < n, and j < i on a diagonal tile
             int64_t lim64 = i < n ? n - jb : 0;
             if (X == Y && i - jb < lim64) lim64 = i - jb;
@@ -451,8 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             {
                 float v0[32], v1[32];
                 const uint32_t taddr = tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * half);
-                tmem_ld32(taddr, v0);
-                tmem_ld32(taddr + 32, v1);
+                tmem_ld64(taddr, v0, v1);
 #pragma unroll
                 for (int q = 0; q < 32; ++q) { v[q] = v0[q]; v[32 + q] = v1[q]; }
             }
@@ -512,6 +524,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             pX = X;
             pY = Y;
+            X = Xn; Y = Yn; have = hn;
+            va = na; vb = nbv; vi = ni;
             ++t;
         }
         if (BWD && !*fail && t >= 1 &&
