@@ -46,7 +46,7 @@ NU, EPS = 1.0, 1e-4
 # (2), R^3 = r_ij^3 r_ik^3 r_jk^3 (2), the bracket 1 + 3 cos cos cos (2, one
 # FMA) and the running sum (1): 22 flops.
 FLOPS_PER_TRIPLE = 22
-ROWS_NAMES = ("edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
+ROWS_NAMES = ("cover2_n16384", "cover3_n1024", "edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
               "stress_n65536_d64", "edm_n16384_d64", "stress_n16384_d64")
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one k_atm_energy_tab<lambda> launch on this
@@ -429,7 +429,39 @@ def row_stress_n16384_d64(torch, sx, peaks):
     return _stress_tensor(torch, sx, peaks, x, y, ("lambda",))
 
 
+def _cover_row(torch, sx, m, n, rho):
+    """Coverage of the m-simplex with one thread per element: each map's grid
+    launched as is, every thread decoding its block and counting its element
+    (an atomic increment) or itself as idle.  The per-element work is one
+    atomic, so here the threads a map launches outside the simplex weigh as
+    much as the work itself (the parallel space of Sec. III)."""
+    vol = n * (n + 1) // 2 if m == 2 else n * (n + 1) * (n + 2) // 6
+    count = torch.empty(vol, dtype=torch.int32, device="cuda")
+    idle = torch.empty(1, dtype=torch.int64, device="cuda")
+    fn = sx.simplex_map2 if m == 2 else sx.simplex_map3
+    r = {"unit": "elements/s", "elements": vol, "rho": rho}
+    for mp in ("lambda", "bbox", "linear"):
+        ms = _median_ms(torch, lambda: fn(n, rho, mp, count, idle), 5)
+        r[mp] = vol / (ms / 1e3)
+        r[mp + "_ms"] = ms
+        r[mp + "_idle_threads"] = int(idle.item())
+    r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    return r
+
+
+def row_cover2_n16384(torch, sx, peaks):
+    """Coverage of the 2-simplex, n=16384, 16x16 threads per block."""
+    return _cover_row(torch, sx, 2, 16384, 16)
+
+
+def row_cover3_n1024(torch, sx, peaks):
+    """Coverage of the 3-simplex, n=1024, 8x8x8 threads per block."""
+    return _cover_row(torch, sx, 3, 1024, 8)
+
+
 ROWS = {
+    "cover2_n16384": row_cover2_n16384,
+    "cover3_n1024": row_cover3_n1024,
     "edm_n1024_d3": row_edm_n1024_d3,
     "edm_n32768_d256": row_edm_n32768_d256,
     "edm_n65536_d64": row_edm_n65536_d64,

@@ -133,6 +133,11 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
     AtmEnergySmem &S = *reinterpret_cast<AtmEnergySmem *>(smem_raw);
     __shared__ float red[16];
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    if (L.cnt == 0) {   // a block outside the simplex exits at once
+        if (threadIdx.x == 0)
+            partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
+        return;
+    }
     const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
     float hi = 0.f, lo = 0.f;
 #pragma unroll 1
@@ -260,6 +265,11 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
     AtmEnergyTabSmem &S = *reinterpret_cast<AtmEnergyTabSmem *>(smem_raw);
     __shared__ float red[16];
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    if (L.cnt == 0) {   // a block outside the simplex exits at once
+        if (threadIdx.x == 0)
+            partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
+        return;
+    }
     const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
     const uint32_t bar = umma::smem_u32(&S.bar);
     if (threadIdx.x == 0) {
@@ -461,6 +471,11 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
     AtmForceSmem &S = *reinterpret_cast<AtmForceSmem *>(smem_raw);
     __shared__ float red[16];
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    if (L.cnt == 0) {   // a block outside the simplex exits at once
+        if (partials && threadIdx.x == 0)
+            partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
+        return;
+    }
     const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4, lane = tid & 31;
     float hi = 0.f, lo = 0.f;
 #pragma unroll 1

@@ -120,6 +120,10 @@ __global__ void __launch_bounds__(256) k_stress_fwd(int64_t n, int d, const floa
     __shared__ TileSmem dsm;
     __shared__ float red[16];
     const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
+    if (L.cnt == 0) {   // a block outside the simplex exits at once
+        if (threadIdx.x == 0) partials[blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = 0.0;
+        return;
+    }
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     float hi = 0.f, lo = 0.f;
 #pragma unroll 1

@@ -89,13 +89,14 @@ static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
 static_assert(kMaxStages * STAGE_BYTES <= kStages * STAGE_BYTES + C_BYTES, "forward ring fits");
 
 // The tiles a CTA handles: the map's grid (gx x gy, x fastest) cut into C
-// chunks of kChunk consecutive grid blocks; CTA b takes the chunks pi(c) for
+// chunks of `chunk` consecutive grid blocks (up to kChunk, smaller when the
+// grid would give a CTA fewer than four chunks); CTA b takes the chunks pi(c) for
 // c = b, b + gridDim.x, ..., with pi a fixed pseudo-random permutation of
 // [0, C) (chunk_perm), so that no CTA keeps drawing the same position within
 // the map's rows; each grid block maps to zero, one or two tiles.  Along a grid row the row
 // block Y stays fixed for runs of tiles (with the lambda map for
 // 2^floor(log2 wy) consecutive grid blocks of row wy), so within a chunk
-// G_Y accumulates over runs of up to kChunk tiles, while interleaving the
+// G_Y accumulates over runs of up to `chunk` tiles, while interleaving the
 // scattered chunks spreads the map's uneven parts (the diagonal-pair row of
 // lambda, the empty upper half of the bounding box) evenly over the CTAs.
 constexpr int kChunk = 32;
@@ -127,16 +128,16 @@ __device__ __forceinline__ int64_t chunk_perm(int64_t c, int64_t C) {
 template <int MAP>
 struct ChunkWalk {
     int64_t c, w, end, total, nchunks;
-    int wx, wy, gx, nb;
+    int wx, wy, gx, nb, chunk;
     int pend, px, py;
-    __device__ ChunkWalk(int64_t total_, int gx_, int nb_)
-        : c(blockIdx.x), total(total_), nchunks((total_ + kChunk - 1) / kChunk), gx(gx_), nb(nb_),
-          pend(0), px(0), py(0) {
+    __device__ ChunkWalk(int64_t total_, int gx_, int nb_, int chunk_)
+        : c(blockIdx.x), total(total_), nchunks((total_ + chunk_ - 1) / chunk_), gx(gx_), nb(nb_),
+          chunk(chunk_), pend(0), px(0), py(0) {
         open();
     }
     __device__ void open() {
-        w = c < nchunks ? chunk_perm(c, nchunks) * kChunk : total;
-        end = w + kChunk < total ? w + kChunk : total;
+        w = c < nchunks ? chunk_perm(c, nchunks) * chunk : total;
+        end = w + chunk < total ? w + chunk : total;
         wy = (int)(w / gx);
         wx = (int)(w - (int64_t)wy * gx);
     }
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                   const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
                   const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
-                  int gx, int64_t total, float scale4, float *__restrict__ grad,
+                  int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
                   double *__restrict__ partials) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            ChunkWalk<MAP> walk(total, gx, nb);
+            ChunkWalk<MAP> walk(total, gx, nb, chunk);
             uint32_t it = 0, dst, bar;
             int X, Y, pX = 0, pY = 0;
             bool ok = true, have = false;
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
-            ChunkWalk<MAP> walk(total, gx, nb);
+            ChunkWalk<MAP> walk(total, gx, nb, chunk);
             uint32_t it = 0, t = 0, src;
             int X, Y, prevY = -1, prev2Y = -1;
             bool ok = true;
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ngx = gx_buffers(NG);
         unsigned char *rowh = cbuf + half * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128;
         unsigned char *rowl = rowh + 2 * TILE_BYTES;
-        ChunkWalk<MAP> walk(total, gx, nb);
+        ChunkWalk<MAP> walk(total, gx, nb, chunk);
         uint32_t t = 0;
         int X, Y, pX = 0, pY = 0;
         bool have = walk.next(X, Y);
@@ -643,17 +644,17 @@ static int smem_optin() {
 
 template <bool BWD>
 static void launch(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
-                   const float *a, int64_t n, int d, int nb, int gx, int64_t total, float scale4,
-                   float *grad, double *partials) {
+                   const float *a, int64_t n, int d, int nb, int gx, int64_t total, int chunk,
+                   float scale4, float *grad, double *partials) {
     if (map == MAP_LAMBDA)
         k_stress_umma<MAP_LAMBDA, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
     else if (map == MAP_BBOX)
         k_stress_umma<MAP_BBOX, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
     else
         k_stress_umma<MAP_LINEAR, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
 }
 
 }  // namespace summa
@@ -711,18 +712,21 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
     const int64_t total = g.gx * g.gy;
-    const int64_t chunks = (total + kChunk - 1) / kChunk;
+    // chunks of up to kChunk grid blocks, at least four per CTA where the grid allows
+    int64_t chunk = total / (4 * (int64_t)sms);
+    chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
+    const int64_t chunks = (total + chunk - 1) / chunk;
     int64_t ctas = chunks < sms ? chunks : sms;
     if (ctas > kMaxCtas) ctas = kMaxCtas;
     if (bwd && (st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s))))
         return st;
     prof_begin(s);
     if (bwd)
-        launch<true>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total,
+        launch<true>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
                      (float)(4.0 * gscale), grad, nullptr);
     else
-        launch<false>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, 0.f,
-                      nullptr, partials);
+        launch<false>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
+                      0.f, nullptr, partials);
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;
