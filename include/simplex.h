@@ -214,8 +214,10 @@ int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map, int prec)
  * framework whose caching allocator owns the device memory (a side
  * cudaMalloc can fail or fragment that pool), or a latency-critical loop
  * that must not call cudaMalloc/cudaFree because they can synchronise the
- * device.  The paper has no counterpart; this is a packaging of the same
- * kernels (identical results to simplex_atm_energy).
+ * device.  The paper has no counterpart.  It runs the energy kernel that
+ * builds its pair tables per tile (simplex_atm_energy precomputes them into
+ * its workspace), so the two agree to FP32 rounding (well within 1e-6
+ * relative), not bit for bit.
  *
  * Scratch is a fixed 4 MiB array inside the library (one FP64 per grid block
  * plus 1024 reduction slots), held by every GPU that loads the library until

@@ -118,6 +118,23 @@ __device__ __forceinline__ void triple_energy2(const float2 (&uij)[3], float4 C0
     acc = __ffma2_rn(__fmul2_rn(cw, bw), t, acc);
 }
 
+// Two triples (i0, j, k), (i1, j, k) in the two lanes, from the scaled
+// vectors v = r^(3/2) u of the pair tables:
+//   s0 += r_ik^3 r_jk^3,
+//   s1 += (v_ij.v_ik)(v_ij.v_jk)(v_ik.v_jk) = r_ij^3 r_ik^3 r_jk^3 (u_ij.u_ik)(u_ij.u_jk)(u_ik.u_jk),
+// so that the energy of the pair (i, j) over its k is r_ij^3 s0 - 3 s1
+// (cos g_j = -u_ij.u_jk).  12 packed FP32x2 operations.
+__device__ __forceinline__ void triple_energy2s(const float2 (&vij)[3], float4 C0, float4 C1,
+                                                float4 B0, float4 B1, float2 &s0, float2 &s1) {
+    const float2 cx = lo2(C0), cy = hi2(C0), cz = lo2(C1), cw = hi2(C1);
+    const float2 bx = lo2(B0), by = hi2(B0), bz = lo2(B1), bw = hi2(B1);
+    const float2 ci = __ffma2_rn(vij[0], cx, __ffma2_rn(vij[1], cy, __fmul2_rn(vij[2], cz)));
+    const float2 cj = __ffma2_rn(vij[0], bx, __ffma2_rn(vij[1], by, __fmul2_rn(vij[2], bz)));
+    const float2 ck = __ffma2_rn(cx, bx, __ffma2_rn(cy, by, __fmul2_rn(cz, bz)));
+    s1 = __ffma2_rn(__fmul2_rn(ci, cj), ck, s1);
+    s0 = __ffma2_rn(cw, bw, s0);
+}
+
 // The (up to two) data blocks of a grid block, read without dynamic indexing.
 __device__ __forceinline__ void block_of(const List3 &L, int t, int &I, int &J, int &K) {
     I = t ? L.i[1] : L.i[0];
@@ -192,17 +209,26 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
 // blocks, computed once per call instead of once per tile: for the pairs
 // (a in B1, b in B2), in the layout of AtmEnergySmem so that a tile copies
 // them into shared memory as they are (one bulk copy each),
-//   ec form [b][0][t] = (u0.x, u1.x, u0.y, u1.y), [b][1][t] = (u0.z, u1.z, r0^3, r1^3)
+//   ec form [b][0][t] = (v0.x, v1.x, v0.y, v1.y), [b][1][t] = (v0.z, v1.z, r0^3, r1^3)
 //           with pairs (a = t, b) -> 0 and (a = t + 16, b) -> 1;
-//   eb form [b][h][0][t] = (u.x, u.x, u.y, u.y), [b][h][1][t] = (u.z, u.z, r^3, r^3)
+//   eb form [b][h][0][t] = (v.x, v.x, v.y, v.y), [b][h][1][t] = (v.z, v.z, r^3, r^3)
 //           of the pair (a = t + 16h, b);
-// u the unit vector from x_a to x_b, r^3 = (|x_b - x_a|^2 + eps)^-3/2, all
-// zero unless a < b < n.  A tile (I, J, K) takes the ec form of (I, K), the
-// eb form of (J, K) and its pair constants from the ec form of (I, J).
+// r^3 = (|x_b - x_a|^2 + eps)^-3/2 and v = r^(3/2) u, u = r (x_b - x_a), all
+// zero unless a < b < n.  With the scaled vectors the product of the three
+// dot products of a triple is r_ij^3 r_ik^3 r_jk^3 (u_ij.u_ik)(u_ij.u_jk)(u_ik.u_jk)
+// directly (triple_energy2s).  A tile (I, J, K) takes the ec form of (I, K),
+// the eb form of (J, K) and its pair constants from the ec form of (I, J).
 constexpr int kTabEc = R_ * 2 * 16;                // float4 of the ec form (16 KB)
 constexpr int kTabEb = R_ * 2 * 2 * 16;            // float4 of the eb form (32 KB)
 constexpr int kTabPair = kTabEc + kTabEb;          // float4 per block pair (48 KB)
 constexpr int64_t kTabMaxBytes = int64_t(8) << 30; // larger tables: per-tile tables instead
+
+// (r^(3/2) u, r^3) of the edge from -> to, zero outside the simplex.
+__device__ __forceinline__ float4 scaled_pair_term(float4 from, float4 to, bool valid, float eps) {
+    const float4 c = pair_term(from, to, valid, eps);
+    const float h = sqrtf(c.w);
+    return make_float4(c.x * h, c.y * h, c.z * h, c.w);
+}
 
 __host__ __device__ inline int64_t pair_slot(int B1, int B2) {
     return (int64_t)B2 * (B2 + 1) / 2 + B1;
@@ -233,8 +259,8 @@ __global__ void __launch_bounds__(256) k_atm_pairtab(int64_t n, const float *__r
         for (int e = tid; e < R_ * 16; e += 256) {
             const int b = e >> 4, a = e & 15;
             const int64_t gb = (int64_t)B2 * R_ + b, ga = (int64_t)B1 * R_ + a;
-            const float4 u0 = pair_term(xs[0][a], xs[1][b], ga < gb && gb < n, eps);
-            const float4 u1 = pair_term(xs[0][a + 16], xs[1][b], ga + 16 < gb && gb < n, eps);
+            const float4 u0 = scaled_pair_term(xs[0][a], xs[1][b], ga < gb && gb < n, eps);
+            const float4 u1 = scaled_pair_term(xs[0][a + 16], xs[1][b], ga + 16 < gb && gb < n, eps);
             ec[(2 * b) * 16 + a] = make_float4(u0.x, u1.x, u0.y, u1.y);
             ec[(2 * b + 1) * 16 + a] = make_float4(u0.z, u1.z, u0.w, u1.w);
             eb[(4 * b + 0) * 16 + a] = make_float4(u0.x, u0.x, u0.y, u0.y);
@@ -255,8 +281,8 @@ struct AtmEnergyTabSmem {
 
 // The energy kernel fed by the pair tables: per tile, one thread starts two
 // bulk copies (48 KB) into shared memory, every thread reads its pair
-// constants from the (I, J) table meanwhile, then the packed triple loop of
-// k_atm_energy runs unchanged.
+// constants (v_ij, r_ij^3) from the (I, J) table meanwhile, then a packed
+// triple loop over the scaled vectors (triple_energy2s).
 template <int MAP>
 __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
                                                            int nb, int p,
@@ -291,17 +317,17 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
             umma::bulk_load(umma::smem_u32(&S.eb[0][0][0][0]), tab + pair_slot(J, K) * kTabPair + kTabEc,
                             kTabEb * 16, bar);
         }
-        // pair constants of (i, j): the ec form of (I, J) at b = j
+        // pair constants of (i, j), v_ij and r_ij^3: the ec form of (I, J) at b = j
         const float4 *pij = tab + pair_slot(I, J) * kTabPair;
-        float2 uij[2][3];
+        float2 vij[2][3];
         float ra3[2][2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int j = tj + 16 * q;
             const float4 a = __ldg(pij + (2 * j) * 16 + ti), b = __ldg(pij + (2 * j + 1) * 16 + ti);
-            uij[q][0] = make_float2(a.x, a.y);
-            uij[q][1] = make_float2(a.z, a.w);
-            uij[q][2] = make_float2(b.x, b.y);
+            vij[q][0] = make_float2(a.x, a.y);
+            vij[q][1] = make_float2(a.z, a.w);
+            vij[q][2] = make_float2(b.x, b.y);
             ra3[0][q] = b.z;
             ra3[1][q] = b.w;
         }
@@ -318,19 +344,20 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
                 }
             }
         }
-        float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+        float2 s00 = make_float2(0.f, 0.f), s01 = make_float2(0.f, 0.f);
+        float2 s10 = make_float2(0.f, 0.f), s11 = make_float2(0.f, 0.f);
 #pragma unroll 4
         for (int k = 0; k < R_; ++k) {
             const float4 C0 = S.ec[k][0][ti], C1 = S.ec[k][1][ti];
             const float4 B00 = S.eb[k][0][0][tj], B01 = S.eb[k][0][1][tj];
             const float4 B10 = S.eb[k][1][0][tj], B11 = S.eb[k][1][1][tj];
-            triple_energy2(uij[0], C0, C1, B00, B01, acc0);
-            triple_energy2(uij[1], C0, C1, B10, B11, acc1);
+            triple_energy2s(vij[0], C0, C1, B00, B01, s00, s10);
+            triple_energy2s(vij[1], C0, C1, B10, B11, s01, s11);
         }
-        add_ff(hi, lo, acc0.x * ra3[0][0], 0.f);
-        add_ff(hi, lo, acc0.y * ra3[1][0], 0.f);
-        add_ff(hi, lo, acc1.x * ra3[0][1], 0.f);
-        add_ff(hi, lo, acc1.y * ra3[1][1], 0.f);
+        add_ff(hi, lo, fmaf(ra3[0][0], s00.x, -3.0f * s10.x), 0.f);
+        add_ff(hi, lo, fmaf(ra3[1][0], s00.y, -3.0f * s10.y), 0.f);
+        add_ff(hi, lo, fmaf(ra3[0][1], s01.x, -3.0f * s11.x), 0.f);
+        add_ff(hi, lo, fmaf(ra3[1][1], s01.y, -3.0f * s11.y), 0.f);
     }
     const bool any_bad = __syncthreads_or(bad) != 0;
     const double s = block_sum_ff<256>(hi, lo, red);

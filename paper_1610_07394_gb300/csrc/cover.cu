@@ -39,6 +39,16 @@ __global__ void k_map_blocks(int map, Grid g, int nb, int64_t total, int32_t *ou
         table_entry<M>(map, g, nb, w, out + 2 * M * w);
 }
 
+// Adds this warp's idle threads to the block's count: one vote, one atomic
+// per warp (all of the warp's threads reach this point together; a block's
+// last warp may be partial).
+__device__ __forceinline__ void count_idle(bool took, unsigned int *s_idle) {
+    const unsigned active = __activemask();
+    const unsigned idle_lanes = __ballot_sync(active, !took);
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    if ((tid & 31) == __ffs(active) - 1 && idle_lanes) atomicAdd(s_idle, (unsigned)__popc(idle_lanes));
+}
+
 // One thread per (r, c) of a rho x rho block; see simplex_map2 in simplex.h.
 template <int MAP>
 __global__ void k_cover2(int64_t n, int rho, int nb, int32_t *count,
@@ -62,7 +72,7 @@ __global__ void k_cover2(int64_t n, int rho, int nb, int32_t *count,
         const int64_t i = (int64_t)L.y[0] * rho + r, j = (int64_t)L.x[0] * rho + c;
         if (j <= i && i < n) { atomicAdd(count + (i * (i + 1) / 2 + j), 1); took = true; }
     }
-    if (!took) atomicAdd(&s_idle, 1u);
+    count_idle(took, &s_idle);
     __syncthreads();
     if (r == 0 && c == 0 && s_idle) atomicAdd(idle, (unsigned long long)s_idle);
 }
@@ -87,7 +97,7 @@ __global__ void k_cover3(int64_t n, int rho, int nb, int p, int32_t *count,
             took = true;
         }
     }
-    if (!took) atomicAdd(&s_idle, 1u);
+    count_idle(took, &s_idle);
     __syncthreads();
     if (lead && s_idle) atomicAdd(idle, (unsigned long long)s_idle);
 }
