@@ -15,6 +15,25 @@ __global__ void __launch_bounds__(256) k_edm_simt(int64_t n, int d, const float 
     __shared__ TileSmem sm;
     const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (L.pair && L.cnt == 2) {
+        // the two diagonal blocks of lambda's grid row 0 in one packed pass
+        const int64_t b0 = (int64_t)L.d0 * kEdmRho, b1 = (int64_t)L.d1 * kEdmRho;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        pair_sqdist(x, n, d, b0, b1, sm, acc);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = w + 8 * m;
+            const bool first = lane <= r;
+            const int64_t i = first ? b0 + r : b1 + 31 - r;
+            const int64_t j = first ? b0 + lane : b1 + lane - r - 1;
+            if (i < n) out[i * (i + 1) / 2 + j] = acc[m];
+        }
+        if (w == 0 && b1 + lane < n) {
+            const int64_t i = b1 + lane;
+            out[i * (i + 1) / 2 + i] = 0.0f;   // the second block's diagonal
+        }
+        return;
+    }
     for (int t = 0; t < L.cnt; ++t) {
         const int64_t row0 = (int64_t)L.y[t] * kEdmRho, col0 = (int64_t)L.x[t] * kEdmRho;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};

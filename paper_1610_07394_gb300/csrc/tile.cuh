@@ -46,6 +46,38 @@ __device__ __forceinline__ void tile_sqdist(const float *__restrict__ x, int64_t
     }
 }
 
+// A diagonal block pair (blocks at b0 and b1, b0 < b1) packed into one
+// 32 x 33 rectangle, as the 2-simplex map pairs them in its grid row 0:
+// element (r, c), c <= r, is (i, j) = (b0 + r, b0 + c) of the first block's
+// lower triangle; c > r is (b1 + 31 - r, b1 + c - r - 1) of the second's
+// strictly lower triangle (its diagonal, column 32, is zero).  acc[m] +=
+// |x_i - x_j|^2 for rows r = w + 8m and column c = lane; the first block's
+// points are staged in sm.rows, the second's in sm.cols.
+__device__ __forceinline__ void pair_sqdist(const float *__restrict__ x, int64_t n, int d,
+                                            int64_t b0, int64_t b1, TileSmem &sm, float acc[4]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < d; c0 += 32) {
+        const int dc = d - c0 < 32 ? d - c0 : 32;
+        __syncthreads();
+        load_chunk(x, n, d, b0, c0, dc, sm.rows);
+        load_chunk(x, n, d, b1, c0, dc, sm.cols);
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int r = w + 8 * m;
+            const bool first = lane <= r;
+            const float *pi = first ? &sm.rows[r][0] : &sm.cols[31 - r][0];
+            const float *pj = first ? &sm.rows[lane][0] : &sm.cols[lane - r - 1][0];
+            float a = acc[m];
+            for (int cc = 0; cc < dc; ++cc) {
+                const float diff = pi[cc] - pj[cc];
+                a = fmaf(diff, diff, a);
+            }
+            acc[m] = a;
+        }
+    }
+}
+
 }  // namespace sx
 
 namespace sx {
