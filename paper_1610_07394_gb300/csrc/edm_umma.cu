@@ -24,6 +24,7 @@
 // bounded in time; a wait that runs out sets a device error flag
 // (simplex_device_errors) and the block stops instead of hanging.
 #include <cstddef>
+#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -111,7 +112,7 @@ struct TileWalk {
     int64_t w, total;   // linear grid-block index (x fastest) and grid size
     int wx, wy, gx, nb;
     int pend, px, py;   // second tile of a diagonal pair, still to visit
-    __device__ TileWalk(int gx_, int64_t total_, int nb_)
+    __device__ TileWalk(int gx_, int64_t total_, int /* super-blocks: unused */, int nb_)
         : w(blockIdx.x), total(total_), gx(gx_), nb(nb_), pend(0), px(0), py(0) {
         wy = (int)(blockIdx.x / (unsigned)gx_);
         wx = (int)(blockIdx.x - (unsigned)wy * (unsigned)gx_);
@@ -132,6 +133,65 @@ struct TileWalk {
         }
         return false;
     }
+    __device__ bool next(int &X, int &Y, bool &valid) {
+        valid = true;
+        return next(X, Y);
+    }
+};
+
+// The tiles of one CTA of a two-CTA cluster.  The map runs over the 2-simplex
+// of 256 x 256 super-blocks (nb2 = ceil(nb / 2)); the cluster takes the grid
+// blocks w = c, c + clusters, ... (c its index) and each super-block (sX, sY)
+// gives both CTAs two steps in lockstep: CTA rank r the column block
+// X = 2 sX + r, step s the row block Y = 2 sY + s.  Both CTAs need the same row
+// block at every step, so its operand tiles are loaded once for the pair (TMA
+// multicast).  A step whose tile lies above the diagonal or past the last
+// block (the second column block of a diagonal super-block at s = 0; row
+// blocks past nb when nb is odd) is still computed, to keep the lockstep,
+// and is marked invalid: nothing is written.
+template <int MAP>
+struct PairWalk {
+    int64_t w, total;
+    int wx, wy, gx, nb2, nb, step, sX, sY, pend, px, py;
+    uint32_t rank, stride;
+    __device__ PairWalk(int gx_, int64_t total_, int nb2_, int nb_)
+        : total(total_), gx(gx_), nb2(nb2_), nb(nb_), step(2), sX(0), sY(0), pend(0), px(0),
+          py(0) {
+        rank = cluster_rank();
+        stride = gridDim.x >> 1;
+        w = blockIdx.x >> 1;
+        wy = (int)(w / gx_);
+        wx = (int)(w - (int64_t)wy * gx_);
+    }
+    __device__ bool next(int &X, int &Y, bool &valid) {
+        if (step >= 2) {
+            if (pend) {
+                pend = 0;
+                sX = px; sY = py;
+            } else {
+                bool found = false;
+                while (w < total) {
+                    const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
+                                                      : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
+                    w += stride;
+                    wx += (int)stride;
+                    while (wx >= gx) { wx -= gx; ++wy; }
+                    if (L.cnt == 0) continue;
+                    sX = L.x[0]; sY = L.y[0];
+                    if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
+                    found = true;
+                    break;
+                }
+                if (!found) return false;
+            }
+            step = 0;
+        }
+        X = 2 * sX + (int)rank;
+        Y = 2 * sY + step;
+        ++step;
+        valid = X <= Y && Y < nb;
+        return true;
+    }
 };
 
 // Norms of a tile's rows and columns for one epilogue thread: columns
@@ -145,13 +205,14 @@ __device__ __forceinline__ void load_norms(const float *__restrict__ nrm, int64_
     ni = i < n ? __ldg(nrm + i) : 0.0f;
 }
 
-template <int MAP>
+template <int MAP, bool MC>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
                                                           const __grid_constant__ CUtensorMap map_lo,
                                                           const float *__restrict__ x,
                                                           const float *__restrict__ nrm,
                                                           float *__restrict__ out, int64_t n, int d,
-                                                          int nb, int gx, int64_t total) {
+                                                          int nb, int nb2, int gx, int64_t total) {
+    using Walk = typename std::conditional<MC, PairWalk<MAP>, TileWalk<MAP>>::type;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -166,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&ctl.full[s]), 1);
-            mbar_init(smem_u32(&ctl.empty[s]), 1);
+            mbar_init(smem_u32(&ctl.empty[s]), MC ? 2 : 1);   // both CTAs release a shared stage
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl.tfull[a]), 1);
@@ -187,16 +248,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (MC) cluster_sync();   // the peer's barriers exist before any multicast reaches them
     const uint32_t tmem = ctl.tmem;
     const int nchunks = (d + KC - 1) / KC;
 
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            TileWalk<MAP> walk(gx, total, nb);
+            Walk walk(gx, total, nb2, nb);
+            const uint32_t rank = MC ? cluster_rank() : 0u;
             int X, Y;
+            bool valid;
             uint32_t it = 0;
-            while (!*fail && walk.next(X, Y)) {
+            while (!*fail && walk.next(X, Y, valid)) {
                 for (int c = 0; c < nchunks; ++c, ++it) {
                     const int s = (int)(it % kStages);
                     const uint32_t ph = (it / kStages) & 1;
@@ -204,8 +268,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                     const uint32_t bar = smem_u32(&ctl.full[s]);
                     const uint32_t dst = s_stages + s * STAGE_BYTES;
                     mbar_expect_tx(bar, STAGE_BYTES);
-                    tma_load_2d(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar);
-                    tma_load_2d(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar);
+                    if (MC) {
+                        // the row block's tiles once for the pair: hi from rank 0, lo from rank 1
+                        if (rank == 0) tma_load_2d_mc(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar, 3);
+                        else tma_load_2d_mc(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar, 3);
+                    } else {
+                        tma_load_2d(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar);
+                        tma_load_2d(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar);
+                    }
                     tma_load_2d(dst + 2 * TILE_BYTES, &map_hi, c * KC, X * TN, bar);
                     tma_load_2d(dst + 3 * TILE_BYTES, &map_lo, c * KC, X * TN, bar);
                 }
@@ -219,10 +289,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            TileWalk<MAP> walk(gx, total, nb);
+            Walk walk(gx, total, nb2, nb);
             int X, Y;
+            bool valid;
             uint32_t it = 0, tt = 0;
-            while (!*fail && walk.next(X, Y)) {
+            while (!*fail && walk.next(X, Y, valid)) {
                 const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
                 if (!mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error)) break;
                 tc_fence_after();
@@ -243,7 +314,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                         mma_bf16(dtm, ah, bl, kIdesc, 1u);
                         mma_bf16(dtm, al, bh, kIdesc, 1u);
                     }
-                    mma_commit(smem_u32(&ctl.empty[s]));
+                    // the stage is free once this CTA's MMAs (and, for a shared stage, the
+                    // peer's) have read it
+                    if (MC) mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
+                    else mma_commit(smem_u32(&ctl.empty[s]));
                 }
                 mma_commit(smem_u32(&ctl.tfull[acc]));
                 ++tt;
@@ -258,16 +332,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         float *stg = stg_all + quarter * 32 * kRowPitch;   // shared with the other half's warp
         // this warp's 64 column norms (its own buffer: no cross-warp sync)
         float *nc = &ctl.ncol[ew][0];
-        TileWalk<MAP> walk(gx, total, nb);
+        Walk walk(gx, total, nb2, nb);
         int X, Y;
-        bool have = walk.next(X, Y);
+        bool valid;
+        bool have = walk.next(X, Y, valid);
         // norms of the current tile, loaded one tile ahead
         float pa = 0.f, pb = 0.f, pni = 0.f;
         if (have) load_norms(nrm, n, X, Y, half, r, lane, pa, pb, pni);
-        uint32_t tt = 0;
+        uint32_t tt = 0, st = 0;   // tiles, and tiles staged and written
         while (have && !*fail) {
             int Xn, Yn;
-            const bool hn = walk.next(Xn, Yn);
+            bool vn;
+            const bool hn = walk.next(Xn, Yn, vn);
             float na = 0.f, nbv = 0.f, nni = 0.f;
             if (hn) load_norms(nrm, n, Xn, Yn, half, r, lane, na, nbv, nni);
             const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
@@ -294,6 +370,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            if (!valid) {   // a lockstep tile outside the simplex: nothing to write
+                X = Xn; Y = Yn; have = hn; valid = vn;
+                pa = na; pb = nbv; pni = nni;
+                ++tt;
+                continue;
+            }
             // D = |x_i|^2 + |x_j|^2 - 2 g; flag entries with D < (|x_i|^2 + |x_j|^2)/64
             float lows[4] = {1.0f, 1.0f, 1.0f, 1.0f};   // independent chains
 #pragma unroll
@@ -321,18 +403,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 }
             }
             // the staging is free once both warps' copies of the previous tile have read it
-            if (tt > 0) {
+            if (st > 0) {
                 bulk_wait_read();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&ctl.sfree[quarter]));
-                if (!mbar_wait(smem_u32(&ctl.sfree[quarter]), (tt - 1) & 1, fail, &g_error)) break;
+                if (!mbar_wait(smem_u32(&ctl.sfree[quarter]), (st - 1) & 1, fail, &g_error)) break;
             }
 #pragma unroll
             for (int q = 0; q < 32; ++q) { myrow[q] = v0[q]; myrow[32 + q] = v1[q]; }
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&ctl.sfull[quarter]));
-            if (!mbar_wait(smem_u32(&ctl.sfull[quarter]), tt & 1, fail, &g_error)) break;
+            if (!mbar_wait(smem_u32(&ctl.sfull[quarter]), st & 1, fail, &g_error)) break;
             if (!diag) {
                 // One bulk copy per row segment of the tile (128 columns, both
                 // halves): lanes 0-15 of this warp take rows 16 half .. +15; the
@@ -357,9 +439,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 if (rc <= 63) myrow[rc] = 0.0f;           // D_ii = 0 exactly
                 for (int e = 0; e <= last; ++e) out[gbase + e] = myrow[e];
             }
-            X = Xn; Y = Yn; have = hn;
+            X = Xn; Y = Yn; have = hn; valid = vn;
             pa = na; pb = nbv; pni = nni;
             ++tt;
+            ++st;
         }
     }
     bulk_wait_all();   // staging rows must stay valid until the copies have read them
@@ -369,6 +452,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         tc_fence_after();
         tmem_dealloc(tmem, kAccCols);
     }
+    // neither CTA of a pair leaves while the other may still multicast into
+    // its shared memory or arrive on its barriers
+    if (MC) cluster_sync();
 }
 
 static int smem_optin() {
@@ -381,13 +467,51 @@ static int smem_optin() {
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM_BYTES)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA, false>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX, false>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR, false>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA, true>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX, true>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR, true>, a, PSMEM_BYTES)) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
     return SIMPLEX_OK;
+}
+
+// Operand tiles are shared by a CTA pair where the kernel is bound by loading
+// them (d >= 128: four or more K chunks per tile); at d = 64 the packed output
+// writes bound it.
+static bool use_multicast(int64_t d) { return d >= 128; }
+
+// Two-CTA clusters that fit on the device at once (one CTA per SM), once per
+// device; half the SM count if the query fails.
+static int64_t max_pairs(int sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return sms / 2;
+    static std::mutex mu;
+    static int64_t cached[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached[dev]) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms & ~1));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = PSMEM_BYTES;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int num = 0;
+        if (cudaOccupancyMaxActiveClusters(&num, k_edm_umma<MAP_LAMBDA, true>, &cfg) != cudaSuccess || num < 1) {
+            cudaGetLastError();
+            num = sms / 2;
+        }
+        cached[dev] = num;
+    }
+    return cached[dev];
 }
 
 }  // namespace umma
@@ -423,15 +547,46 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
     int dev = 0, sms = 0;
     if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
-    const int64_t total = g.gx * g.gy;
-    const unsigned ctas = (unsigned)(total < sms ? total : sms);
-    prof_begin(s);
-    if (map == MAP_LAMBDA)
-        k_edm_umma<MAP_LAMBDA><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)g.gx, total);
-    else if (map == MAP_BBOX)
-        k_edm_umma<MAP_BBOX><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)g.gx, total);
-    else
-        k_edm_umma<MAP_LINEAR><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)g.gx, total);
+    if (!use_multicast(d)) {
+        const int64_t total = g.gx * g.gy;
+        const unsigned ctas = (unsigned)(total < sms ? total : sms);
+        prof_begin(s);
+        if (map == MAP_LAMBDA)
+            k_edm_umma<MAP_LAMBDA, false><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb, (int)g.gx, total);
+        else if (map == MAP_BBOX)
+            k_edm_umma<MAP_BBOX, false><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb, (int)g.gx, total);
+        else
+            k_edm_umma<MAP_LINEAR, false><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb, (int)g.gx, total);
+    } else {
+        // two-CTA clusters over the map's grid of 256 x 256 super-blocks
+        const int64_t nb2 = (nb + 1) / 2;
+        const Grid g2 = grid2(nb2, map);
+        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
+        const int64_t total2 = g2.gx * g2.gy;
+        int64_t clusters = max_pairs(sms);
+        if (clusters > total2) clusters = total2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * clusters));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = PSMEM_BYTES;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        prof_begin(s);
+        cudaError_t e;
+        if (map == MAP_LAMBDA)
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LAMBDA, true>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        else if (map == MAP_BBOX)
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_BBOX, true>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        else
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LINEAR, true>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        if (e != cudaSuccess) { prof_end(s); return cuda_status(e); }
+    }
     prof_end(s);
     note_launches(1);
     return launch_status();
