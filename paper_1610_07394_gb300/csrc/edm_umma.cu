@@ -139,61 +139,6 @@ struct TileWalk {
     }
 };
 
-// The tiles of one CTA of a two-CTA cluster.  The map runs over the 2-simplex
-// of 256 x 256 super-blocks (nb2 = ceil(nb / 2)); the cluster takes the grid
-// blocks w = c, c + clusters, ... (c its index) and each super-block (sX, sY)
-// gives both CTAs two steps in lockstep: CTA rank r the column block
-// X = 2 sX + r, step s the row block Y = 2 sY + s.  Both CTAs need the same row
-// block at every step, so its operand tiles are loaded once for the pair (TMA
-// multicast).  A step whose tile lies above the diagonal or past the last
-// block (the second column block of a diagonal super-block at s = 0; row
-// blocks past nb when nb is odd) is still computed, to keep the lockstep,
-// and is marked invalid: nothing is written.
-template <int MAP>
-struct PairWalk {
-    int64_t w, total;
-    int wx, wy, gx, nb2, nb, step, sX, sY, pend, px, py;
-    uint32_t rank, stride;
-    __device__ PairWalk(int gx_, int64_t total_, int nb2_, int nb_)
-        : total(total_), gx(gx_), nb2(nb2_), nb(nb_), step(2), sX(0), sY(0), pend(0), px(0),
-          py(0) {
-        rank = cluster_rank();
-        stride = gridDim.x >> 1;
-        w = blockIdx.x >> 1;
-        wy = (int)(w / gx_);
-        wx = (int)(w - (int64_t)wy * gx_);
-    }
-    __device__ bool next(int &X, int &Y, bool &valid) {
-        if (step >= 2) {
-            if (pend) {
-                pend = 0;
-                sX = px; sY = py;
-            } else {
-                bool found = false;
-                while (w < total) {
-                    const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
-                                                      : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
-                    w += stride;
-                    wx += (int)stride;
-                    while (wx >= gx) { wx -= gx; ++wy; }
-                    if (L.cnt == 0) continue;
-                    sX = L.x[0]; sY = L.y[0];
-                    if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
-                    found = true;
-                    break;
-                }
-                if (!found) return false;
-            }
-            step = 0;
-        }
-        X = 2 * sX + (int)rank;
-        Y = 2 * sY + step;
-        ++step;
-        valid = X <= Y && Y < nb;
-        return true;
-    }
-};
-
 // Norms of a tile's rows and columns for one epilogue thread: columns
 // col0 + 64 half + lane and + 32 (a, b) and its row row0 + r (ni); 0 past n.
 __device__ __forceinline__ void load_norms(const float *__restrict__ nrm, int64_t n, int X, int Y,

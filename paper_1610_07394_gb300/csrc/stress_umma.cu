@@ -35,6 +35,7 @@
 // drains tile t), eight epilogue warps (two per TMEM lane quarter) read the
 // accumulators.  Every wait is bounded (simplex_device_errors).
 #include <cstddef>
+#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -130,7 +131,7 @@ struct ChunkWalk {
     int64_t c, w, end, total, nchunks;
     int wx, wy, gx, nb, chunk;
     int pend, px, py;
-    __device__ ChunkWalk(int64_t total_, int gx_, int nb_, int chunk_)
+    __device__ ChunkWalk(int gx_, int64_t total_, int /* super-blocks: unused */, int nb_, int chunk_)
         : c(blockIdx.x), total(total_), nchunks((total_ + chunk_ - 1) / chunk_), gx(gx_), nb(nb_),
           chunk(chunk_), pend(0), px(0), py(0) {
         open();
@@ -159,6 +160,10 @@ struct ChunkWalk {
             if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
             return true;
         }
+    }
+    __device__ bool next(int &X, int &Y, bool &valid) {
+        valid = true;
+        return next(X, Y);
     }
 };
 
@@ -240,14 +245,18 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// The forward kernel runs as two-CTA clusters (PairWalk): the row block's P
+// tiles are loaded once for the pair by TMA multicast.
 template <int MAP, bool BWD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stress_umma(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
                   const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                   const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
                   const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
-                  int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
+                  int nb2, int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
                   double *__restrict__ partials) {
+    constexpr bool MC = !BWD;
+    using Walk = typename std::conditional<MC, PairWalk<MAP>, ChunkWalk<MAP>>::type;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&ctl.full[s]), 1);
-            mbar_init(smem_u32(&ctl.empty[s]), 1);
+            mbar_init(smem_u32(&ctl.empty[s]), MC ? 2 : 1);   // both CTAs release a shared stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&ctl.tfull[b]), 1);
@@ -291,21 +300,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (MC) cluster_sync();   // the peer's barriers exist before any multicast reaches them
     const uint32_t tmem = ctl.tmem;
     float lhi = 0.f, llo = 0.f;   // loss partial (forward)
 
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            ChunkWalk<MAP> walk(total, gx, nb, chunk);
+            Walk walk(gx, total, nb2, nb, chunk);
+            const uint32_t rank = MC ? cluster_rank() : 0u;
             uint32_t it = 0, dst, bar;
             int X, Y, pX = 0, pY = 0;
-            bool ok = true, have = false;
-            while (ok && !*fail && walk.next(X, Y)) {
+            bool ok = true, have = false, valid;
+            while (ok && !*fail && walk.next(X, Y, valid)) {
                 for (int c = 0; c < nc1; ++c) {
                     if (!(ok = ring_acquire<NS>(ctl, s_stages, it, STAGE_BYTES, dst, bar, fail))) break;
-                    tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
-                    tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
+                    if (MC) {
+                        // the row block's tiles once for the pair: hi from rank 0, lo from rank 1
+                        if (rank == 0) tma_load_2d_mc(dst, &mPh, c * KC, Y * TM, bar, 3);
+                        else tma_load_2d_mc(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar, 3);
+                    } else {
+                        tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
+                        tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
+                    }
                     tma_load_2d(dst + 2 * TILE_BYTES, &mQh, c * KC, X * TN, bar);
                     tma_load_2d(dst + 3 * TILE_BYTES, &mQl, c * KC, X * TN, bar);
                 }
@@ -335,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
-            ChunkWalk<MAP> walk(total, gx, nb, chunk);
+            Walk walk(gx, total, nb2, nb, chunk);
             uint32_t it = 0, t = 0, src;
             int X, Y, prevY = -1, prev2Y = -1;
             bool ok = true;
@@ -392,7 +409,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma_commit(smem_u32(&ctl.g2done));
                 return true;
             };
-            while (ok && !*fail && walk.next(X, Y)) {
+            bool valid;
+            while (ok && !*fail && walk.next(X, Y, valid)) {
                 const uint32_t acc = t & 1, aph = (t >> 1) & 1;
                 if (!(ok = mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error))) break;
                 tc_fence_after();
@@ -410,7 +428,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mma_bf16(dtm, ah, bl, id1, 1u);
                         mma_bf16(dtm, al, bh, id1, 1u);
                     }
-                    mma_commit(smem_u32(&ctl.empty[it % NS]));
+                    // the stage is free once this CTA's MMAs (and, for a shared stage,
+                    // the peer's) have read it
+                    if (MC) mma_commit_mc(smem_u32(&ctl.empty[it % NS]), 3);
+                    else mma_commit(smem_u32(&ctl.empty[it % NS]));
                     ++it;
                 }
                 if (!ok) break;
@@ -435,16 +456,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ngx = gx_buffers(NG);
         unsigned char *rowh = cbuf + half * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128;
         unsigned char *rowl = rowh + 2 * TILE_BYTES;
-        ChunkWalk<MAP> walk(total, gx, nb, chunk);
+        Walk walk(gx, total, nb2, nb, chunk);
         uint32_t t = 0;
         int X, Y, pX = 0, pY = 0;
-        bool have = walk.next(X, Y);
+        bool valid;
+        bool have = walk.next(X, Y, valid);
         // a of the current tile's columns (va, vb) and row (vi), loaded a tile ahead
         float va = 0.f, vb = 0.f, vi = 0.f;
         if (have) load_a(a, n, X, Y, half, r, lane, va, vb, vi);
         while (have && !*fail) {
             int Xn, Yn;
-            const bool hn = walk.next(Xn, Yn);
+            bool vn;
+            const bool hn = walk.next(Xn, Yn, vn);
             float na = 0.f, nbv = 0.f, ni = 0.f;
             if (hn) load_a(a, n, Xn, Yn, half, r, lane, na, nbv, ni);
             const uint32_t acc = t & 1, aph = (t >> 1) & 1;
@@ -455,7 +478,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t i = row0 + r;
             const float ai = vi;
             // valid columns q < lim: j < n, and j < i on a diagonal tile
-            int64_t lim64 = i < n ? n - jb : 0;
+            // (a lockstep step outside the simplex has no valid column)
+            int64_t lim64 = i < n && valid ? n - jb : 0;
             if (X == Y && i - jb < lim64) lim64 = i - jb;
             const int lim = lim64 < 0 ? 0 : (lim64 > 64 ? 64 : (int)lim64);
             __syncwarp();
@@ -525,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             pX = X;
             pY = Y;
-            X = Xn; Y = Yn; have = hn;
+            X = Xn; Y = Yn; have = hn; valid = vn;
             va = na; vb = nbv; vi = ni;
             ++t;
         }
@@ -548,6 +572,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const double s = block_sum_ff<kThreads>(lhi, llo, ctl.red);
         if (tid == 0) partials[blockIdx.x] = s;
     }
+    // neither CTA of a pair leaves while the other may still multicast into
+    // its shared memory or arrive on its barriers
+    if (MC) cluster_sync();
 }
 
 // P = [S | Delta], Q = [Delta | S] (BF16 hi, lo; rows of 2d), a = S . Delta in
@@ -643,18 +670,73 @@ static int smem_optin() {
 }
 
 template <bool BWD>
-static void launch(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
-                   const float *a, int64_t n, int d, int nb, int gx, int64_t total, int chunk,
-                   float scale4, float *grad, double *partials) {
+static cudaError_t launch(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
+                          const float *a, int64_t n, int d, int nb, int nb2, int gx, int64_t total,
+                          int chunk, float scale4, float *grad, double *partials) {
+    if (BWD) {
+        if (map == MAP_LAMBDA)
+            k_stress_umma<MAP_LAMBDA, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
+                m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+        else if (map == MAP_BBOX)
+            k_stress_umma<MAP_BBOX, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
+                m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+        else
+            k_stress_umma<MAP_LINEAR, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
+                m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+        return cudaGetLastError();
+    }
+    // the forward runs as two-CTA clusters
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     if (map == MAP_LAMBDA)
-        k_stress_umma<MAP_LAMBDA, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
-    else if (map == MAP_BBOX)
-        k_stress_umma<MAP_BBOX, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
-    else
-        k_stress_umma<MAP_LINEAR, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
+        return cudaLaunchKernelEx(&cfg, k_stress_umma<MAP_LAMBDA, BWD>, m[0], m[1], m[2], m[3], m[4], m[5], x, a,
+                                  n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+    if (map == MAP_BBOX)
+        return cudaLaunchKernelEx(&cfg, k_stress_umma<MAP_BBOX, BWD>, m[0], m[1], m[2], m[3], m[4], m[5], x, a,
+                                  n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+    return cudaLaunchKernelEx(&cfg, k_stress_umma<MAP_LINEAR, BWD>, m[0], m[1], m[2], m[3], m[4], m[5], x, a,
+                              n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+}
+
+// Two-CTA clusters of the forward kernel that fit on the device at once (one
+// CTA per SM), once per device; half the SM count if the query fails.
+static int64_t max_pairs(int sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return sms / 2;
+    static std::mutex mu;
+    static int64_t cached[64] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached[dev]) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms & ~1));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int num = 0;
+        if (cudaOccupancyMaxActiveClusters(&num, k_stress_umma<MAP_LAMBDA, false>, &cfg) != cudaSuccess ||
+            num < 1) {
+            cudaGetLastError();
+            num = sms / 2;
+        }
+        cached[dev] = num;
+    }
+    return cached[dev];
 }
 
 }  // namespace summa
@@ -711,24 +793,37 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     int dev = 0, sms = 0;
     if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
-    const int64_t total = g.gx * g.gy;
-    // chunks of up to kChunk grid blocks, at least four per CTA where the grid allows
-    int64_t chunk = total / (4 * (int64_t)sms);
-    chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
-    const int64_t chunks = (total + chunk - 1) / chunk;
-    int64_t ctas = chunks < sms ? chunks : sms;
-    if (ctas > kMaxCtas) ctas = kMaxCtas;
-    if (bwd && (st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s))))
-        return st;
-    prof_begin(s);
-    if (bwd)
-        launch<true>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
-                     (float)(4.0 * gscale), grad, nullptr);
-    else
-        launch<false>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
-                      0.f, nullptr, partials);
+    int64_t ctas;
+    cudaError_t le;
+    if (bwd) {
+        const int64_t total = g.gx * g.gy;
+        // chunks of up to kChunk grid blocks, at least four per CTA where the grid allows
+        int64_t chunk = total / (4 * (int64_t)sms);
+        chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
+        const int64_t chunks = (total + chunk - 1) / chunk;
+        ctas = chunks < sms ? chunks : sms;
+        if (ctas > kMaxCtas) ctas = kMaxCtas;
+        if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
+        prof_begin(s);
+        le = launch<true>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)nb, (int)g.gx, total,
+                          (int)chunk, (float)(4.0 * gscale), grad, nullptr);
+    } else {
+        // two-CTA clusters over the map's grid of 256 x 256 super-blocks
+        const int64_t nb2 = (nb + 1) / 2;
+        const Grid g2 = grid2(nb2, map);
+        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
+        const int64_t total2 = g2.gx * g2.gy;
+        int64_t clusters = max_pairs(sms);
+        if (clusters > total2) clusters = total2;
+        if (clusters > kMaxCtas / 2) clusters = kMaxCtas / 2;
+        ctas = 2 * clusters;
+        prof_begin(s);
+        le = launch<false>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)nb2, (int)g2.gx,
+                           total2, 0, 0.f, nullptr, partials);
+    }
     prof_end(s);
     note_launches(1);
+    if (le != cudaSuccess) return cuda_status(le);
     if ((st = launch_status())) return st;
     if (bwd) return SIMPLEX_OK;
     if ((st = reduce_partials(partials, ctas, partials + kMaxCtas, loss, s))) return st;
