@@ -135,6 +135,11 @@ __device__ __forceinline__ void triple_energy2s(const float2 (&vij)[3], float4 C
     s0 = __ffma2_rn(cw, bw, s0);
 }
 
+// The grid's z-layers run in reverse launch order (block z decodes grid layer
+// gz - 1 - z): the lambda map's last layers hold the J = K plane, whose
+// diagonal-pair row gives blocks two tiles each; launched first, they finish
+// inside the grid instead of trailing its last wave.  The map is unchanged.
+
 // The (up to two) data blocks of a grid block, read without dynamic indexing.
 __device__ __forceinline__ void block_of(const List3 &L, int t, int &I, int &J, int &K) {
     I = t ? L.i[1] : L.i[0];
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AtmEnergySmem &S = *reinterpret_cast<AtmEnergySmem *>(smem_raw);
     __shared__ float red[16];
-    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, gridDim.z - 1 - blockIdx.z, p, nb);
     if (L.cnt == 0) {   // a block outside the simplex exits at once
         if (threadIdx.x == 0)
             partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AtmEnergyTabSmem &S = *reinterpret_cast<AtmEnergyTabSmem *>(smem_raw);
     __shared__ float red[16];
-    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, gridDim.z - 1 - blockIdx.z, p, nb);
     if (L.cnt == 0) {   // a block outside the simplex exits at once
         if (threadIdx.x == 0)
             partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
@@ -497,7 +502,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AtmForceSmem &S = *reinterpret_cast<AtmForceSmem *>(smem_raw);
     __shared__ float red[16];
-    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
+    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, gridDim.z - 1 - blockIdx.z, p, nb);
     if (L.cnt == 0) {   // a block outside the simplex exits at once
         if (partials && threadIdx.x == 0)
             partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
