@@ -210,22 +210,20 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy(int64_t n, const float *_
 
 // ---------------------------------------------------------------- pair tables
 
-// The energy tables of every block pair (B1 <= B2) of the 2-simplex of
-// blocks, computed once per call instead of once per tile: for the pairs
-// (a in B1, b in B2), in the layout of AtmEnergySmem so that a tile copies
-// them into shared memory as they are (one bulk copy each),
-//   ec form [b][0][t] = (v0.x, v1.x, v0.y, v1.y), [b][1][t] = (v0.z, v1.z, r0^3, r1^3)
-//           with pairs (a = t, b) -> 0 and (a = t + 16, b) -> 1;
-//   eb form [b][h][0][t] = (v.x, v.x, v.y, v.y), [b][h][1][t] = (v.z, v.z, r^3, r^3)
-//           of the pair (a = t + 16h, b);
-// r^3 = (|x_b - x_a|^2 + eps)^-3/2 and v = r^(3/2) u, u = r (x_b - x_a), all
-// zero unless a < b < n.  With the scaled vectors the product of the three
-// dot products of a triple is r_ij^3 r_ik^3 r_jk^3 (u_ij.u_ik)(u_ij.u_jk)(u_ik.u_jk)
-// directly (triple_energy2s).  A tile (I, J, K) takes the ec form of (I, K),
-// the eb form of (J, K) and its pair constants from the ec form of (I, J).
-constexpr int kTabEc = R_ * 2 * 16;                // float4 of the ec form (16 KB)
-constexpr int kTabEb = R_ * 2 * 2 * 16;            // float4 of the eb form (32 KB)
-constexpr int kTabPair = kTabEc + kTabEb;          // float4 per block pair (48 KB)
+// The pair table of every block pair (B1 <= B2) of the 2-simplex of blocks,
+// computed once per call instead of once per tile.  For the pairs (a in B1,
+// b in B2) it holds the scaled edge vector v = r^(3/2) u (u = r (x_b - x_a))
+// and r^3 = (|x_b - x_a|^2 + eps)^-3/2, all zero unless a < b < n, packed
+// over pairs of consecutive b for FP32x2 arithmetic:
+//   tab[h][0][a] = (v_b0.x, v_b1.x, v_b0.y, v_b1.y),
+//   tab[h][1][a] = (v_b0.z, v_b1.z, r_b0^3, r_b1^3),   b0 = 2h, b1 = 2h + 1.
+// One form serves every role: a tile (I, J, K) copies the tables of (I, K)
+// and (J, K) into shared memory as they are (one bulk copy each) and reads
+// its pair constants (i, j) from the table of (I, J).  With the scaled
+// vectors the product of the three dot products of a triple is
+// r_ij^3 r_ik^3 r_jk^3 (u_ij.u_ik)(u_ij.u_jk)(u_ik.u_jk) directly
+// (triple_energy2s).
+constexpr int kTabPair = (R_ / 2) * 2 * R_;        // float4 per block pair (16 KB)
 constexpr int64_t kTabMaxBytes = int64_t(8) << 30; // larger tables: per-tile tables instead
 
 // (r^(3/2) u, r^3) of the edge from -> to, zero outside the simplex.
@@ -259,35 +257,38 @@ __global__ void __launch_bounds__(256) k_atm_pairtab(int64_t n, const float *__r
             xs[which][o] = v;
         }
         __syncthreads();
-        float4 *ec = tab + pair_slot(B1, B2) * kTabPair;
-        float4 *eb = ec + kTabEc;
-        for (int e = tid; e < R_ * 16; e += 256) {
-            const int b = e >> 4, a = e & 15;
-            const int64_t gb = (int64_t)B2 * R_ + b, ga = (int64_t)B1 * R_ + a;
-            const float4 u0 = scaled_pair_term(xs[0][a], xs[1][b], ga < gb && gb < n, eps);
-            const float4 u1 = scaled_pair_term(xs[0][a + 16], xs[1][b], ga + 16 < gb && gb < n, eps);
-            ec[(2 * b) * 16 + a] = make_float4(u0.x, u1.x, u0.y, u1.y);
-            ec[(2 * b + 1) * 16 + a] = make_float4(u0.z, u1.z, u0.w, u1.w);
-            eb[(4 * b + 0) * 16 + a] = make_float4(u0.x, u0.x, u0.y, u0.y);
-            eb[(4 * b + 1) * 16 + a] = make_float4(u0.z, u0.z, u0.w, u0.w);
-            eb[(4 * b + 2) * 16 + a] = make_float4(u1.x, u1.x, u1.y, u1.y);
-            eb[(4 * b + 3) * 16 + a] = make_float4(u1.z, u1.z, u1.w, u1.w);
+        float4 *out = tab + pair_slot(B1, B2) * kTabPair;
+        for (int e = tid; e < (R_ / 2) * R_; e += 256) {
+            const int h = e / R_, a = e % R_, b0 = 2 * h, b1 = 2 * h + 1;
+            const int64_t ga = (int64_t)B1 * R_ + a;
+            const int64_t g0 = (int64_t)B2 * R_ + b0, g1 = (int64_t)B2 * R_ + b1;
+            const float4 u0 = scaled_pair_term(xs[0][a], xs[1][b0], ga < g0 && g0 < n, eps);
+            const float4 u1 = scaled_pair_term(xs[0][a], xs[1][b1], ga < g1 && g1 < n, eps);
+            out[(2 * h) * R_ + a] = make_float4(u0.x, u1.x, u0.y, u1.y);
+            out[(2 * h + 1) * R_ + a] = make_float4(u0.z, u1.z, u0.w, u1.w);
         }
     }
 }
 
 __device__ int g_atm_error;   // set when a bounded wait of the energy kernel runs out
 
+// A tile's two tables: ik = table of (I, K) (a = i, b = k), jk = table of
+// (J, K) (a = j, b = k).  A warp's 16 distinct ti read 256 contiguous bytes
+// of ik (two wavefronts, no bank conflict); its two tj read two addresses of
+// jk (one broadcast wavefront).
 struct AtmEnergyTabSmem {
-    float4 ec[R_][2][16];
-    float4 eb[R_][2][2][16];
+    float4 ik[R_ / 2][2][R_];
+    float4 jk[R_ / 2][2][R_];
     uint64_t bar;
 };
 
 // The energy kernel fed by the pair tables: per tile, one thread starts two
-// bulk copies (48 KB) into shared memory, every thread reads its pair
+// bulk copies (2 x 16 KB) into shared memory, every thread reads its pair
 // constants (v_ij, r_ij^3) from the (I, J) table meanwhile, then a packed
-// triple loop over the scaled vectors (triple_energy2s).
+// triple loop over the scaled vectors (triple_energy2s) whose two lanes are
+// two consecutive k: the (i, k) and (j, k) values are loaded as packed
+// pairs, the pair constants of (i, j) are the same in both lanes, and each
+// thread's 2 x 2 pairs (i, j) reuse every load twice.
 template <int MAP>
 __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
                                                            int nb, int p,
@@ -316,26 +317,30 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
         block_of(L, t, I, J, K);
         if (t) __syncthreads();   // every thread is done with the previous tile's tables
         if (threadIdx.x == 0 && !bad) {
-            umma::mbar_expect_tx(bar, (uint32_t)(kTabPair * 16));
-            umma::bulk_load(umma::smem_u32(&S.ec[0][0][0]), tab + pair_slot(I, K) * kTabPair,
-                            kTabEc * 16, bar);
-            umma::bulk_load(umma::smem_u32(&S.eb[0][0][0][0]), tab + pair_slot(J, K) * kTabPair + kTabEc,
-                            kTabEb * 16, bar);
+            umma::mbar_expect_tx(bar, (uint32_t)(2 * kTabPair * 16));
+            umma::bulk_load(umma::smem_u32(&S.ik[0][0][0]), tab + pair_slot(I, K) * kTabPair,
+                            kTabPair * 16, bar);
+            umma::bulk_load(umma::smem_u32(&S.jk[0][0][0]), tab + pair_slot(J, K) * kTabPair,
+                            kTabPair * 16, bar);
         }
-        // pair constants of (i, j), v_ij and r_ij^3: the ec form of (I, J) at b = j
-        const float4 *pij = tab + pair_slot(I, J) * kTabPair;
-        float2 vij[2][3];
-        float ra3[2][2];
+        // pair constants of (i, j) = (ti + 16p, tj + 16q): v_ij in both lanes
+        // (r_ij^3 is read again after the loop, to spare registers), from the
+        // (I, J) table at a = i, b = j (lane j & 1)
+        const float4 *pij = tab + pair_slot(I, J) * kTabPair + (tj >> 1) * 2 * R_ + ti;
+        const bool odd = tj & 1;
+        float2 vij[2][2][3];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int j = tj + 16 * q;
-            const float4 a = __ldg(pij + (2 * j) * 16 + ti), b = __ldg(pij + (2 * j + 1) * 16 + ti);
-            vij[q][0] = make_float2(a.x, a.y);
-            vij[q][1] = make_float2(a.z, a.w);
-            vij[q][2] = make_float2(b.x, b.y);
-            ra3[0][q] = b.z;
-            ra3[1][q] = b.w;
-        }
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp) {
+                const float4 *e = pij + (16 * q) * R_ + 16 * pp;
+                const float4 a = __ldg(e), b = __ldg(e + R_);
+                const float vx = odd ? a.y : a.x, vy = odd ? a.w : a.z;
+                const float vz = odd ? b.y : b.x;
+                vij[pp][q][0] = make_float2(vx, vx);
+                vij[pp][q][1] = make_float2(vy, vy);
+                vij[pp][q][2] = make_float2(vz, vz);
+            }
         // bounded wait for the tables; a timeout flags the error, drains
         // (bounded) and lets the block finish with a NaN result
         if (!bad) {
@@ -349,20 +354,33 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
                 }
             }
         }
-        float2 s00 = make_float2(0.f, 0.f), s01 = make_float2(0.f, 0.f);
-        float2 s10 = make_float2(0.f, 0.f), s11 = make_float2(0.f, 0.f);
-#pragma unroll 4
-        for (int k = 0; k < R_; ++k) {
-            const float4 C0 = S.ec[k][0][ti], C1 = S.ec[k][1][ti];
-            const float4 B00 = S.eb[k][0][0][tj], B01 = S.eb[k][0][1][tj];
-            const float4 B10 = S.eb[k][1][0][tj], B11 = S.eb[k][1][1][tj];
-            triple_energy2s(vij[0], C0, C1, B00, B01, s00, s10);
-            triple_energy2s(vij[1], C0, C1, B10, B11, s01, s11);
+        float2 s0[2][2], s1[2][2];
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) s0[pp][q] = s1[pp][q] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int h = 0; h < R_ / 2; ++h) {
+            // pairs in the order (0,0) (0,1) (1,1) (1,0): three of the four
+            // loaded (i, k) / (j, k) values are live at a time
+            const float4 C00 = S.ik[h][0][ti], C01 = S.ik[h][1][ti];
+            const float4 B00 = S.jk[h][0][tj], B01 = S.jk[h][1][tj];
+            triple_energy2s(vij[0][0], C00, C01, B00, B01, s0[0][0], s1[0][0]);
+            const float4 B10 = S.jk[h][0][tj + 16], B11 = S.jk[h][1][tj + 16];
+            triple_energy2s(vij[0][1], C00, C01, B10, B11, s0[0][1], s1[0][1]);
+            const float4 C10 = S.ik[h][0][ti + 16], C11 = S.ik[h][1][ti + 16];
+            triple_energy2s(vij[1][1], C10, C11, B10, B11, s0[1][1], s1[1][1]);
+            triple_energy2s(vij[1][0], C10, C11, B00, B01, s0[1][0], s1[1][0]);
         }
-        add_ff(hi, lo, fmaf(ra3[0][0], s00.x, -3.0f * s10.x), 0.f);
-        add_ff(hi, lo, fmaf(ra3[1][0], s00.y, -3.0f * s10.y), 0.f);
-        add_ff(hi, lo, fmaf(ra3[0][1], s01.x, -3.0f * s11.x), 0.f);
-        add_ff(hi, lo, fmaf(ra3[1][1], s01.y, -3.0f * s11.y), 0.f);
+#pragma unroll
+        for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float4 b = __ldg(pij + (16 * q + 1) * R_ + 16 * pp);
+                const float ra3 = odd ? b.w : b.z;
+                add_ff(hi, lo, fmaf(ra3, s0[pp][q].x + s0[pp][q].y, -3.0f * (s1[pp][q].x + s1[pp][q].y)),
+                       0.f);
+            }
     }
     const bool any_bad = __syncthreads_or(bad) != 0;
     const double s = block_sum_ff<256>(hi, lo, red);

@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                         const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
                         const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
                         const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
-                        mma_bf16(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16(dtm, ah, bl, kIdesc, 1u);
+                        mma_bf16_afill(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast(dtm, ah, bl, kIdesc, 1u);
                         mma_bf16(dtm, al, bh, kIdesc, 1u);
                     }
                     // the stage is free once this CTA's MMAs (and, for a shared stage, the

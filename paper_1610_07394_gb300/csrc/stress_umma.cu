@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t bh = sw128_desc(src + h * xt_box + ks * 32);
                         const uint64_t bl = sw128_desc(src + (2 + h) * xt_box + ks * 32);
                         const uint32_t acc = (h == 0 && ks == 0 && !sameY) ? 0u : 1u;
-                        mma_bf16(tmem + kGY, ah, bh, id_row, acc);
-                        mma_bf16(tmem + kGY, ah, bl, id_row, 1u);
+                        mma_bf16_afill(tmem + kGY, ah, bh, id_row, acc);
+                        mma_bf16_alast(tmem + kGY, ah, bl, id_row, 1u);
                         mma_bf16(tmem + kGY, al, bh, id_row, 1u);
                     }
                 mma_commit(smem_u32(&ctl.empty[it % NS]));
@@ -400,8 +400,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t hb = (uint32_t)(ks >> 2), kb = (uint32_t)(ks & 3) * 32;
                     const uint64_t bh = sw128_desc(src + hb * xt_box + kb);
                     const uint64_t bl = sw128_desc(src + (2 + hb) * xt_box + kb);
-                    mma_bf16(tgx, ah, bh, id_col, ks ? 1u : 0u);
-                    mma_bf16(tgx, ah, bl, id_col, 1u);
+                    mma_bf16_afill(tgx, ah, bh, id_col, ks ? 1u : 0u);
+                    mma_bf16_alast(tgx, ah, bl, id_col, 1u);
                     mma_bf16(tgx, al, bh, id_col, 1u);
                 }
                 mma_commit(smem_u32(&ctl.empty[it % NS]));
@@ -424,8 +424,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t al = sw128_desc(src + TILE_BYTES + ko);
                         const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + ko);
                         const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + ko);
-                        mma_bf16(dtm, ah, bh, id1, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16(dtm, ah, bl, id1, 1u);
+                        mma_bf16_afill(dtm, ah, bh, id1, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast(dtm, ah, bl, id1, 1u);
                         mma_bf16(dtm, al, bh, id1, 1u);
                     }
                     // the stage is free once this CTA's MMAs (and, for a shared stage,

@@ -90,9 +90,9 @@ def test_grid_and_workspace_sizes(L):
     assert sx.simplex_grid_blocks(4, 32, "lambda") == -1
     rho = sx.simplex_block_rho("atm_energy")
     nb = -(-1024 // rho)
-    # pair tables (48 KB per block pair of the 2-simplex of blocks), then one
+    # pair tables (16 KB per block pair of the 2-simplex of blocks), then one
     # FP64 partial per grid block and 1024 reduction slots
-    assert sx.simplex_workspace_bytes("atm_energy", 1024, 3, "lambda") == nb * (nb + 1) // 2 * 49152 + 8 * (
+    assert sx.simplex_workspace_bytes("atm_energy", 1024, 3, "lambda") == nb * (nb + 1) // 2 * 16384 + 8 * (
         sx.simplex_grid_blocks(3, nb, "lambda") + 1024)
     assert sx.simplex_workspace_bytes("atm_forces", 1024, 3, "lambda") == 8 * (
         sx.simplex_grid_blocks(3, nb, "lambda") + 1024)
