@@ -577,6 +577,260 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (MC) cluster_sync();
 }
 
+// ---------------------------------------------------------------- forward in 128 x 256 steps
+
+// The forward kernel in 128 x 256 steps.  A two-CTA cluster walks the map's
+// grid of 256 x 256 super-blocks (sX, sY); CTA r computes row block
+// Y = 2 sY + r against both column blocks 2 sX and 2 sX + 1 with M = 128,
+// N = 256 MMAs (both column blocks in one 256-row B operand).  Each CTA
+// loads its own row block's P tiles and multicasts the Q tiles of column
+// block 2 sX + r into both CTAs, so per K chunk a CTA reads 64 KB from L2 for
+// 128 x 256 pairs (the 128 x 128 steps with a shared row block read 96 KB for
+// two 128 x 128 tiles).  A quadrant above the diagonal (r = 0 on a diagonal
+// super-block) or past the last block is computed and contributes nothing.
+namespace f256 {
+
+constexpr int TN2 = 2 * TN;                    // 256 columns per step
+constexpr int A_BYTES = TILE_BYTES;            // 16 KB: 128 rows x 64 BF16
+constexpr int B_BYTES = 2 * TILE_BYTES;        // 32 KB: 256 rows x 64 BF16
+constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;   // 96 KB: P hi, P lo, Q hi, Q lo
+constexpr int NS = 2;
+
+struct Ctl2 {
+    uint64_t full[NS], empty[NS];   // ring: TMA -> MMA -> TMA (both CTAs release a stage)
+    uint64_t tfull[2], tempty[2];   // accumulators: MMA -> epilogue -> MMA
+    uint64_t done;                  // every MMA of the block complete
+    uint32_t tmem;
+    int fail;
+    alignas(16) float acol[kEpiWarps][TN];   // a_j of each epilogue warp's 128 columns
+    float red[2 * (kThreads / 32)];
+};
+
+constexpr int kCtl2Bytes = 8192;
+constexpr int SMEM2 = 1024 + NS * STAGE + kCtl2Bytes;
+static_assert(sizeof(Ctl2) <= kCtl2Bytes, "control block");
+static_assert(SMEM2 <= 227 * 1024, "shared memory per block");
+static_assert(2 * TN2 <= kTmemCols, "two accumulators of 256 columns");
+
+// The super-blocks of a cluster: the map's grid over nb2 = ceil(nb / 2)
+// blocks of 256, every cluster-th grid block, both CTAs of a cluster in the
+// same order (the multicast of a stage needs both on the same super-block).
+template <int MAP>
+struct SuperWalk {
+    int64_t w, total;
+    int wx, wy, gx, nb2, stride, pend, px, py;
+    __device__ SuperWalk(int gx_, int64_t total_, int nb2_)
+        : total(total_), gx(gx_), nb2(nb2_), pend(0), px(0), py(0) {
+        stride = (int)(gridDim.x >> 1);
+        w = blockIdx.x >> 1;
+        wy = (int)(w / gx_);
+        wx = (int)(w - (int64_t)wy * gx_);
+    }
+    __device__ bool next(int &sX, int &sY) {
+        if (pend) { pend = 0; sX = px; sY = py; return true; }
+        while (w < total) {
+            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
+                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
+            w += stride;
+            wx += stride;
+            while (wx >= gx) { wx -= gx; ++wy; }
+            if (L.cnt == 0) continue;
+            sX = L.x[0]; sY = L.y[0];
+            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
+            return true;
+        }
+        return false;
+    }
+};
+
+template <int MAP>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_stress_fwd256(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
+                    const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
+                    const float *__restrict__ a, int64_t n, int d, int nb, int nb2, int gx,
+                    int64_t total, double *__restrict__ partials) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    Ctl2 &ctl = *reinterpret_cast<Ctl2 *>(base + NS * STAGE);
+    const uint32_t s_stages = smem_u32(base);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int *fail = &ctl.fail;
+    const int nc1 = (2 * d) / KC;   // K chunks
+    const uint32_t rank = cluster_rank();
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&ctl.full[s]), 1);
+            mbar_init(smem_u32(&ctl.empty[s]), 2);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&ctl.tfull[b]), 1);
+            mbar_init(smem_u32(&ctl.tempty[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(&ctl.done), 1);
+        ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&mPh);
+        prefetch_map(&mPl);
+        prefetch_map(&mQh);
+        prefetch_map(&mQl);
+    }
+    if (warp == 1) tmem_alloc(smem_u32(&ctl.tmem), kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    cluster_sync();   // the peer's barriers exist before any multicast reaches them
+    const uint32_t tmem = ctl.tmem;
+    float lhi = 0.f, llo = 0.f;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            SuperWalk<MAP> walk(gx, total, nb2);
+            uint32_t it = 0;
+            int sX, sY;
+            bool ok = true;
+            while (ok && !*fail && walk.next(sX, sY)) {
+                const int Y = 2 * sY + (int)rank, Xr = 2 * sX + (int)rank;
+                for (int c = 0; c < nc1; ++c) {
+                    const uint32_t s = it % NS, ph = (it / NS) & 1;
+                    // free once both CTAs' MMAs have read the stage
+                    if (!(ok = mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error))) break;
+                    const uint32_t bar = smem_u32(&ctl.full[s]), dst = s_stages + s * STAGE;
+                    mbar_expect_tx(bar, STAGE);
+                    tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
+                    tma_load_2d(dst + A_BYTES, &mPl, c * KC, Y * TM, bar);
+                    // this CTA's column block, rows 128 r .. 128 r + 127 of both CTAs' B
+                    tma_load_2d_mc(dst + 2 * A_BYTES + rank * TILE_BYTES, &mQh, c * KC, Xr * TN, bar, 3);
+                    tma_load_2d_mc(dst + 2 * A_BYTES + B_BYTES + rank * TILE_BYTES, &mQl, c * KC, Xr * TN,
+                                   bar, 3);
+                    ++it;
+                }
+            }
+            // a failed block waits (bounded) for the loads it may have in flight
+            if (*fail)
+                for (uint32_t k = it > (uint32_t)NS ? it - NS : 0; k < it; ++k)
+                    mbar_drain(smem_u32(&ctl.full[k % NS]), (k / NS) & 1);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id = idesc_bf16(TM, TN2, false, false);
+            SuperWalk<MAP> walk(gx, total, nb2);
+            uint32_t it = 0, t = 0;
+            int sX, sY;
+            bool ok = true;
+            while (ok && !*fail && walk.next(sX, sY)) {
+                const uint32_t acc = t & 1, aph = (t >> 1) & 1;
+                if (!(ok = mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error))) break;
+                tc_fence_after();
+                const uint32_t dtm = tmem + acc * TN2;
+                for (int c = 0; c < nc1; ++c) {
+                    const uint32_t s = it % NS;
+                    if (!(ok = mbar_wait(smem_u32(&ctl.full[s]), (it / NS) & 1, fail, &g_error))) break;
+                    tc_fence_after();
+                    const uint32_t src = s_stages + s * STAGE;
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint32_t ko = ks * 32;
+                        const uint64_t ah = sw128_desc(src + ko);
+                        const uint64_t al = sw128_desc(src + A_BYTES + ko);
+                        const uint64_t bh = sw128_desc(src + 2 * A_BYTES + ko);
+                        const uint64_t bl = sw128_desc(src + 2 * A_BYTES + B_BYTES + ko);
+                        mma_bf16_afill(dtm, ah, bh, id, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast(dtm, ah, bl, id, 1u);
+                        mma_bf16(dtm, al, bh, id, 1u);
+                    }
+                    // the stage is free once this CTA's MMAs and the peer's have read it
+                    mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
+                    ++it;
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&ctl.tfull[acc]));
+                ++t;
+            }
+            // everything issued has completed before the block releases TMEM
+            mma_commit(smem_u32(&ctl.done));
+            mbar_drain(smem_u32(&ctl.done), 0);
+        }
+    } else {
+        // ---------------- epilogue: 8 warps, two per TMEM lane quarter, one
+        // column block each
+        const int ew = warp - 2;                 // 0..7
+        const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+        const int h = ew >> 2;                   // column block 2 sX + h: accumulator columns 128 h ..
+        const int r = 32 * quarter + lane;       // this thread's row in the tile
+        float *ac = &ctl.acol[ew][0];
+        SuperWalk<MAP> walk(gx, total, nb2);
+        uint32_t t = 0;
+        int sX, sY;
+        while (!*fail && walk.next(sX, sY)) {
+            const int Y = 2 * sY + (int)rank, X = 2 * sX + h;
+            const uint32_t acc = t & 1, aph = (t >> 1) & 1;
+            const int64_t i = (int64_t)Y * TM + r, jb = (int64_t)X * TN;
+            __syncwarp();   // the previous step's reads of ac are done
+#pragma unroll
+            for (int q = 0; q < TN; q += 32) {
+                const int64_t j = jb + q + lane;
+                ac[q + lane] = j < n ? __ldg(a + j) : 0.0f;
+            }
+            const float ai = i < n ? __ldg(a + i) : 0.0f;
+            // valid columns q < lim: j < n, j < i on a diagonal tile; none above
+            // the diagonal or past the last block
+            int64_t lim64 = (i < n && X <= Y && Y < nb) ? n - jb : 0;
+            if (X == Y && i - jb < lim64) lim64 = i - jb;
+            const int lim = lim64 < 0 ? 0 : (lim64 > TN ? TN : (int)lim64);
+            __syncwarp();
+            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail, &g_error)) break;
+            tc_fence_after();
+            float sq = 0.f;
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                float v0[32], v1[32];
+                const uint32_t taddr = tmem + acc * TN2 + ((uint32_t)(32 * quarter) << 16) +
+                                       (uint32_t)(TN * h + 64 * part);
+                tmem_ld64(taddr, v0, v1);
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    const int c0 = 64 * part + q;
+                    const float4 a0 = *reinterpret_cast<const float4 *>(ac + c0);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(ac + c0 + 32);
+                    const float x0[4] = {a0.x, a0.y, a0.z, a0.w}, x1[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float r0 = (ai + x0[k]) - v0[q + k];
+                        float r1 = (ai + x1[k]) - v1[q + k];
+                        r0 = c0 + k < lim ? r0 : 0.0f;
+                        r1 = c0 + 32 + k < lim ? r1 : 0.0f;
+                        sq = fmaf(r0, r0, sq);
+                        sq = fmaf(r1, r1, sq);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            add_ff(lhi, llo, sq, 0.f);
+            ++t;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+    const double s = block_sum_ff<kThreads>(lhi, llo, ctl.red);
+    if (tid == 0) partials[blockIdx.x] = s;
+    // neither CTA of a pair leaves while the other may still multicast into
+    // its shared memory or arrive on its barriers
+    cluster_sync();
+}
+
+}  // namespace f256
+
 // P = [S | Delta], Q = [Delta | S] (BF16 hi, lo; rows of 2d), a = S . Delta in
 // FP32, and for the backward pass X^T hi, lo (rows t < d: coordinates; row d:
 // ones; rows d+1 .. NG-1: zeros; row pitch `pitch`).  32 points per block.
@@ -653,6 +907,14 @@ static cudaError_t optin_one() {
     return cudaFuncSetAttribute(k_stress_umma<MAP_LINEAR, BWD>, a, SMEM_BYTES);
 }
 
+static cudaError_t optin_fwd256() {
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(f256::k_stress_fwd256<MAP_LAMBDA>, a, f256::SMEM2)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(f256::k_stress_fwd256<MAP_BBOX>, a, f256::SMEM2)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f256::k_stress_fwd256<MAP_LINEAR>, a, f256::SMEM2);
+}
+
 static int smem_optin() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -662,7 +924,7 @@ static int smem_optin() {
     if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
-        if ((e = optin_one<false>()) != cudaSuccess || (e = optin_one<true>()) != cudaSuccess)
+        if ((e = optin_fwd256()) != cudaSuccess || (e = optin_one<true>()) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -685,11 +947,11 @@ static cudaError_t launch(int map, unsigned ctas, cudaStream_t s, const CUtensor
                 m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
         return cudaGetLastError();
     }
-    // the forward runs as two-CTA clusters
+    // the forward runs as two-CTA clusters in 128 x 256 steps
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cfg.dynamicSmemBytes = f256::SMEM2;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -699,13 +961,13 @@ static cudaError_t launch(int map, unsigned ctas, cudaStream_t s, const CUtensor
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (map == MAP_LAMBDA)
-        return cudaLaunchKernelEx(&cfg, k_stress_umma<MAP_LAMBDA, BWD>, m[0], m[1], m[2], m[3], m[4], m[5], x, a,
-                                  n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+        return cudaLaunchKernelEx(&cfg, f256::k_stress_fwd256<MAP_LAMBDA>, m[0], m[1], m[2], m[3], a, n, d, nb,
+                                  nb2, gx, total, partials);
     if (map == MAP_BBOX)
-        return cudaLaunchKernelEx(&cfg, k_stress_umma<MAP_BBOX, BWD>, m[0], m[1], m[2], m[3], m[4], m[5], x, a,
-                                  n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
-    return cudaLaunchKernelEx(&cfg, k_stress_umma<MAP_LINEAR, BWD>, m[0], m[1], m[2], m[3], m[4], m[5], x, a,
-                              n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
+        return cudaLaunchKernelEx(&cfg, f256::k_stress_fwd256<MAP_BBOX>, m[0], m[1], m[2], m[3], a, n, d, nb,
+                                  nb2, gx, total, partials);
+    return cudaLaunchKernelEx(&cfg, f256::k_stress_fwd256<MAP_LINEAR>, m[0], m[1], m[2], m[3], a, n, d, nb,
+                              nb2, gx, total, partials);
 }
 
 // Two-CTA clusters of the forward kernel that fit on the device at once (one
@@ -720,7 +982,7 @@ static int64_t max_pairs(int sms) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(sms & ~1));
         cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.dynamicSmemBytes = f256::SMEM2;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = 2;
@@ -729,7 +991,7 @@ static int64_t max_pairs(int sms) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int num = 0;
-        if (cudaOccupancyMaxActiveClusters(&num, k_stress_umma<MAP_LAMBDA, false>, &cfg) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveClusters(&num, f256::k_stress_fwd256<MAP_LAMBDA>, &cfg) != cudaSuccess ||
             num < 1) {
             cudaGetLastError();
             num = sms / 2;
