@@ -11,7 +11,10 @@
 // (rows j).  P and Q are split into BF16 hi + lo and M accumulates
 // hi.hi + hi.lo + lo.hi in FP32 in tensor memory (GEMM1).
 //
-// Forward: L = sum_{j<i} r_ij^2, from the accumulator in the epilogue.
+// Forward: L = sum_{j<i} r_ij^2, from the accumulator in the epilogue, in
+// steps of 128 x 256 pairs (k_stress_umma_fwd: a two-CTA cluster per
+// 256 x 256 super-block of the map, N = 256 MMAs, the column blocks' Q tiles
+// shared by TMA multicast).
 //
 // Backward: dL/dx_i = 4 sum_{j != i} r_ij (x_i - x_j).  The epilogue writes
 // the masked residual tile C (C_ij = r_ij for valid j < i, else 0) to shared
@@ -29,13 +32,13 @@
 // buffers where TMEM has room) is flushed per tile.  Flushes are FP32 vector
 // atomics into grad.
 //
-// Persistent and warp-specialised, one CTA per SM: warp 0 issues TMA loads
-// into a two-stage ring of 64 KB stages (GEMM1 chunks, then GEMM2 coordinate
-// tiles), warp 1 issues the MMAs (GEMM1 of tile t+1 runs while the epilogue
-// drains tile t), eight epilogue warps (two per TMEM lane quarter) read the
+// Both kernels are persistent and warp-specialised, one CTA per SM: warp 0
+// issues TMA loads into a two-stage ring (backward: 64 KB stages of GEMM1
+// chunks, then GEMM2 coordinate tiles; forward: 96 KB stages), warp 1
+// issues the MMAs (the accumulation of step t+1 runs while the epilogue
+// drains step t), eight epilogue warps (two per TMEM lane quarter) read the
 // accumulators.  Every wait is bounded (simplex_device_errors).
 #include <cstddef>
-#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -53,9 +56,6 @@ constexpr int KC = 64;                         // K chunk: 64 BF16 = one 128-byt
 constexpr int TILE_BYTES = TM * KC * 2;        // 16 KB: 128 rows x 64 BF16
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;    // 64 KB
 constexpr int kStages = 2;                     // ring depth of the backward kernel
-constexpr int kMaxStages = 3;                  // the forward kernel also uses the C area as a stage
-template <bool BWD>
-__host__ __device__ constexpr int stages_of() { return BWD ? kStages : kMaxStages; }
 constexpr int C_BYTES = 4 * TILE_BYTES;        // C hi, lo for column halves 0, 1
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -69,7 +69,7 @@ constexpr int kMaxCtas = 1024;
 __device__ int g_error;   // set when a bounded wait runs out
 
 struct Ctl {
-    uint64_t full[kMaxStages], empty[kMaxStages];   // ring: TMA -> MMA -> TMA
+    uint64_t full[kStages], empty[kStages];   // ring: TMA -> MMA -> TMA
     uint64_t tfull[2], tempty[2];             // GEMM1 accumulators: MMA -> epilogue -> MMA
     uint64_t cready;                          // C tile written (epilogue -> MMA)
     uint64_t g2done;                          // GEMM2 of a tile complete (MMA -> epilogue)
@@ -87,7 +87,6 @@ constexpr int SMEM_BYTES = 1024 + kStages * STAGE_BYTES + C_BYTES + kCtlBytes;
 static_assert(sizeof(Ctl) <= kCtlBytes, "control block");
 static_assert(offsetof(Ctl, acol) % 16 == 0, "float4 reads of a_j");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
-static_assert(kMaxStages * STAGE_BYTES <= kStages * STAGE_BYTES + C_BYTES, "forward ring fits");
 
 // The tiles a CTA handles: the map's grid (gx x gy, x fastest) cut into C
 // chunks of `chunk` consecutive grid blocks (up to kChunk, smaller when the
@@ -131,7 +130,7 @@ struct ChunkWalk {
     int64_t c, w, end, total, nchunks;
     int wx, wy, gx, nb, chunk;
     int pend, px, py;
-    __device__ ChunkWalk(int gx_, int64_t total_, int /* super-blocks: unused */, int nb_, int chunk_)
+    __device__ ChunkWalk(int gx_, int64_t total_, int nb_, int chunk_)
         : c(blockIdx.x), total(total_), nchunks((total_ + chunk_ - 1) / chunk_), gx(gx_), nb(nb_),
           chunk(chunk_), pend(0), px(0), py(0) {
         open();
@@ -160,10 +159,6 @@ struct ChunkWalk {
             if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
             return true;
         }
-    }
-    __device__ bool next(int &X, int &Y, bool &valid) {
-        valid = true;
-        return next(X, Y);
     }
 };
 
@@ -245,23 +240,20 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// The forward kernel runs as two-CTA clusters (PairWalk): the row block's P
-// tiles are loaded once for the pair by TMA multicast.
-template <int MAP, bool BWD>
+// The backward kernel (gradient): 128 x 128 tiles, GEMM1 then GEMM2.
+template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_stress_umma(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
-                  const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
-                  const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
-                  const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
-                  int nb2, int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
-                  double *__restrict__ partials) {
-    constexpr bool MC = !BWD;
-    using Walk = typename std::conditional<MC, PairWalk<MAP>, ChunkWalk<MAP>>::type;
+    k_stress_umma_bwd(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
+                      const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
+                      const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
+                      const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
+                      int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad) {
+    using Walk = ChunkWalk<MAP>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    constexpr int NS = stages_of<BWD>();
-    unsigned char *cbuf = base + kStages * STAGE_BYTES;   // backward only (the forward's third stage)
+    constexpr int NS = kStages;
+    unsigned char *cbuf = base + kStages * STAGE_BYTES;   // the C tile
     Ctl &ctl = *reinterpret_cast<Ctl *>(cbuf + C_BYTES);
     const uint32_t s_stages = smem_u32(base), s_c = smem_u32(cbuf);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -273,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&ctl.full[s]), 1);
-            mbar_init(smem_u32(&ctl.empty[s]), MC ? 2 : 1);   // both CTAs release a shared stage
+            mbar_init(smem_u32(&ctl.empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&ctl.tfull[b]), 1);
@@ -291,42 +283,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         prefetch_map(&mPl);
         prefetch_map(&mQh);
         prefetch_map(&mQl);
-        if (BWD) {
-            prefetch_map(&mTh);
-            prefetch_map(&mTl);
-        }
+        prefetch_map(&mTh);
+        prefetch_map(&mTl);
     }
     if (warp == 1) tmem_alloc(smem_u32(&ctl.tmem), kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (MC) cluster_sync();   // the peer's barriers exist before any multicast reaches them
     const uint32_t tmem = ctl.tmem;
-    float lhi = 0.f, llo = 0.f;   // loss partial (forward)
 
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            Walk walk(gx, total, nb2, nb, chunk);
-            const uint32_t rank = MC ? cluster_rank() : 0u;
+            Walk walk(gx, total, nb, chunk);
             uint32_t it = 0, dst, bar;
             int X, Y, pX = 0, pY = 0;
-            bool ok = true, have = false, valid;
-            while (ok && !*fail && walk.next(X, Y, valid)) {
+            bool ok = true, have = false;
+            while (ok && !*fail && walk.next(X, Y)) {
                 for (int c = 0; c < nc1; ++c) {
                     if (!(ok = ring_acquire<NS>(ctl, s_stages, it, STAGE_BYTES, dst, bar, fail))) break;
-                    if (MC) {
-                        // the row block's tiles once for the pair: hi from rank 0, lo from rank 1
-                        if (rank == 0) tma_load_2d_mc(dst, &mPh, c * KC, Y * TM, bar, 3);
-                        else tma_load_2d_mc(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar, 3);
-                    } else {
-                        tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
-                        tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
-                    }
+                    tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
+                    tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
                     tma_load_2d(dst + 2 * TILE_BYTES, &mQh, c * KC, X * TN, bar);
                     tma_load_2d(dst + 3 * TILE_BYTES, &mQl, c * KC, X * TN, bar);
                 }
-                if (BWD && ok && have) {
+                if (ok && have) {
                     // GEMM2 operands of the previous tile: X^T of its columns, then of its rows
                     if ((ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
                         load_xt(&mTh, &mTl, pX, dst, xt_box, bar);
@@ -335,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 pX = X; pY = Y; have = true;
             }
-            if (BWD && ok && !*fail && have) {
+            if (ok && !*fail && have) {
                 if ((ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
                     load_xt(&mTh, &mTl, pX, dst, xt_box, bar);
                 if (ok && (ok = ring_acquire<NS>(ctl, s_stages, it, 4 * xt_box, dst, bar, fail)))
@@ -352,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
-            Walk walk(gx, total, nb2, nb, chunk);
+            Walk walk(gx, total, nb, chunk);
             uint32_t it = 0, t = 0, src;
             int X, Y, prevY = -1, prev2Y = -1;
             bool ok = true;
@@ -409,8 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mma_commit(smem_u32(&ctl.g2done));
                 return true;
             };
-            bool valid;
-            while (ok && !*fail && walk.next(X, Y, valid)) {
+            while (ok && !*fail && walk.next(X, Y)) {
                 const uint32_t acc = t & 1, aph = (t >> 1) & 1;
                 if (!(ok = mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error))) break;
                 tc_fence_after();
@@ -428,20 +408,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mma_bf16_alast(dtm, ah, bl, id1, 1u);
                         mma_bf16(dtm, al, bh, id1, 1u);
                     }
-                    // the stage is free once this CTA's MMAs (and, for a shared stage,
-                    // the peer's) have read it
-                    if (MC) mma_commit_mc(smem_u32(&ctl.empty[it % NS]), 3);
-                    else mma_commit(smem_u32(&ctl.empty[it % NS]));
+                    mma_commit(smem_u32(&ctl.empty[it % NS]));
                     ++it;
                 }
                 if (!ok) break;
                 mma_commit(smem_u32(&ctl.tfull[acc]));
-                if (BWD && t >= 1 && !(ok = gemm2(t - 1, t >= 2 && prevY == prev2Y))) break;
+                if (t >= 1 && !(ok = gemm2(t - 1, t >= 2 && prevY == prev2Y))) break;
                 prev2Y = prevY;
                 prevY = Y;
                 ++t;
             }
-            if (BWD && ok && !*fail && t >= 1) gemm2(t - 1, t >= 2 && prevY == prev2Y);
+            if (ok && !*fail && t >= 1) gemm2(t - 1, t >= 2 && prevY == prev2Y);
             // everything issued has completed before the block releases TMEM
             mma_commit(smem_u32(&ctl.done));
             mbar_drain(smem_u32(&ctl.done), 0);
@@ -456,18 +433,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ngx = gx_buffers(NG);
         unsigned char *rowh = cbuf + half * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128;
         unsigned char *rowl = rowh + 2 * TILE_BYTES;
-        Walk walk(gx, total, nb2, nb, chunk);
+        Walk walk(gx, total, nb, chunk);
         uint32_t t = 0;
         int X, Y, pX = 0, pY = 0;
-        bool valid;
-        bool have = walk.next(X, Y, valid);
+        bool have = walk.next(X, Y);
         // a of the current tile's columns (va, vb) and row (vi), loaded a tile ahead
         float va = 0.f, vb = 0.f, vi = 0.f;
         if (have) load_a(a, n, X, Y, half, r, lane, va, vb, vi);
         while (have && !*fail) {
             int Xn, Yn;
-            bool vn;
-            const bool hn = walk.next(Xn, Yn, vn);
+            const bool hn = walk.next(Xn, Yn);
             float na = 0.f, nbv = 0.f, ni = 0.f;
             if (hn) load_a(a, n, Xn, Yn, half, r, lane, na, nbv, ni);
             const uint32_t acc = t & 1, aph = (t >> 1) & 1;
@@ -478,8 +453,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t i = row0 + r;
             const float ai = vi;
             // valid columns q < lim: j < n, and j < i on a diagonal tile
-            // (a lockstep step outside the simplex has no valid column)
-            int64_t lim64 = i < n && valid ? n - jb : 0;
+            int64_t lim64 = i < n ? n - jb : 0;
             if (X == Y && i - jb < lim64) lim64 = i - jb;
             const int lim = lim64 < 0 ? 0 : (lim64 > 64 ? 64 : (int)lim64);
             __syncwarp();
@@ -496,7 +470,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
-            float sq = 0.f;
 #pragma unroll
             for (int q = 0; q < 64; q += 4) {
                 const float4 aj = *reinterpret_cast<const float4 *>(ac + q);
@@ -505,55 +478,50 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int k = 0; k < 4; ++k) {
                     const float rq = (ai + al4[k]) - v[q + k];
                     v[q + k] = q + k < lim ? rq : 0.0f;
-                    sq = fmaf(v[q + k], v[q + k], sq);
                 }
             }
-            if (!BWD) {
-                add_ff(lhi, llo, sq, 0.f);
-            } else {
-                // the C buffer is free once GEMM2 of the previous tile has completed
-                if (t >= 1 && !mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) break;
-                tc_fence_after();
+            // the C buffer is free once GEMM2 of the previous tile has completed
+            if (t >= 1 && !mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) break;
+            tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    uint32_t ph[4], pl[4];
+            for (int c = 0; c < 8; ++c) {
+                uint32_t ph[4], pl[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float f0 = v[8 * c + 2 * k], f1 = v[8 * c + 2 * k + 1];
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
-                        const __nv_bfloat162 hh = __halves2bfloat162(h0, h1);
-                        ph[k] = *reinterpret_cast<const uint32_t *>(&hh);
-                        pl[k] = pack_bf16(f0 - __bfloat162float(h0), f1 - __bfloat162float(h1));
-                    }
-                    const int off = (c ^ (r & 7)) << 4;
-                    *reinterpret_cast<uint4 *>(rowh + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                    *reinterpret_cast<uint4 *>(rowl + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                for (int k = 0; k < 4; ++k) {
+                    const float f0 = v[8 * c + 2 * k], f1 = v[8 * c + 2 * k + 1];
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+                    const __nv_bfloat162 hh = __halves2bfloat162(h0, h1);
+                    ph[k] = *reinterpret_cast<const uint32_t *>(&hh);
+                    pl[k] = pack_bf16(f0 - __bfloat162float(h0), f1 - __bfloat162float(h1));
                 }
-                fence_proxy_async();
+                const int off = (c ^ (r & 7)) << 4;
+                *reinterpret_cast<uint4 *>(rowh + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4 *>(rowl + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.cready));
+            if (t >= 1) {
+                // the previous tile's sides: its columns always, its rows at the end of a run
+                const uint32_t pb = (t - 1) % (uint32_t)ngx;
+                flush_g(tmem, kGY + NG * (1 + pb), pX, quarter, half, lane, d, n, scale4, x, grad);
+                tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ctl.cready));
-                if (t >= 1) {
-                    // the previous tile's sides: its columns always, its rows at the end of a run
-                    const uint32_t pb = (t - 1) % (uint32_t)ngx;
-                    flush_g(tmem, kGY + NG * (1 + pb), pX, quarter, half, lane, d, n, scale4, x, grad);
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.gxfree[pb]));
+                if (Y != pY) {
+                    flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&ctl.gxfree[pb]));
-                    if (Y != pY) {
-                        flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&ctl.gyfree));
-                    }
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl.gyfree));
                 }
             }
             pX = X;
             pY = Y;
-            X = Xn; Y = Yn; have = hn; valid = vn;
+            X = Xn; Y = Yn; have = hn;
             va = na; vb = nbv; vi = ni;
             ++t;
         }
-        if (BWD && !*fail && t >= 1 &&
+        if (!*fail && t >= 1 &&
             mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) {
             tc_fence_after();
             flush_g(tmem, kGY + NG * (1 + (t - 1) % (uint32_t)ngx), pX, quarter, half, lane, d, n, scale4,
@@ -568,13 +536,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
-    if (!BWD) {
-        const double s = block_sum_ff<kThreads>(lhi, llo, ctl.red);
-        if (tid == 0) partials[blockIdx.x] = s;
-    }
-    // neither CTA of a pair leaves while the other may still multicast into
-    // its shared memory or arrive on its barriers
-    if (MC) cluster_sync();
 }
 
 // ---------------------------------------------------------------- forward in 128 x 256 steps
@@ -645,7 +606,7 @@ struct SuperWalk {
 
 template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_stress_fwd256(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
+    k_stress_umma_fwd(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
                     const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                     const float *__restrict__ a, int64_t n, int d, int nb, int nb2, int gx,
                     int64_t total, double *__restrict__ partials) {
@@ -898,21 +859,20 @@ static Layout layout_of(int64_t n, int64_t d, bool bwd) {
     return L;
 }
 
-template <bool BWD>
-static cudaError_t optin_one() {
+static cudaError_t optin_bwd() {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_stress_umma<MAP_LAMBDA, BWD>, a, SMEM_BYTES)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_stress_umma<MAP_BBOX, BWD>, a, SMEM_BYTES)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_stress_umma<MAP_LINEAR, BWD>, a, SMEM_BYTES);
+    if ((e = cudaFuncSetAttribute(k_stress_umma_bwd<MAP_LAMBDA>, a, SMEM_BYTES)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_stress_umma_bwd<MAP_BBOX>, a, SMEM_BYTES)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_stress_umma_bwd<MAP_LINEAR>, a, SMEM_BYTES);
 }
 
 static cudaError_t optin_fwd256() {
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(f256::k_stress_fwd256<MAP_LAMBDA>, a, f256::SMEM2)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(f256::k_stress_fwd256<MAP_BBOX>, a, f256::SMEM2)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(f256::k_stress_fwd256<MAP_LINEAR>, a, f256::SMEM2);
+    if ((e = cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_LAMBDA>, a, f256::SMEM2)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_BBOX>, a, f256::SMEM2)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_LINEAR>, a, f256::SMEM2);
 }
 
 static int smem_optin() {
@@ -924,30 +884,31 @@ static int smem_optin() {
     if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
-        if ((e = optin_fwd256()) != cudaSuccess || (e = optin_one<true>()) != cudaSuccess)
+        if ((e = optin_fwd256()) != cudaSuccess || (e = optin_bwd()) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
     return SIMPLEX_OK;
 }
 
-template <bool BWD>
-static cudaError_t launch(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
-                          const float *a, int64_t n, int d, int nb, int nb2, int gx, int64_t total,
-                          int chunk, float scale4, float *grad, double *partials) {
-    if (BWD) {
-        if (map == MAP_LAMBDA)
-            k_stress_umma<MAP_LAMBDA, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-                m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
-        else if (map == MAP_BBOX)
-            k_stress_umma<MAP_BBOX, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-                m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
-        else
-            k_stress_umma<MAP_LINEAR, BWD><<<ctas, kThreads, SMEM_BYTES, s>>>(
-                m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, nb2, gx, total, chunk, scale4, grad, partials);
-        return cudaGetLastError();
-    }
-    // the forward runs as two-CTA clusters in 128 x 256 steps
+static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
+                              const float *a, int64_t n, int d, int nb, int gx, int64_t total, int chunk,
+                              float scale4, float *grad) {
+    if (map == MAP_LAMBDA)
+        k_stress_umma_bwd<MAP_LAMBDA><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad);
+    else if (map == MAP_BBOX)
+        k_stress_umma_bwd<MAP_BBOX><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad);
+    else
+        k_stress_umma_bwd<MAP_LINEAR><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad);
+    return cudaGetLastError();
+}
+
+// The forward runs as two-CTA clusters in 128 x 256 steps.
+static cudaError_t launch_fwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *a,
+                              int64_t n, int d, int nb, int nb2, int gx, int64_t total, double *partials) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kThreads);
@@ -961,12 +922,12 @@ static cudaError_t launch(int map, unsigned ctas, cudaStream_t s, const CUtensor
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (map == MAP_LAMBDA)
-        return cudaLaunchKernelEx(&cfg, f256::k_stress_fwd256<MAP_LAMBDA>, m[0], m[1], m[2], m[3], a, n, d, nb,
+        return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_LAMBDA>, m[0], m[1], m[2], m[3], a, n, d, nb,
                                   nb2, gx, total, partials);
     if (map == MAP_BBOX)
-        return cudaLaunchKernelEx(&cfg, f256::k_stress_fwd256<MAP_BBOX>, m[0], m[1], m[2], m[3], a, n, d, nb,
+        return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_BBOX>, m[0], m[1], m[2], m[3], a, n, d, nb,
                                   nb2, gx, total, partials);
-    return cudaLaunchKernelEx(&cfg, f256::k_stress_fwd256<MAP_LINEAR>, m[0], m[1], m[2], m[3], a, n, d, nb,
+    return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_LINEAR>, m[0], m[1], m[2], m[3], a, n, d, nb,
                               nb2, gx, total, partials);
 }
 
@@ -991,7 +952,7 @@ static int64_t max_pairs(int sms) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int num = 0;
-        if (cudaOccupancyMaxActiveClusters(&num, f256::k_stress_fwd256<MAP_LAMBDA>, &cfg) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveClusters(&num, f256::k_stress_umma_fwd<MAP_LAMBDA>, &cfg) != cudaSuccess ||
             num < 1) {
             cudaGetLastError();
             num = sms / 2;
@@ -1067,8 +1028,8 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
         if (ctas > kMaxCtas) ctas = kMaxCtas;
         if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
         prof_begin(s);
-        le = launch<true>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)nb, (int)g.gx, total,
-                          (int)chunk, (float)(4.0 * gscale), grad, nullptr);
+        le = launch_bwd(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
+                        (float)(4.0 * gscale), grad);
     } else {
         // two-CTA clusters over the map's grid of 256 x 256 super-blocks
         const int64_t nb2 = (nb + 1) / 2;
@@ -1080,8 +1041,8 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
         if (clusters > kMaxCtas / 2) clusters = kMaxCtas / 2;
         ctas = 2 * clusters;
         prof_begin(s);
-        le = launch<false>(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)nb2, (int)g2.gx,
-                           total2, 0, 0.f, nullptr, partials);
+        le = launch_fwd(map, (unsigned)ctas, s, m, a, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2,
+                        partials);
     }
     prof_end(s);
     note_launches(1);
