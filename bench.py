@@ -405,7 +405,8 @@ def _stress_tensor(torch, sx, peaks, x, y, maps):
     """Tensor-core stress forward and backward (BF16 hi+lo products): pairs/s
     per map and the issued MMA rate of the lambda map against the measured
     BF16 peak.  Per 128 x 128 tile the forward issues three K = 2d products,
-    the backward adds three K = 128 products of N = d + 16 for each side."""
+    the backward adds three K = 128 products of N = d + 16 for each side;
+    the rate of the pass that returns loss and gradient together as well."""
     n, d = x.shape
     pairs = n * (n - 1) // 2
     nb = -(-n // 128)
@@ -430,6 +431,12 @@ def _stress_tensor(torch, sx, peaks, x, y, maps):
             r["tc_bwd_ms"] = ms
             r["tc_bwd_mma_tflops"] = b_mma / (ms / 1e3) / 1e12
         del wb
+    # loss and gradient in one pass (the backward kernel summing the loss too)
+    wfb = sx.workspace("stress_fwd_bwd", n, d, "lambda", "bf16x3")
+    ms = _median_ms(torch, lambda: sx.simplex_stress_fwd_bwd(x, y, 1.0, g, loss, "lambda", "bf16x3", wfb), 3)
+    r["tc_fwd_bwd_lambda"] = pairs / (ms / 1e3)
+    r["tc_fwd_bwd_ms"] = ms
+    del wfb
     bf16 = peaks.get("bf16_tflops") if peaks else None
     if bf16:
         r["tc_fwd_bf16_frac"] = r["tc_fwd_mma_tflops"] / bf16

@@ -72,10 +72,11 @@ typedef enum {
 typedef enum {
     SIMPLEX_OP_MAP2 = 0, SIMPLEX_OP_MAP3 = 1, SIMPLEX_OP_EDM = 2,
     SIMPLEX_OP_ATM_ENERGY = 3, SIMPLEX_OP_ATM_FORCES = 4,
-    SIMPLEX_OP_STRESS_FWD = 5, SIMPLEX_OP_STRESS_BWD = 6
+    SIMPLEX_OP_STRESS_FWD = 5, SIMPLEX_OP_STRESS_BWD = 6, SIMPLEX_OP_STRESS_FWD_BWD = 7
 } simplex_op;
 
-/* ABI version of this header (bumped on any signature change). */
+/* ABI version of this header (bumped on any signature change or added entry
+ * point; 2 added simplex_stress_fwd_bwd). */
 int simplex_abi_version(void);
 
 /* Human-readable text of a status code (static storage). */
@@ -199,6 +200,19 @@ int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const float *y,
 int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
                        double gscale, float *grad, int map, int prec,
                        void *workspace, int64_t ws_bytes, void *stream);
+
+/*
+ * Loss and gradient in one pass (Sec. I: one sweep of the 2-simplex of
+ * pairs serves both): grad as simplex_stress_bwd (times gscale, written) and
+ * loss as simplex_stress_fwd (device, 1 double, written, not scaled), both
+ * from the same residual tiles.  Workspace: simplex_workspace_bytes(
+ * SIMPLEX_OP_STRESS_FWD_BWD, ...) bytes, 256-byte aligned (per-block loss
+ * partials, and the tensor-core operands where prec selects them).
+ * SIMPLEX_EINVAL if loss or grad is NULL.
+ */
+int simplex_stress_fwd_bwd(int64_t n, int64_t d, const float *x, const float *y,
+                           double gscale, float *grad, double *loss, int map, int prec,
+                           void *workspace, int64_t ws_bytes, void *stream);
 
 /* Synchronises `stream` and reports whether any bounded device-side wait of
  * the tensor-core kernels ran out since the last check (SIMPLEX_ETIMEOUT,

@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(_HERE, "libsimplex.so")
 MAPS = {"lambda": 0, "bbox": 1, "linear": 2}
 PRECS = {"fp32": 0, "bf16x3": 1, "auto": 2}
 OPS = {"map2": 0, "map3": 1, "edm": 2, "atm_energy": 3, "atm_forces": 4,
-       "stress_fwd": 5, "stress_bwd": 6}
+       "stress_fwd": 5, "stress_bwd": 6, "stress_fwd_bwd": 7}
 
 # Every symbol the header declares (the tests check the library exports them).
 EXPORTS = [
@@ -37,6 +37,7 @@ EXPORTS = [
     "simplex_map3", "simplex_edm_packed", "simplex_atm_energy", "simplex_atm_forces",
     "simplex_stress_fwd", "simplex_stress_bwd", "simplex_workspace_bytes", "simplex_profile",
     "simplex_profile_read", "simplex_atm_energy_noalloc", "simplex_device_errors",
+    "simplex_stress_fwd_bwd",
 ]
 
 
@@ -68,6 +69,7 @@ def _signatures(L):
         "simplex_atm_forces": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _vp, _i32, _vp, _i64, _vp]),
         "simplex_stress_fwd": (_i32, [_i64, _i64, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _i64, _vp]),
         "simplex_stress_bwd": (_i32, [_i64, _i64, _vp, _vp, _f64, _vp, _i32, _i32, _vp, _i64, _vp]),
+        "simplex_stress_fwd_bwd": (_i32, [_i64, _i64, _vp, _vp, _f64, _vp, _vp, _i32, _i32, _vp, _i64, _vp]),
         "simplex_workspace_bytes": (_i64, [_i32, _i64, _i64, _i32, _i32]),
         "simplex_profile": (_i32, [_i32]),
         "simplex_device_errors": (_i32, [_vp]),
@@ -220,6 +222,16 @@ def simplex_stress_bwd(x, y, gscale, grad, map="lambda", prec="fp32", workspace=
         0 if workspace is None else workspace.numel(), _stream(stream)))
 
 
+def simplex_stress_fwd_bwd(x, y, gscale, grad, loss, map="lambda", prec="fp32", workspace=None,
+                           stream=None):
+    n, d = x.shape
+    ws = _ptr_or_null(workspace, torch.uint8, "workspace")
+    _check("simplex_stress_fwd_bwd", lib().simplex_stress_fwd_bwd(
+        n, d, _cuda(x, torch.float32, "x"), _cuda(y, torch.float32, "y"), float(gscale),
+        _cuda(grad, torch.float32, "grad"), _cuda(loss, torch.float64, "loss"), _map(map), _prec(prec),
+        ws, 0 if workspace is None else workspace.numel(), _stream(stream)))
+
+
 def simplex_device_errors(stream=None):
     """Raises if a bounded device-side wait ran out (synchronises the stream)."""
     _check("simplex_device_errors", lib().simplex_device_errors(_stream(stream)))
@@ -332,6 +344,15 @@ def stress_bwd(x, y, gscale=1.0, map="lambda", prec="fp32"):
     grad = torch.empty_like(x)
     simplex_stress_bwd(x, y, gscale, grad, map, prec, workspace("stress_bwd", n, d, map, prec))
     return grad
+
+
+def stress_fwd_bwd(x, y, gscale=1.0, map="lambda", prec="fp32"):
+    """(loss, gradient times gscale) from one pass over the pairs."""
+    n, d = x.shape
+    loss = torch.empty((), dtype=torch.float64, device=x.device)
+    grad = torch.empty_like(x)
+    simplex_stress_fwd_bwd(x, y, gscale, grad, loss, map, prec, workspace("stress_fwd_bwd", n, d, map, prec))
+    return loss, grad
 
 
 class StressLoss(torch.autograd.Function):

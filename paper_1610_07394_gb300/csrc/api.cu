@@ -105,7 +105,7 @@ int reduce_partials(const double *partials, int64_t count, double *tmp, double *
 
 using namespace sx;
 
-extern "C" int simplex_abi_version(void) { return 1; }
+extern "C" int simplex_abi_version(void) { return 2; }
 
 extern "C" int simplex_profile(int on) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -169,7 +169,8 @@ extern "C" int simplex_block_rho(int op, int64_t d, int prec) {
         case SIMPLEX_OP_ATM_ENERGY:
         case SIMPLEX_OP_ATM_FORCES: return kAtmRho;
         case SIMPLEX_OP_STRESS_FWD:
-        case SIMPLEX_OP_STRESS_BWD: return stress_use_umma(d, prec) ? kStressUmmaRho : kStressRho;
+        case SIMPLEX_OP_STRESS_BWD:
+        case SIMPLEX_OP_STRESS_FWD_BWD: return stress_use_umma(d, prec) ? kStressUmmaRho : kStressRho;
         default: return -1;
     }
 }
@@ -194,6 +195,12 @@ extern "C" int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map
         }
         case SIMPLEX_OP_STRESS_BWD:
             return stress_use_umma(d, prec) ? stress_umma_workspace_bytes(n, d, true) : 0;
+        case SIMPLEX_OP_STRESS_FWD_BWD: {
+            if (stress_use_umma(d, prec)) return stress_umma_workspace_bytes(n, d, true);
+            const int64_t nb = (n + kStressRho - 1) / kStressRho;
+            const Grid g = grid2(nb, map);
+            return 8 * (g.gx * g.gy + kReduceSlots);
+        }
         default: return -1;
     }
 }

@@ -227,12 +227,17 @@ __device__ __forceinline__ void side_grad(const float *__restrict__ x, int64_t n
     }
 }
 
+// With `partials`, the loss of the same residual tiles as well (one FP64
+// partial per block): loss and gradient in one pass.
 template <int MAP>
 __global__ void __launch_bounds__(256) k_stress_bwd(int64_t n, int d, const float *__restrict__ x,
                                                     const float *__restrict__ y, float scale4,
-                                                    int nb, float *__restrict__ grad) {
+                                                    int nb, float *__restrict__ grad,
+                                                    double *__restrict__ partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StressSmem &sm = *reinterpret_cast<StressSmem *>(smem_raw);
+    __shared__ float red[16];
+    float hi = 0.f, lo = 0.f;
     // the x tiles of the gradient products reuse the S / Delta staging area
     float (*xo)[SR] = reinterpret_cast<float (*)[SR]>(&sm.sr[0][0]);
     float (*xs)[SR] = xo + SR;
@@ -245,13 +250,17 @@ __global__ void __launch_bounds__(256) k_stress_bwd(int64_t n, int d, const floa
         const int64_t row0 = (int64_t)Y * SR, col0 = (int64_t)X * SR;
         float r[4][4];
         residual_tile(x, y, n, d, row0, col0, sm, r);
+        float loc = 0.f;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int64_t i = row0 + 4 * ty + a, j = col0 + 4 * tx + b;
-                sm.C[4 * tx + b][4 * ty + a] = (j < i && i < n) ? r[a][b] : 0.f;
+                const float c = (j < i && i < n) ? r[a][b] : 0.f;
+                sm.C[4 * tx + b][4 * ty + a] = c;
+                loc = fmaf(c, c, loc);
             }
+        if (partials) add_ff(hi, lo, loc, 0.f);
         __syncthreads();
         if (threadIdx.x < SR) {
             float s = 0.f;
@@ -267,6 +276,10 @@ __global__ void __launch_bounds__(256) k_stress_bwd(int64_t n, int d, const floa
         side_grad(x, n, d, row0, col0, false, sm, scale4, grad, xo, xs);
         side_grad(x, n, d, col0, row0, true, sm, scale4, grad, xo, xs);
         __syncthreads();
+    }
+    if (partials) {
+        const double s = block_sum_ff<256>(hi, lo, red);
+        if (threadIdx.x == 0) partials[blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = s;
     }
 }
 
@@ -339,27 +352,50 @@ extern "C" int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const fl
     return reduce_partials(partials, blocks, partials + blocks, loss, s);
 }
 
-extern "C" int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
-                                  double gscale, float *grad, int map, int prec, void *workspace,
-                                  int64_t ws_bytes, void *stream) {
+// Gradient (times gscale) and, when `loss` is not NULL, the loss from the
+// same pass.
+static int stress_grad(int64_t n, int64_t d, const float *x, const float *y, double gscale,
+                       float *grad, double *loss, int map, int prec, void *workspace,
+                       int64_t ws_bytes, cudaStream_t s) {
     if (!grad) return SIMPLEX_EINVAL;
     Grid g;
     int64_t nb;
     int st = stress_check(n, d, x, y, map, prec, g, nb);
     if (st) return st;
-    if (!aligned(grad, 16)) return SIMPLEX_EALIGN;
+    if (!aligned(grad, 16) || (loss && !aligned(loss, 8))) return SIMPLEX_EALIGN;
     if (stress_use_umma(d, prec))
-        return stress_umma_run(true, n, d, x, y, nullptr, nullptr, gscale, grad, map, workspace,
-                               ws_bytes, (cudaStream_t)stream);
+        return stress_umma_run(true, n, d, x, y, nullptr, loss, gscale, grad, map, workspace, ws_bytes, s);
+    const int64_t blocks = g.gx * g.gy;
+    double *partials = nullptr;
+    if (loss) {
+        if (!workspace || ws_bytes < 8 * (blocks + kReduceSlots) || !aligned(workspace, 256))
+            return SIMPLEX_EWORKSPACE;
+        partials = (double *)workspace;
+    }
     if ((st = stress_optin())) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
     const float scale4 = (float)(4.0 * gscale);
     prof_begin(s);
-    if (map == MAP_LAMBDA) k_stress_bwd<MAP_LAMBDA><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad);
-    else if (map == MAP_BBOX) k_stress_bwd<MAP_BBOX><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad);
-    else k_stress_bwd<MAP_LINEAR><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad);
+    if (map == MAP_LAMBDA) k_stress_bwd<MAP_LAMBDA><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
+    else if (map == MAP_BBOX) k_stress_bwd<MAP_BBOX><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
+    else k_stress_bwd<MAP_LINEAR><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
     prof_end(s);
     note_launches(1);
-    return launch_status();
+    if ((st = launch_status())) return st;
+    return loss ? reduce_partials(partials, blocks, partials + blocks, loss, s) : SIMPLEX_OK;
+}
+
+extern "C" int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
+                                  double gscale, float *grad, int map, int prec, void *workspace,
+                                  int64_t ws_bytes, void *stream) {
+    return stress_grad(n, d, x, y, gscale, grad, nullptr, map, prec, workspace, ws_bytes,
+                       (cudaStream_t)stream);
+}
+
+extern "C" int simplex_stress_fwd_bwd(int64_t n, int64_t d, const float *x, const float *y,
+                                      double gscale, float *grad, double *loss, int map, int prec,
+                                      void *workspace, int64_t ws_bytes, void *stream) {
+    if (!loss) return SIMPLEX_EINVAL;
+    return stress_grad(n, d, x, y, gscale, grad, loss, map, prec, workspace, ws_bytes,
+                       (cudaStream_t)stream);
 }

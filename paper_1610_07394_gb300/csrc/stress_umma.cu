@@ -240,14 +240,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// The backward kernel (gradient): 128 x 128 tiles, GEMM1 then GEMM2.
+// The backward kernel (gradient): 128 x 128 tiles, GEMM1 then GEMM2.  With
+// `partials` it also sums the loss from the same residual tiles (one FP64
+// partial per CTA): loss and gradient in one pass.
 template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stress_umma_bwd(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
                       const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                       const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
                       const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
-                      int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad) {
+                      int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
+                      double *__restrict__ partials) {
     using Walk = ChunkWalk<MAP>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -291,6 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl.tmem;
+    float lhi = 0.f, llo = 0.f;   // loss partial (with `partials`)
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            float sq = 0.f;
 #pragma unroll
             for (int q = 0; q < 64; q += 4) {
                 const float4 aj = *reinterpret_cast<const float4 *>(ac + q);
@@ -478,8 +483,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int k = 0; k < 4; ++k) {
                     const float rq = (ai + al4[k]) - v[q + k];
                     v[q + k] = q + k < lim ? rq : 0.0f;
+                    sq = fmaf(v[q + k], v[q + k], sq);
                 }
             }
+            if (partials) add_ff(lhi, llo, sq, 0.f);
             // the C buffer is free once GEMM2 of the previous tile has completed
             if (t >= 1 && !mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) break;
             tc_fence_after();
@@ -535,6 +542,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
+    }
+    if (partials) {
+        const double s = block_sum_ff<kThreads>(lhi, llo, ctl.red);
+        if (tid == 0) partials[blockIdx.x] = s;
     }
 }
 
@@ -893,16 +904,16 @@ static int smem_optin() {
 
 static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
                               const float *a, int64_t n, int d, int nb, int gx, int64_t total, int chunk,
-                              float scale4, float *grad) {
+                              float scale4, float *grad, double *partials) {
     if (map == MAP_LAMBDA)
         k_stress_umma_bwd<MAP_LAMBDA><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
     else if (map == MAP_BBOX)
         k_stress_umma_bwd<MAP_BBOX><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
     else
         k_stress_umma_bwd<MAP_LINEAR><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
     return cudaGetLastError();
 }
 
@@ -1029,7 +1040,7 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
         if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
         prof_begin(s);
         le = launch_bwd(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
-                        (float)(4.0 * gscale), grad);
+                        (float)(4.0 * gscale), grad, loss ? partials : nullptr);
     } else {
         // two-CTA clusters over the map's grid of 256 x 256 super-blocks
         const int64_t nb2 = (nb + 1) / 2;
@@ -1048,7 +1059,7 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     note_launches(1);
     if (le != cudaSuccess) return cuda_status(le);
     if ((st = launch_status())) return st;
-    if (bwd) return SIMPLEX_OK;
+    if (bwd) return loss ? reduce_partials(partials, ctas, partials + kMaxCtas, loss, s) : SIMPLEX_OK;
     if ((st = reduce_partials(partials, ctas, partials + kMaxCtas, loss, s))) return st;
     if (!d_out) return SIMPLEX_OK;
     // the packed D itself: tensor-core EDM where it applies, else FP32

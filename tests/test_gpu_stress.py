@@ -198,3 +198,31 @@ def test_stress_tensor_scale_config(gpu, oracle):
     assert row_err(g, G_all).max() <= TC_G_TOL
     rows = synth.sample_indices(16, w["n"], seed=44)
     assert row_err(g[rows], oracle.stress_grad_rows(x, y, rows)).max() <= TC_G_TOL
+    # loss and gradient in one pass, at the same size
+    lf, gf = gpu.stress_fwd_bwd(xt, yt, 1.0, "lambda", "bf16x3")
+    assert abs(lf.item() - L_ref) <= TC_L_TOL * L_ref
+    assert row_err(gf.double().cpu().numpy(), G_all).max() <= TC_G_TOL
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("prec,n,d", [("fp32", 1, 4), ("fp32", 2, 1), ("fp32", 100, 8), ("fp32", 257, 64),
+                                      ("bf16x3", 1, 32), ("bf16x3", 300, 64), ("bf16x3", 513, 96)])
+def test_stress_fwd_bwd_one_pass(gpu, oracle, mp, prec, n, d):
+    """simplex_stress_fwd_bwd: the oracle's loss (unscaled) and gradient
+    (times gscale) within each precision's tolerances, and the gradient of
+    simplex_stress_bwd up to the order of the FP32 atomic flushes."""
+    x = synth.normal(n, d, seed=900 + n)
+    y = synth.perturbed(x, 0.1, seed=901 + n)
+    xt, yt = to_gpu(x), to_gpu(y)
+    loss, g = gpu.stress_fwd_bwd(xt, yt, 2.5, mp, prec)
+    ref = oracle.stress_loss(x, y)
+    if n == 1:
+        assert loss.item() == 0.0 and bool((g == 0).all())
+        return
+    tol = TC_L_TOL * ref if prec == "bf16x3" else max(L_TOL * ref, loss_bound(x, y))
+    assert abs(loss.item() - ref) <= tol
+    G = 2.5 * oracle.stress_grad_rows(x, y, range(n))
+    gd = g.double().cpu().numpy()
+    assert row_err(gd, G).max() <= (TC_G_TOL if prec == "bf16x3" else G_TOL)
+    gs = gpu.stress_bwd(xt, yt, 2.5, mp, prec).double()
+    assert (g.double() - gs).abs().max().item() <= 1e-5 * gs.abs().max().item()

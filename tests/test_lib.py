@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_abi_and_strerror(L):
-    assert sx.simplex_abi_version() == 1
+    assert sx.simplex_abi_version() == 2
     for st in range(7):
         assert L.simplex_strerror(st)
     assert L.simplex_last_cuda_error() == 0
@@ -97,6 +97,13 @@ def test_grid_and_workspace_sizes(L):
     assert sx.simplex_workspace_bytes("atm_forces", 1024, 3, "lambda") == 8 * (
         sx.simplex_grid_blocks(3, nb, "lambda") + 1024)
     assert sx.simplex_workspace_bytes("map2", 10, 1) == 0
+    # loss and gradient in one pass: FP32 tiles need one FP64 partial per grid
+    # block (64-point blocks); the tensor-core path the backward's workspace
+    nb64 = -(-1000 // sx.simplex_block_rho("stress_fwd_bwd", 8, "fp32"))
+    assert sx.simplex_workspace_bytes("stress_fwd_bwd", 1000, 8, "lambda", "fp32") == 8 * (
+        sx.simplex_grid_blocks(2, nb64, "lambda") + 1024)
+    assert sx.simplex_workspace_bytes("stress_fwd_bwd", 1000, 64, "lambda", "bf16x3") == \
+        sx.simplex_workspace_bytes("stress_bwd", 1000, 64, "lambda", "bf16x3") > 0
     assert sx.simplex_workspace_bytes("atm_energy", 0, 3) == -1
 
 
@@ -113,6 +120,10 @@ def test_validation_before_gpu_work(L):
     assert L.simplex_map2(10, 33, 0, 16, 16, null) == 1                          # rho > 32
     assert L.simplex_map3(10, 11, 0, 16, 16, null) == 1                          # rho^3 > 1024
     assert L.simplex_stress_bwd(8, 4, 16, 16, 1.0, 20, 0, 0, null, 0, null) == 2  # grad not 16B
+    assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, null, 0, 0, null, 0, null) == 1  # NULL loss
+    assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, null, 16, 0, 0, null, 0, null) == 1  # NULL grad
+    assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, 12, 0, 0, null, 0, null) == 2    # loss not 8B
+    assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, 16, 0, 0, null, 0, null) == 6    # no workspace
     assert L.simplex_map_blocks_host(2, 4, 0, null) == 1
 
 
