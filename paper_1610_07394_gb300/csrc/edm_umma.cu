@@ -11,20 +11,25 @@
 // form cancels) are recomputed in FP32 from the coordinates; the diagonal is
 // exactly 0.
 //
-// Persistent and warp-specialised: one CTA per SM walks the grid of the
-// chosen block-space map (grid blocks blockIdx.x, blockIdx.x + gridDim.x, ...)
-// and handles the tiles they map to.  Warp 0 issues the TMA loads of the
-// four 128 x 64 BF16 operand tiles of each K-chunk (128-byte swizzle) into a
-// two-stage ring; warp 1 issues the tcgen05.mma instructions (M = N = 128,
-// K = 16, three products per K step) into one of two 128-column TMEM
-// accumulators; eight epilogue warps (two per TMEM lane quarter) read a
-// finished accumulator with tcgen05.ld, form D, stage rows through shared
-// memory and write each packed row segment with coalesced stores, while the
-// MMA warp already fills the other accumulator.  Every mbarrier wait is
-// bounded in time; a wait that runs out sets a device error flag
-// (simplex_device_errors) and the block stops instead of hanging.
+// Persistent and warp-specialised, one CTA per SM, over the chosen map's grid
+// of 256 x 256 super-blocks (the map over ceil(nb / 2) blocks).  Warp 0
+// issues the TMA loads of the 128 x 64 BF16 operand tiles of each K chunk
+// (128-byte swizzle), warp 1 the tcgen05.mma instructions (M = N = 128,
+// K = 16, three products per K step) into 128-column TMEM accumulators, and
+// eight epilogue warps (two per TMEM lane quarter) read a finished
+// accumulator with tcgen05.ld, form D, stage rows through shared memory and
+// write each packed row segment with one bulk copy, while the MMA warp
+// already fills the next accumulator.  Two kernels:
+//  * k_edm_umma_wide (d < 128, bound by the stores): a CTA takes a
+//    super-block as two steps of two horizontally adjacent tiles, so that a
+//    row of a step is one segment of up to 256 outputs (a copy of up to
+//    1 KB);
+//  * k_edm_umma (d >= 128, bound by the operand loads): two-CTA clusters
+//    walk the super-blocks in lockstep, CTA r taking column block 2 sX + r,
+//    and the row block's tiles are loaded once for the pair by multicast.
+// Every mbarrier wait is bounded in time; a wait that runs out sets a device
+// error flag (simplex_device_errors) and the block stops instead of hanging.
 #include <cstddef>
-#include <type_traits>
 #include <mutex>
 
 #include "common.cuh"
@@ -104,41 +109,6 @@ static_assert(sizeof(PCtl) <= kCtlBytes, "control block");
 static_assert(offsetof(PCtl, ncol) % 16 == 0, "float4 reads of the column norms");
 static_assert(PSMEM_BYTES <= 227 * 1024, "shared memory per block");
 
-// The tiles of the grid blocks this CTA owns, in order: grid blocks
-// w = blockIdx.x + k gridDim.x of the map's grid (gx x gy), each sent by the
-// map to zero, one or two 128 x 128 tiles (column block X <= row block Y).
-template <int MAP>
-struct TileWalk {
-    int64_t w, total;   // linear grid-block index (x fastest) and grid size
-    int wx, wy, gx, nb;
-    int pend, px, py;   // second tile of a diagonal pair, still to visit
-    __device__ TileWalk(int gx_, int64_t total_, int /* super-blocks: unused */, int nb_)
-        : w(blockIdx.x), total(total_), gx(gx_), nb(nb_), pend(0), px(0), py(0) {
-        wy = (int)(blockIdx.x / (unsigned)gx_);
-        wx = (int)(blockIdx.x - (unsigned)wy * (unsigned)gx_);
-    }
-    __device__ bool next(int &X, int &Y) {
-        if (pend) { pend = 0; X = px; Y = py; return true; }
-        while (w < total) {
-            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb)
-                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb);
-            // advance by gridDim.x grid blocks without a division
-            w += gridDim.x;
-            wx += (int)gridDim.x;
-            while (wx >= gx) { wx -= gx; ++wy; }
-            if (L.cnt == 0) continue;
-            X = L.x[0]; Y = L.y[0];
-            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
-            return true;
-        }
-        return false;
-    }
-    __device__ bool next(int &X, int &Y, bool &valid) {
-        valid = true;
-        return next(X, Y);
-    }
-};
-
 // Norms of a tile's rows and columns for one epilogue thread: columns
 // col0 + 64 half + lane and + 32 (a, b) and its row row0 + r (ni); 0 past n.
 __device__ __forceinline__ void load_norms(const float *__restrict__ nrm, int64_t n, int X, int Y,
@@ -150,14 +120,14 @@ __device__ __forceinline__ void load_norms(const float *__restrict__ nrm, int64_
     ni = i < n ? __ldg(nrm + i) : 0.0f;
 }
 
-template <int MAP, bool MC>
+template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
                                                           const __grid_constant__ CUtensorMap map_lo,
                                                           const float *__restrict__ x,
                                                           const float *__restrict__ nrm,
                                                           float *__restrict__ out, int64_t n, int d,
                                                           int nb, int nb2, int gx, int64_t total) {
-    using Walk = typename std::conditional<MC, PairWalk<MAP>, TileWalk<MAP>>::type;
+    using Walk = PairWalk<MAP>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -172,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&ctl.full[s]), 1);
-            mbar_init(smem_u32(&ctl.empty[s]), MC ? 2 : 1);   // both CTAs release a shared stage
+            mbar_init(smem_u32(&ctl.empty[s]), 2);   // both CTAs release a shared stage
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl.tfull[a]), 1);
@@ -193,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (MC) cluster_sync();   // the peer's barriers exist before any multicast reaches them
+    cluster_sync();   // the peer's barriers exist before any multicast reaches them
     const uint32_t tmem = ctl.tmem;
     const int nchunks = (d + KC - 1) / KC;
 
@@ -201,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         // ---------------- TMA producer
         if (lane == 0) {
             Walk walk(gx, total, nb2, nb);
-            const uint32_t rank = MC ? cluster_rank() : 0u;
+            const uint32_t rank = cluster_rank();
             int X, Y;
             bool valid;
             uint32_t it = 0;
@@ -213,14 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                     const uint32_t bar = smem_u32(&ctl.full[s]);
                     const uint32_t dst = s_stages + s * STAGE_BYTES;
                     mbar_expect_tx(bar, STAGE_BYTES);
-                    if (MC) {
-                        // the row block's tiles once for the pair: hi from rank 0, lo from rank 1
-                        if (rank == 0) tma_load_2d_mc(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar, 3);
-                        else tma_load_2d_mc(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar, 3);
-                    } else {
-                        tma_load_2d(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar);
-                        tma_load_2d(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar);
-                    }
+                    // the row block's tiles once for the pair: hi from rank 0, lo from rank 1
+                    if (rank == 0) tma_load_2d_mc(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar, 3);
+                    else tma_load_2d_mc(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar, 3);
                     tma_load_2d(dst + 2 * TILE_BYTES, &map_hi, c * KC, X * TN, bar);
                     tma_load_2d(dst + 3 * TILE_BYTES, &map_lo, c * KC, X * TN, bar);
                 }
@@ -259,10 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                         mma_bf16_alast(dtm, ah, bl, kIdesc, 1u);
                         mma_bf16(dtm, al, bh, kIdesc, 1u);
                     }
-                    // the stage is free once this CTA's MMAs (and, for a shared stage, the
-                    // peer's) have read it
-                    if (MC) mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
-                    else mma_commit(smem_u32(&ctl.empty[s]));
+                    // the stage is free once this CTA's MMAs and the peer's have read it
+                    mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
                 }
                 mma_commit(smem_u32(&ctl.tfull[acc]));
                 ++tt;
@@ -399,8 +362,340 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     }
     // neither CTA of a pair leaves while the other may still multicast into
     // its shared memory or arrive on its barriers
-    if (MC) cluster_sync();
+    cluster_sync();
 }
+
+// ---------------------------------------------------------------- rows of 256 columns
+
+// The kernel for d < 128, where the packed stores bound it, in steps of two
+// horizontally adjacent tiles: each CTA walks the map's grid of 256 x 256
+// super-blocks (sX, sY) and takes a super-block as two steps (row block
+// 2 sY + s against column blocks 2 sX and 2 sX + 1), so that each row of a
+// step is one packed segment of up to 256 outputs, written by one bulk copy
+// of up to 1 KB.  The bulk copies cost a fixed time per copy besides their
+// bytes, and copies of 1 KB instead of 512 B take a quarter off the store
+// time.  One 64 KB operand stage (A and B of one tile; the stores leave the
+// loads time to spare), four 128-column TMEM accumulators (two steps), and
+// staging of 32 rows x 256 columns per TMEM lane quarter.
+namespace wide {
+
+constexpr int kWStages = 1;
+constexpr int kWPitch = 260;                          // 256 columns + the shift to 16 bytes
+constexpr int kWStageBytes = 4 * 32 * kWPitch * 4;    // four lane quarters
+constexpr int kWAccCols = 4 * TN;                     // four accumulators
+
+struct WCtl {
+    uint64_t full[kWStages], empty[kWStages];   // operand stage: TMA -> MMA -> TMA
+    uint64_t tfull[4], tempty[4];               // accumulators: MMA -> epilogue -> MMA
+    uint64_t sfull[4], sfree[4];                // per lane quarter: staging written / copied out
+    uint32_t tmem;
+    int fail;
+    alignas(16) float ncol[kEpiWarps][TN];      // each epilogue warp's 128 column norms
+};
+
+constexpr int kWCtlBytes = 8192;
+constexpr int WSMEM_BYTES = 1024 + kWStages * STAGE_BYTES + kWStageBytes + kWCtlBytes;
+static_assert(sizeof(WCtl) <= kWCtlBytes, "control block");
+static_assert(offsetof(WCtl, ncol) % 16 == 0, "float4 reads of the column norms");
+static_assert(WSMEM_BYTES <= 227 * 1024, "shared memory per block");
+
+// The steps of a CTA: super-blocks w = blockIdx.x + k gridDim.x of the
+// map's grid over nb2 = ceil(nb / 2) blocks of 256, two steps each (row
+// blocks 2 sY, 2 sY + 1; a row block past the last is skipped).
+template <int MAP>
+struct StepWalk {
+    int64_t w, total;
+    int wx, wy, gx, nb2, nb, step, sX, sY, pend, px, py;
+    __device__ StepWalk(int gx_, int64_t total_, int nb2_, int nb_)
+        : w(blockIdx.x), total(total_), gx(gx_), nb2(nb2_), nb(nb_), step(2), sX(0), sY(0), pend(0),
+          px(0), py(0) {
+        wy = (int)(blockIdx.x / (unsigned)gx_);
+        wx = (int)(blockIdx.x - (unsigned)wy * (unsigned)gx_);
+    }
+    // the next step: column blocks X0 = 2 sX and X0 + 1, row block Y
+    __device__ bool next(int &X0, int &Y) {
+        for (;;) {
+            if (step >= 2) {
+                if (pend) {
+                    pend = 0;
+                    sX = px; sY = py;
+                } else {
+                    bool found = false;
+                    while (w < total) {
+                        const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
+                                                          : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
+                        w += gridDim.x;
+                        wx += (int)gridDim.x;
+                        while (wx >= gx) { wx -= gx; ++wy; }
+                        if (L.cnt == 0) continue;
+                        sX = L.x[0]; sY = L.y[0];
+                        if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
+                        found = true;
+                        break;
+                    }
+                    if (!found) return false;
+                }
+                step = 0;
+            }
+            X0 = 2 * sX;
+            Y = 2 * sY + step;
+            ++step;
+            if (Y < nb) return true;
+        }
+    }
+};
+
+template <int MAP>
+__global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_constant__ CUtensorMap map_hi,
+                                                               const __grid_constant__ CUtensorMap map_lo,
+                                                               const float *__restrict__ x,
+                                                               const float *__restrict__ nrm,
+                                                               float *__restrict__ out, int64_t n, int d,
+                                                               int nb, int nb2, int gx, int64_t total) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float *stg_all = reinterpret_cast<float *>(base + kWStages * STAGE_BYTES);
+    WCtl &ctl = *reinterpret_cast<WCtl *>(base + kWStages * STAGE_BYTES + kWStageBytes);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t s_stages = smem_u32(base);
+    volatile int *fail = &ctl.fail;
+
+    if (tid == 0) {
+        for (int s = 0; s < kWStages; ++s) {
+            mbar_init(smem_u32(&ctl.full[s]), 1);
+            mbar_init(smem_u32(&ctl.empty[s]), 1);
+        }
+        for (int a = 0; a < 4; ++a) {
+            mbar_init(smem_u32(&ctl.tfull[a]), 1);
+            mbar_init(smem_u32(&ctl.tempty[a]), kEpiWarps / 2);   // the four warps of that tile
+        }
+        for (int q = 0; q < 4; ++q) {
+            mbar_init(smem_u32(&ctl.sfull[q]), 2);
+            mbar_init(smem_u32(&ctl.sfree[q]), 2);
+        }
+        ctl.fail = *reinterpret_cast<volatile int *>(&g_error) ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        prefetch_map(&map_hi);
+        prefetch_map(&map_lo);
+    }
+    if (warp == 1) tmem_alloc(smem_u32(&ctl.tmem), kWAccCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl.tmem;
+    const int nchunks = (d + KC - 1) / KC;
+
+    if (warp == 0) {
+        // ---------------- TMA producer: per step the two tiles, per tile its K chunks
+        if (lane == 0) {
+            StepWalk<MAP> walk(gx, total, nb2, nb);
+            int X0, Y;
+            uint32_t it = 0;
+            bool ok = true;
+            while (ok && !*fail && walk.next(X0, Y)) {
+                for (int t = 0; t < 2 && ok; ++t)
+                    for (int c = 0; c < nchunks; ++c, ++it) {
+                        const int s = (int)(it % kWStages);
+                        const uint32_t ph = (it / kWStages) & 1;
+                        if (!(ok = mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error))) break;
+                        const uint32_t bar = smem_u32(&ctl.full[s]);
+                        const uint32_t dst = s_stages + s * STAGE_BYTES;
+                        mbar_expect_tx(bar, STAGE_BYTES);
+                        tma_load_2d(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar);
+                        tma_load_2d(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar);
+                        tma_load_2d(dst + 2 * TILE_BYTES, &map_hi, c * KC, (X0 + t) * TN, bar);
+                        tma_load_2d(dst + 3 * TILE_BYTES, &map_lo, c * KC, (X0 + t) * TN, bar);
+                    }
+            }
+            // a failed block waits (bounded) for its loads in flight
+            if (*fail && it > 0) {
+                const uint32_t last = it - 1;
+                mbar_drain(smem_u32(&ctl.full[last % kWStages]), (last / kWStages) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer: tile tt into accumulator tt mod 4
+        if (lane == 0) {
+            StepWalk<MAP> walk(gx, total, nb2, nb);
+            int X0, Y;
+            uint32_t it = 0, tt = 0;
+            bool ok = true;
+            while (ok && !*fail && walk.next(X0, Y)) {
+                for (int t = 0; t < 2 && ok; ++t, ++tt) {
+                    const uint32_t acc = tt & 3, use = tt >> 2;
+                    if (!(ok = mbar_wait(smem_u32(&ctl.tempty[acc]), (use & 1) ^ 1, fail, &g_error))) break;
+                    tc_fence_after();
+                    const uint32_t dtm = tmem + acc * TN;
+                    for (int c = 0; c < nchunks; ++c, ++it) {
+                        const int s = (int)(it % kWStages);
+                        if (!(ok = mbar_wait(smem_u32(&ctl.full[s]), (it / kWStages) & 1, fail, &g_error)))
+                            break;
+                        tc_fence_after();
+                        const uint32_t src = s_stages + s * STAGE_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < KC / 16; ++ks) {
+                            const uint32_t koff = ks * 32;
+                            const uint64_t ah = sw128_desc(src + 0 * TILE_BYTES + koff);
+                            const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
+                            const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
+                            const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
+                            mma_bf16_afill(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                            mma_bf16_alast(dtm, ah, bl, kIdesc, 1u);
+                            mma_bf16(dtm, al, bh, kIdesc, 1u);
+                        }
+                        mma_commit(smem_u32(&ctl.empty[s]));
+                    }
+                    if (ok) mma_commit(smem_u32(&ctl.tfull[acc]));
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: 8 warps; warp (quarter, h) reads TMEM lanes
+        // 32 quarter .. +31 of the step's tile h (columns 128 h .. of the step)
+        const int ew = warp - 2;                 // 0..7
+        const int quarter = warp & 3;
+        const int h = ew >> 2;
+        const int r = 32 * quarter + lane;       // this thread's row in the step
+        float *stg = stg_all + quarter * 32 * kWPitch;   // shared with the other tile's warp
+        float *nc = &ctl.ncol[ew][0];
+        StepWalk<MAP> walk(gx, total, nb2, nb);
+        int X0, Y;
+        uint32_t tt = 0, st = 0;   // tiles, steps
+        // norms of a step's columns (this warp's tile, four per lane) and of
+        // this thread's row, loaded a step ahead
+        auto load_step = [&](int X0s, int Ys, float (&cn)[4], float &rn) {
+            const int64_t cb = (int64_t)X0s * TN + TN * h + lane, ii = (int64_t)Ys * TM + r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cn[q] = cb + 32 * q < n ? __ldg(nrm + cb + 32 * q) : 0.0f;
+            rn = ii < n ? __ldg(nrm + ii) : 0.0f;
+        };
+        bool have = walk.next(X0, Y);
+        float pcn[4] = {0.f, 0.f, 0.f, 0.f}, prn = 0.f;
+        if (have) load_step(X0, Y, pcn, prn);
+        while (have && !*fail) {
+            int X0n, Yn;
+            const bool hn = walk.next(X0n, Yn);
+            float ncn[4] = {0.f, 0.f, 0.f, 0.f}, nrn = 0.f;
+            if (hn) load_step(X0n, Yn, ncn, nrn);
+            const uint32_t acc = (tt + h) & 3, use = (tt + h) >> 2;
+            const int64_t row0 = (int64_t)Y * TM, col0 = (int64_t)X0 * TN, colh = col0 + TN * h;
+            __syncwarp();   // the previous step's reads of nc are done
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nc[32 * q + lane] = pcn[q];
+            const int64_t i = row0 + r;
+            const float ni = prn;
+            // staging row of row i: step column c at myrow[c], offset by the
+            // floats from the row start back to the previous 16-byte boundary of out
+            const int64_t grow = i * (i + 1) / 2 + col0;
+            const int shift = (int)((reinterpret_cast<uintptr_t>(out + grow) >> 2) & 3);
+            float *myrow = stg + lane * kWPitch + shift;
+            __syncwarp();
+            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), use & 1, fail, &g_error)) break;
+            tc_fence_after();
+            // part p: columns 64 p .. 64 p + 63 of this warp's tile.  Part 0 is
+            // read and formed before the wait for the staging, so that it
+            // overlaps the previous step's copies.
+            bool staged_ok = true;
+#pragma unroll 1
+            for (int part = 0; part < 2; ++part) {
+                float v0[32], v1[32];
+                const uint32_t taddr =
+                    tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * part);
+                tmem_ld64(taddr, v0, v1);
+                const float *ncp = nc + 64 * part;
+                // D = |x_i|^2 + |x_j|^2 - 2 g; flag entries with D < (|x_i|^2 + |x_j|^2)/64
+                float lows[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    const float4 a = *reinterpret_cast<const float4 *>(ncp + q);
+                    const float4 b = *reinterpret_cast<const float4 *>(ncp + 32 + q);
+                    const float sa[4] = {ni + a.x, ni + a.y, ni + a.z, ni + a.w};
+                    const float sb[4] = {ni + b.x, ni + b.y, ni + b.z, ni + b.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        v0[q + k] = fmaf(-2.0f, v0[q + k], sa[k]);
+                        v1[q + k] = fmaf(-2.0f, v1[q + k], sb[k]);
+                        lows[k] = fminf(lows[k], fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
+                                                       fmaf(-0.015625f, sb[k], v1[q + k])));
+                    }
+                }
+                const float low = fminf(fminf(lows[0], lows[1]), fminf(lows[2], lows[3]));
+                if (__any_sync(0xffffffffu, low < 0.0f)) {
+#pragma unroll
+                    for (int q = 0; q < 64; ++q) {
+                        float &vq = q < 32 ? v0[q] : v1[q - 32];
+                        const int64_t j = colh + 64 * part + q;
+                        const float sj = ni + ncp[q];
+                        if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
+                    }
+                }
+                // the staging is free once both warps' copies of the previous step have read it
+                if (part == 0 && st > 0) {
+                    bulk_wait_read();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl.sfree[quarter]));
+                    if (!mbar_wait(smem_u32(&ctl.sfree[quarter]), (st - 1) & 1, fail, &g_error)) {
+                        staged_ok = false;
+                        break;
+                    }
+                }
+                float *dst = myrow + TN * h + 64 * part;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) { dst[q] = v0[q]; dst[32 + q] = v1[q]; }
+            }
+            if (!staged_ok) break;
+            // the accumulator is read: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            // D_ii = 0 exactly (the diagonal column, where it falls in this warp's tile)
+            const int64_t cdiag = i - colh;
+            if (cdiag >= 0 && cdiag < TN) myrow[TN * h + (int)cdiag] = 0.0f;
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&ctl.sfull[quarter]));
+            if (!mbar_wait(smem_u32(&ctl.sfull[quarter]), st & 1, fail, &g_error)) break;
+            // One bulk copy per row of the step (lanes 0-15 of this warp: rows
+            // 16 h .. 16 h + 15 of the quarter): the columns j <= i, j < n of
+            // the 256, its ragged head and tail (at most 3 floats each) by
+            // plain stores.
+            const int rr = 16 * h + lane;
+            const int64_t ir = row0 + 32 * quarter + rr;
+            if (lane < 16 && ir < n) {
+                const int64_t lim = (ir + 1 < n ? ir + 1 : n) - col0;
+                const int len = lim <= 0 ? 0 : (lim >= 2 * TN ? 2 * TN : (int)lim);
+                const int64_t gb = ir * (ir + 1) / 2 + col0;
+                const int sh = (int)((reinterpret_cast<uintptr_t>(out + gb) >> 2) & 3);
+                const float *sr = stg + rr * kWPitch + sh;   // column c at sr[c]
+                const int hd = ((4 - sh) & 3) < len ? ((4 - sh) & 3) : len;
+                const int body = (len - hd) & ~3;
+                if (body > 0) {
+                    bulk_store(out + gb + hd, smem_u32(sr + hd), (uint32_t)body * 4);
+                    bulk_commit();
+                }
+                for (int e = 0; e < hd; ++e) out[gb + e] = sr[e];
+                for (int e = hd + body; e < len; ++e) out[gb + e] = sr[e];
+            }
+            tt += 2;
+            ++st;
+            X0 = X0n; Y = Yn; have = hn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pcn[q] = ncn[q];
+            prn = nrn;
+        }
+    }
+    bulk_wait_all();   // staging rows must stay valid until the copies have read them
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, kWAccCols);
+    }
+}
+
+}  // namespace wide
 
 static int smem_optin() {
     int dev = 0;
@@ -412,12 +707,12 @@ static int smem_optin() {
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA, false>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX, false>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR, false>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA, true>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX, true>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR, true>, a, PSMEM_BYTES)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LAMBDA>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_BBOX>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LINEAR>, a, wide::WSMEM_BYTES)) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -450,7 +745,7 @@ static int64_t max_pairs(int sms) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int num = 0;
-        if (cudaOccupancyMaxActiveClusters(&num, k_edm_umma<MAP_LAMBDA, true>, &cfg) != cudaSuccess || num < 1) {
+        if (cudaOccupancyMaxActiveClusters(&num, k_edm_umma<MAP_LAMBDA>, &cfg) != cudaSuccess || num < 1) {
             cudaGetLastError();
             num = sms / 2;
         }
@@ -493,15 +788,19 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
     if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
     if (!use_multicast(d)) {
-        const int64_t total = g.gx * g.gy;
-        const unsigned ctas = (unsigned)(total < sms ? total : sms);
+        // one CTA per SM over the map's grid of 256 x 256 super-blocks, rows of 256 columns
+        const int64_t nb2 = (nb + 1) / 2;
+        const Grid g2 = grid2(nb2, map);
+        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
+        const int64_t total2 = g2.gx * g2.gy;
+        const unsigned ctas = (unsigned)(total2 < sms ? total2 : sms);
         prof_begin(s);
         if (map == MAP_LAMBDA)
-            k_edm_umma<MAP_LAMBDA, false><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb, (int)g.gx, total);
+            wide::k_edm_umma_wide<MAP_LAMBDA><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else if (map == MAP_BBOX)
-            k_edm_umma<MAP_BBOX, false><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb, (int)g.gx, total);
+            wide::k_edm_umma_wide<MAP_BBOX><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else
-            k_edm_umma<MAP_LINEAR, false><<<ctas, kThreads, PSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb, (int)g.gx, total);
+            wide::k_edm_umma_wide<MAP_LINEAR><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
     } else {
         // two-CTA clusters over the map's grid of 256 x 256 super-blocks
         const int64_t nb2 = (nb + 1) / 2;
@@ -525,11 +824,11 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
         prof_begin(s);
         cudaError_t e;
         if (map == MAP_LAMBDA)
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LAMBDA, true>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LAMBDA>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else if (map == MAP_BBOX)
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_BBOX, true>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_BBOX>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LINEAR, true>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LINEAR>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         if (e != cudaSuccess) { prof_end(s); return cuda_status(e); }
     }
     prof_end(s);

@@ -140,8 +140,11 @@ def test_edm_bf16x3_scale_config(gpu, oracle):
     torch.cuda.empty_cache()
 
 
-def test_edm_bf16x3_maps_agree(gpu):
-    x = to_gpu(synth.normal(1500, 128, seed=33))
+@pytest.mark.parametrize("n,d", [(1500, 128), (1501, 64)])
+def test_edm_bf16x3_maps_agree(gpu, n, d):
+    """Both tensor-core kernels (two-CTA clusters for d >= 128, rows of 256
+    columns below) write the same entries under every map."""
+    x = to_gpu(synth.normal(n, d, seed=33))
     a = gpu.edm_packed(x, "lambda", "bf16x3")
     assert torch.equal(a, gpu.edm_packed(x, "bbox", "bf16x3"))
     assert torch.equal(a, gpu.edm_packed(x, "linear", "bf16x3"))
