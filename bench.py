@@ -184,12 +184,12 @@ def oracle_energy_rate(x, seconds_min=10.0, i_hi=None):
         run = lambda: oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)  # noqa: E731
     reps, t0 = 0, time.perf_counter()
     while True:
-        run()
+        val = run()
         reps += 1
         el = time.perf_counter() - t0
         if el >= seconds_min:
             break
-    return units * reps / el, units, reps, el
+    return units * reps / el, units, reps, el, val
 
 
 def reference_arm(args):
@@ -616,10 +616,14 @@ def our_arm(args):
         "clocks": clk,
     }
     if rank == 0 and world == 1:
-        rate, u, reps, el = oracle_energy_rate(xh)
+        rate, u, reps, el, e_ref = oracle_energy_rate(xh)
         line["cpu_baseline"] = {"value": rate, "unit": "triplets/s", "cores": 1, "kind": "oracle",
                                 "sample": f"the whole n=1024 sum ({u} triples) x{reps}, {el:.1f} s, "
                                           "FP64 C oracle, 1 thread"}
+        # the timed step's energy against the oracle's sum (parity of the measured run)
+        e_gpu = float(e.item())
+        line["accuracy"] = {"energy": e_gpu, "energy_oracle": e_ref,
+                            "rel_err": abs(e_gpu - e_ref) / abs(e_ref), "tolerance": 1e-6}
     if rows is not None:
         line["rows"] = rows
     if rank == 0:
