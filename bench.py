@@ -269,7 +269,7 @@ def row_edm_n1024_d3(torch, sx, peaks):
     reps = 1000
     r = {"unit": "pairs/s", "pairs": pairs, "prec": "fp32",
          "note": f"CUDA graph of {reps} launches per timed step; output L2-resident"}
-    for mp in ("lambda", "bbox", "linear"):
+    for mp in ("lambda", "bbox", "linear", "rb"):
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -287,10 +287,11 @@ def row_edm_n1024_d3(torch, sx, peaks):
         r[mp + "_hbm_gbs"] = 4 * pairs / (ms / 1e3) / 1e9
         del g
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    r["lambda_vs_rb"] = r["lambda"] / r["rb"]
     return r
 
 
-def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox")):
+def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox", "rb")):
     n, d = x.shape
     o = torch.empty(n * (n + 1) // 2, device="cuda")
     pairs = o.numel()
@@ -301,6 +302,8 @@ def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox")):
         r[mp] = pairs / (ms / 1e3)
         r[mp + "_ms"] = ms
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    if "rb" in r:
+        r["lambda_vs_rb"] = r["lambda"] / r["rb"]
     t = r["lambda_ms"] / 1e3
     r["hbm_gbs_lambda"] = 4.0 * pairs / t / 1e9          # packed output written
     r["hbm_frac_lambda"] = r["hbm_gbs_lambda"] / peaks["hbm_gbs"]
@@ -397,7 +400,7 @@ def row_stress_n65536_d64(torch, sx, peaks):
     r["bwd_tflops"] = 8 * d * r["bwd_lambda"] / 1e12
     r["fwd_fp32_frac"] = r["fwd_tflops"] / fp32
     r["bwd_fp32_frac"] = r["bwd_tflops"] / fp32
-    r.update(_stress_tensor(torch, sx, peaks, x, y, ("lambda", "bbox", "linear")))
+    r.update(_stress_tensor(torch, sx, peaks, x, y, ("lambda", "bbox", "linear", "rb")))
     return r
 
 
@@ -464,12 +467,15 @@ def _cover_row(torch, sx, m, n, rho):
     idle = torch.empty(1, dtype=torch.int64, device="cuda")
     fn = sx.simplex_map2 if m == 2 else sx.simplex_map3
     r = {"unit": "elements/s", "elements": vol, "rho": rho}
-    for mp in ("lambda", "bbox", "linear"):
+    maps = ("lambda", "bbox", "linear", "rb") if m == 2 else ("lambda", "bbox", "linear")
+    for mp in maps:
         ms = _median_ms(torch, lambda: fn(n, rho, mp, count, idle), 5)
         r[mp] = vol / (ms / 1e3)
         r[mp + "_ms"] = ms
         r[mp + "_idle_threads"] = int(idle.item())
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    if m == 2:
+        r["lambda_vs_rb"] = r["lambda"] / r["rb"]
     return r
 
 

@@ -26,7 +26,14 @@
  *                          exiting at once (Sec. I);
  *      SIMPLEX_MAP_LINEAR  linear enumeration inverted with square / cube
  *                          roots plus an exact integer fix-up (Sec. I and
- *                          Sec. II on the earlier block-space maps).
+ *                          Sec. II on the earlier block-space maps);
+ *      SIMPLEX_MAP_RB      rectangular box, 2-simplex only (Sec. II: the RB
+ *                          strategy for packed triangular matrices applied
+ *                          to the parallel space): the block triangle cut
+ *                          at half height, grid row k holding triangle rows
+ *                          floor(nb/2) + k and floor(nb/2) - 1 - k, no idle
+ *                          block for any nb.  The 3-simplex entry points
+ *                          (simplex_map3, ATM) return SIMPLEX_EINVAL for it.
  *  - Return value: a simplex_status.  Argument errors are detected before
  *    anything is enqueued and leave outputs untouched.  A failed launch
  *    returns SIMPLEX_ECUDA; simplex_last_cuda_error() gives the cudaError_t.
@@ -60,7 +67,8 @@ typedef enum {
 typedef enum {
     SIMPLEX_MAP_LAMBDA = 0,
     SIMPLEX_MAP_BBOX = 1,
-    SIMPLEX_MAP_LINEAR = 2
+    SIMPLEX_MAP_LINEAR = 2,
+    SIMPLEX_MAP_RB = 3
 } simplex_map;
 
 typedef enum {
@@ -76,7 +84,7 @@ typedef enum {
 } simplex_op;
 
 /* ABI version of this header (bumped on any signature change or added entry
- * point; 2 added simplex_stress_fwd_bwd). */
+ * point or map; 2 added simplex_stress_fwd_bwd, 3 SIMPLEX_MAP_RB). */
 int simplex_abi_version(void);
 
 /* Human-readable text of a status code (static storage). */
@@ -95,7 +103,8 @@ int simplex_block_rho(int op, int64_t d, int prec);
  * m-simplex (m = 2 or 3), or -1 on bad arguments.  Grid shapes: LAMBDA m=2
  * (p/2) x p, m=3 (p/2) x (p/2) x (p/2 + p/4 + 2) with p the power of two
  * >= max(nb, 2) (the last two z-layers are the plane J = K, mapped by the
- * 2-simplex map); BBOX nb^m; LINEAR nb(nb+1)/2 or nb(nb+1)(nb+2)/6.
+ * 2-simplex map); BBOX nb^m; LINEAR nb(nb+1)/2 or nb(nb+1)(nb+2)/6; RB
+ * (m=2) (nb + 1 - nb mod 2) x ceil(nb/2) = nb(nb+1)/2.
  */
 int64_t simplex_grid_blocks(int m, int64_t nb, int map);
 

@@ -36,8 +36,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-MAP_LAMBDA, MAP_BBOX, MAP_LINEAR = 0, 1, 2
-MAPS = {"lambda": MAP_LAMBDA, "bbox": MAP_BBOX, "linear": MAP_LINEAR}
+MAP_LAMBDA, MAP_BBOX, MAP_LINEAR, MAP_RB = 0, 1, 2, 3
+MAPS = {"lambda": MAP_LAMBDA, "bbox": MAP_BBOX, "linear": MAP_LINEAR, "rb": MAP_RB}
 
 
 def build(force: bool = False) -> str:

@@ -11,8 +11,10 @@
  * What is here, each written from its definition:
  *   - block-space map tables built by *recursive construction* of the sets
  *     S_n^2 (Sec. III-A, Eq. 5-9) and the two-branch S_n^3 (Sec. III-C,
- *     "Alternative Map for 3-Simplices"), the bounding box (Sec. I, f(x)=x)
- *     and the linear enumeration g (Sec. I, Eq. 2 expanded);
+ *     "Alternative Map for 3-Simplices"), the bounding box (Sec. I, f(x)=x),
+ *     the linear enumeration g (Sec. I, Eq. 2 expanded) and, for m = 2, the
+ *     rectangular box (Sec. II: the RB strategy for packed triangular
+ *     matrices, applied to the parallel space) laid out row by row;
  *   - thread-level coverage counts over the discrete orthogonal simplices
  *     Delta_n^2 and Delta_n^3 (Eq. 1-2, volumes of Sec. III-A / III-B);
  *   - the packed Euclidean distance matrix (Sec. I: EDM as a 2-simplex
@@ -37,7 +39,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { MAP_LAMBDA = 0, MAP_BBOX = 1, MAP_LINEAR = 2 };
+enum { MAP_LAMBDA = 0, MAP_BBOX = 1, MAP_LINEAR = 2, MAP_RB = 3 };
 
 static int64_t pow2_at_least(int64_t v)
 {
@@ -56,6 +58,11 @@ int64_t oracle_grid2(int64_t nb, int map, int64_t *gx, int64_t *gy)
         *gx = p / 2; *gy = p;
     } else if (map == MAP_BBOX) {
         *gx = nb; *gy = nb;
+    } else if (map == MAP_RB) {
+        /* one pair of triangle rows per grid row, each pair nb + 1 (nb
+         * even) or nb (nb odd) blocks long */
+        *gy = (nb + 1) / 2;
+        *gx = (nb % 2 == 0) ? nb + 1 : nb;
     } else {
         *gx = nb * (nb + 1) / 2; *gy = 1;
     }
@@ -110,6 +117,19 @@ int64_t oracle_table2(int64_t nb, int map, int32_t *tab)
         for (int64_t wy = 0; wy < gy; ++wy)
             for (int64_t wx = 0; wx <= wy; ++wx)
                 put2(tab + 4 * (wy * gx + wx), 0, wx, wy, nb);
+    } else if (map == MAP_RB) {
+        /* Rectangular box: cut the block triangle (rows y = 0 .. nb-1, row y
+         * holding columns 0 .. y) at half height, h = floor(nb/2).  Grid row
+         * k is filled left to right with the blocks of triangle row h + k and
+         * then, where that row is shorter than the grid, with the blocks of
+         * triangle row h - 1 - k. */
+        int64_t h = nb / 2;
+        for (int64_t k = 0; k < gy; ++k) {
+            int64_t w = k * gx;
+            for (int64_t x = 0; x <= h + k; ++x) put2(tab + 4 * (w++), 0, x, h + k, nb);
+            if (h - 1 - k >= 0)
+                for (int64_t x = 0; x <= h - 1 - k; ++x) put2(tab + 4 * (w++), 0, x, h - 1 - k, nb);
+        }
     } else {
         /* linear enumeration of the lower block triangle, row by row */
         int64_t l = 0;

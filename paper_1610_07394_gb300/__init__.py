@@ -25,7 +25,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsimplex.so")
 
-MAPS = {"lambda": 0, "bbox": 1, "linear": 2}
+MAPS = {"lambda": 0, "bbox": 1, "linear": 2, "rb": 3}
 PRECS = {"fp32": 0, "bf16x3": 1, "auto": 2}
 OPS = {"map2": 0, "map3": 1, "edm": 2, "atm_energy": 3, "atm_forces": 4,
        "stress_fwd": 5, "stress_bwd": 6, "stress_fwd_bwd": 7}

@@ -105,7 +105,7 @@ int reduce_partials(const double *partials, int64_t count, double *tmp, double *
 
 using namespace sx;
 
-extern "C" int simplex_abi_version(void) { return 2; }
+extern "C" int simplex_abi_version(void) { return 3; }
 
 extern "C" int simplex_profile(int on) {
     std::lock_guard<std::mutex> lk(g_prof.mu);
@@ -176,7 +176,10 @@ extern "C" int simplex_block_rho(int op, int64_t d, int prec) {
 }
 
 extern "C" int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map, int prec) {
-    if (n < 1 || d < 1 || map < MAP_LAMBDA || map > MAP_LINEAR) return -1;
+    if (n < 1 || d < 1 || map < MAP_LAMBDA || map > MAP_RB) return -1;
+    // the rectangular box has no 3-simplex form
+    const bool m3 = op == SIMPLEX_OP_MAP3 || op == SIMPLEX_OP_ATM_ENERGY || op == SIMPLEX_OP_ATM_FORCES;
+    if (m3 && map == MAP_RB) return -1;
     switch (op) {
         case SIMPLEX_OP_MAP2:
         case SIMPLEX_OP_MAP3: return 0;

@@ -20,6 +20,7 @@ SX_HD void table_entry(int map, const Grid &g, int nb, int64_t w, int32_t *e) {
     if (M == 2) {
         List2 L = map == MAP_LAMBDA ? decode2_lambda(wx, wy, nb)
                 : map == MAP_BBOX   ? decode2_bbox(wx, wy, nb)
+                : map == MAP_RB     ? decode2_rb(wx, wy, nb)
                                     : decode2_linear(w, nb);
         for (int t = 0; t < L.cnt; ++t) { e[2 * t] = L.x[t]; e[2 * t + 1] = L.y[t]; }
     } else {
@@ -102,14 +103,17 @@ __global__ void k_cover3(int64_t n, int rho, int nb, int p, int32_t *count,
     if (lead && s_idle) atomicAdd(idle, (unsigned long long)s_idle);
 }
 
-static bool valid_map(int map) { return map >= MAP_LAMBDA && map <= MAP_LINEAR; }
+// Every map has an m = 2 form; the rectangular box has no m = 3 form.
+static bool valid_map(int m, int map) {
+    return map >= MAP_LAMBDA && (map <= MAP_LINEAR || (m == 2 && map == MAP_RB));
+}
 
 }  // namespace sx
 
 using namespace sx;
 
 extern "C" int64_t simplex_grid_blocks(int m, int64_t nb, int map) {
-    if ((m != 2 && m != 3) || nb < 1 || nb > (1 << 20) || !valid_map(map)) return -1;
+    if ((m != 2 && m != 3) || nb < 1 || nb > (1 << 20) || !valid_map(m, map)) return -1;
     Grid g = m == 2 ? grid2(nb, map) : grid3(nb, map);
     return g.gx * g.gy * g.gz;
 }
@@ -147,7 +151,7 @@ extern "C" int simplex_map_blocks(int m, int64_t nb, int map, int32_t *out, void
 extern "C" int simplex_map2(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
                             void *stream) {
     if (rho == 0) rho = 16;
-    if (n < 1 || rho < 1 || rho > 32 || !valid_map(map) || !count || !idle) return SIMPLEX_EINVAL;
+    if (n < 1 || rho < 1 || rho > 32 || !valid_map(2, map) || !count || !idle) return SIMPLEX_EINVAL;
     if (!aligned(count, 4) || !aligned(idle, 8)) return SIMPLEX_EALIGN;
     const int64_t nb = (n + rho - 1) / rho;
     if (n > (int64_t)1 << 31) return SIMPLEX_EOVERFLOW;
@@ -162,6 +166,7 @@ extern "C" int simplex_map2(int64_t n, int rho, int map, int32_t *count, int64_t
     prof_begin(s);
     if (map == MAP_LAMBDA) k_cover2<MAP_LAMBDA><<<dim_of(g), blk, 0, s>>>(n, rho, (int)nb, count, id);
     else if (map == MAP_BBOX) k_cover2<MAP_BBOX><<<dim_of(g), blk, 0, s>>>(n, rho, (int)nb, count, id);
+    else if (map == MAP_RB) k_cover2<MAP_RB><<<dim_of(g), blk, 0, s>>>(n, rho, (int)nb, count, id);
     else k_cover2<MAP_LINEAR><<<dim_of(g), blk, 0, s>>>(n, rho, (int)nb, count, id);
     prof_end(s);
     note_launches(1);
@@ -171,7 +176,7 @@ extern "C" int simplex_map2(int64_t n, int rho, int map, int32_t *count, int64_t
 extern "C" int simplex_map3(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
                             void *stream) {
     if (rho == 0) rho = 8;
-    if (n < 1 || rho < 1 || rho > 10 || !valid_map(map) || !count || !idle) return SIMPLEX_EINVAL;
+    if (n < 1 || rho < 1 || rho > 10 || !valid_map(3, map) || !count || !idle) return SIMPLEX_EINVAL;
     if (!aligned(count, 4) || !aligned(idle, 8)) return SIMPLEX_EALIGN;
     if (n > 3000000) return SIMPLEX_EOVERFLOW;   // keeps k(k+1)(k+2) < 2^63
     const int64_t nb = (n + rho - 1) / rho;

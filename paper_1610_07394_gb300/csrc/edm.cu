@@ -65,7 +65,7 @@ using namespace sx;
 
 extern "C" int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *out, int map,
                                   int prec, void *workspace, int64_t ws_bytes, void *stream) {
-    if (n < 1 || d < 1 || !x || !out || map < MAP_LAMBDA || map > MAP_LINEAR) return SIMPLEX_EINVAL;
+    if (n < 1 || d < 1 || !x || !out || map < MAP_LAMBDA || map > MAP_RB) return SIMPLEX_EINVAL;
     if (prec < SIMPLEX_PREC_FP32 || prec > SIMPLEX_PREC_AUTO) return SIMPLEX_EINVAL;
     if (!aligned(x, 4) || !aligned(out, 4)) return SIMPLEX_EALIGN;
     if (d > (1 << 24) || n > ((int64_t)1 << 31) || n * d > ((int64_t)1 << 40)) return SIMPLEX_EOVERFLOW;
@@ -78,6 +78,7 @@ extern "C" int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *o
     prof_begin(s);
     if (map == MAP_LAMBDA) k_edm_simt<MAP_LAMBDA><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
     else if (map == MAP_BBOX) k_edm_simt<MAP_BBOX><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
+    else if (map == MAP_RB) k_edm_simt<MAP_RB><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
     else k_edm_simt<MAP_LINEAR><<<dim_of(g), 256, 0, s>>>(n, (int)d, x, out, (int)nb);
     prof_end(s);
     note_launches(1);

@@ -710,9 +710,11 @@ static int smem_optin() {
         if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_RB>, a, PSMEM_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LAMBDA>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_BBOX>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LINEAR>, a, wide::WSMEM_BYTES)) != cudaSuccess)
+            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LINEAR>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_RB>, a, wide::WSMEM_BYTES)) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -799,6 +801,8 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
             wide::k_edm_umma_wide<MAP_LAMBDA><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else if (map == MAP_BBOX)
             wide::k_edm_umma_wide<MAP_BBOX><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        else if (map == MAP_RB)
+            wide::k_edm_umma_wide<MAP_RB><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else
             wide::k_edm_umma_wide<MAP_LINEAR><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
     } else {
@@ -827,6 +831,8 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
             e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LAMBDA>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else if (map == MAP_BBOX)
             e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_BBOX>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        else if (map == MAP_RB)
+            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_RB>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         else
             e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LINEAR>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         if (e != cudaSuccess) { prof_end(s); return cuda_status(e); }

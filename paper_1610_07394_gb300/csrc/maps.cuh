@@ -27,6 +27,14 @@
 //    authors' earlier work, Sec. II): a 1-D grid over the row-major
 //    enumeration, inverted with sqrtf / cbrtf and then fixed up exactly in
 //    integer arithmetic.
+//  * rectangular box, m = 2 only (Sec. II: the RB strategy for packed
+//    triangular matrices, applied to the parallel space): the lower triangle
+//    of nb blocks per side is cut at half height h = floor(nb / 2) and its top
+//    rows are laid after the bottom ones, grid row k holding triangle row
+//    h + k (columns 0 .. h + k) and then row h - 1 - k (columns
+//    0 .. h - 1 - k): a grid of (nb + 1 - nb mod 2) x ceil(nb / 2) blocks,
+//    exactly the triangle's nb (nb + 1) / 2 for every nb, decoded with one
+//    comparison.
 //
 // Every function is __host__ __device__ so the host-side decode table can be
 // compared against an independent construction without a GPU.
@@ -42,7 +50,7 @@
 
 namespace sx {
 
-enum MapKind { MAP_LAMBDA = 0, MAP_BBOX = 1, MAP_LINEAR = 2 };
+enum MapKind { MAP_LAMBDA = 0, MAP_BBOX = 1, MAP_LINEAR = 2, MAP_RB = 3 };
 
 // floor(log2 v) for v >= 1: (word bits - 1) - clz(v).
 SX_HD int floor_log2(uint32_t v) {
@@ -131,6 +139,16 @@ SX_HD List2 decode2_linear(int64_t l, int nb) {
     return L;
 }
 
+// Rectangular box: grid row wy holds triangle row h + wy, then row h - 1 - wy.
+SX_HD List2 decode2_rb(uint32_t wx, uint32_t wy, int nb) {
+    List2 L;
+    L.cnt = 0; L.pair = false; L.d0 = L.d1 = -1;
+    const int h = nb >> 1, yb = h + (int)wy;
+    if ((int)wx <= yb) push2(L, (int)wx, yb, nb);
+    else push2(L, (int)wx - yb - 1, h - 1 - (int)wy, nb);
+    return L;
+}
+
 // ---------------------------------------------------------------- m = 3
 
 SX_HD void cube3(List3 &L, int h, int off, int s, int u, int v, int nb) {
@@ -195,6 +213,8 @@ SX_HD Grid grid2(int64_t nb, int map) {
         g.p = (int)p; g.gx = p / 2; g.gy = p;
     } else if (map == MAP_BBOX) {
         g.gx = nb; g.gy = nb;
+    } else if (map == MAP_RB) {
+        g.gx = nb + 1 - (nb & 1); g.gy = (nb + 1) / 2;
     } else {
         g.gx = nb * (nb + 1) / 2; g.gy = 1;
     }
@@ -208,6 +228,8 @@ SX_HD Grid grid3(int64_t nb, int map) {
         g.p = (int)p; g.gx = p / 2; g.gy = p / 2; g.gz = p / 2 + p / 4 + 2;
     } else if (map == MAP_BBOX) {
         g.gx = nb; g.gy = nb; g.gz = nb;
+    } else if (map == MAP_RB) {
+        g.gx = 0; g.gy = 0; g.gz = 0;   // no 3-simplex form (callers reject it)
     } else {
         g.gx = nb * (nb + 1) * (nb + 2) / 6; g.gy = 1; g.gz = 1;
     }
@@ -219,6 +241,7 @@ template <int MAP>
 SX_HD List2 decode2(uint32_t wx, uint32_t wy, int nb) {
     if (MAP == MAP_LAMBDA) return decode2_lambda(wx, wy, nb);
     if (MAP == MAP_BBOX) return decode2_bbox(wx, wy, nb);
+    if (MAP == MAP_RB) return decode2_rb(wx, wy, nb);
     return decode2_linear((int64_t)wx, nb);
 }
 

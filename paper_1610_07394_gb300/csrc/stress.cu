@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_stress_bwd(int64_t n, int d, const floa
 
 static int stress_check(int64_t n, int64_t d, const float *x, const float *y, int map, int prec,
                         Grid &g, int64_t &nb) {
-    if (n < 1 || d < 1 || !x || !y || map < MAP_LAMBDA || map > MAP_LINEAR) return SIMPLEX_EINVAL;
+    if (n < 1 || d < 1 || !x || !y || map < MAP_LAMBDA || map > MAP_RB) return SIMPLEX_EINVAL;
     if (prec < SIMPLEX_PREC_FP32 || prec > SIMPLEX_PREC_AUTO) return SIMPLEX_EINVAL;
     if (prec == SIMPLEX_PREC_BF16X3 && !stress_umma_ok(d)) return SIMPLEX_EUNSUPPORTED;
     if (!aligned(x, 4) || !aligned(y, 4)) return SIMPLEX_EALIGN;
@@ -311,9 +311,11 @@ static int stress_optin() {
         if ((e = cudaFuncSetAttribute(k_stress_fwd<MAP_LAMBDA>, a, kStressSmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_stress_fwd<MAP_BBOX>, a, kStressSmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_stress_fwd<MAP_LINEAR>, a, kStressSmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_stress_fwd<MAP_RB>, a, kStressSmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_stress_bwd<MAP_LAMBDA>, a, kStressSmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_stress_bwd<MAP_BBOX>, a, kStressSmem)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_stress_bwd<MAP_LINEAR>, a, kStressSmem)) != cudaSuccess)
+            (e = cudaFuncSetAttribute(k_stress_bwd<MAP_LINEAR>, a, kStressSmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_stress_bwd<MAP_RB>, a, kStressSmem)) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -345,6 +347,7 @@ extern "C" int simplex_stress_fwd(int64_t n, int64_t d, const float *x, const fl
     prof_begin(s);
     if (map == MAP_LAMBDA) k_stress_fwd<MAP_LAMBDA><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, d_out, (int)nb, partials);
     else if (map == MAP_BBOX) k_stress_fwd<MAP_BBOX><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, d_out, (int)nb, partials);
+    else if (map == MAP_RB) k_stress_fwd<MAP_RB><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, d_out, (int)nb, partials);
     else k_stress_fwd<MAP_LINEAR><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, d_out, (int)nb, partials);
     prof_end(s);
     note_launches(1);
@@ -378,6 +381,7 @@ static int stress_grad(int64_t n, int64_t d, const float *x, const float *y, dou
     prof_begin(s);
     if (map == MAP_LAMBDA) k_stress_bwd<MAP_LAMBDA><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
     else if (map == MAP_BBOX) k_stress_bwd<MAP_BBOX><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
+    else if (map == MAP_RB) k_stress_bwd<MAP_RB><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
     else k_stress_bwd<MAP_LINEAR><<<dim_of(g), 256, kStressSmem, s>>>(n, (int)d, x, y, scale4, (int)nb, grad, partials);
     prof_end(s);
     note_launches(1);

@@ -875,6 +875,7 @@ static cudaError_t optin_bwd() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_stress_umma_bwd<MAP_LAMBDA>, a, SMEM_BYTES)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_stress_umma_bwd<MAP_BBOX>, a, SMEM_BYTES)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_stress_umma_bwd<MAP_RB>, a, SMEM_BYTES)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_stress_umma_bwd<MAP_LINEAR>, a, SMEM_BYTES);
 }
 
@@ -883,6 +884,7 @@ static cudaError_t optin_fwd256() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_LAMBDA>, a, f256::SMEM2)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_BBOX>, a, f256::SMEM2)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_RB>, a, f256::SMEM2)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(f256::k_stress_umma_fwd<MAP_LINEAR>, a, f256::SMEM2);
 }
 
@@ -911,6 +913,9 @@ static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUte
     else if (map == MAP_BBOX)
         k_stress_umma_bwd<MAP_BBOX><<<ctas, kThreads, SMEM_BYTES, s>>>(
             m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
+    else if (map == MAP_RB)
+        k_stress_umma_bwd<MAP_RB><<<ctas, kThreads, SMEM_BYTES, s>>>(
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
     else
         k_stress_umma_bwd<MAP_LINEAR><<<ctas, kThreads, SMEM_BYTES, s>>>(
             m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
@@ -937,6 +942,9 @@ static cudaError_t launch_fwd(int map, unsigned ctas, cudaStream_t s, const CUte
                                   nb2, gx, total, partials);
     if (map == MAP_BBOX)
         return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_BBOX>, m[0], m[1], m[2], m[3], a, n, d, nb,
+                                  nb2, gx, total, partials);
+    if (map == MAP_RB)
+        return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_RB>, m[0], m[1], m[2], m[3], a, n, d, nb,
                                   nb2, gx, total, partials);
     return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_LINEAR>, m[0], m[1], m[2], m[3], a, n, d, nb,
                               nb2, gx, total, partials);

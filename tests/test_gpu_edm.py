@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("n,d", [(1, 3), (2, 1), (31, 3), (33, 7), (100, 3), (257, 33),
                                  (600, 64), (1000, 5)])
 def test_edm_small(gpu, oracle, mp, n, d):
@@ -76,11 +76,12 @@ def test_edm_scale_config_sampled(gpu, oracle):
 
 
 def test_edm_maps_agree_bitwise(gpu):
-    """The three maps run the same tile body, so their outputs are identical."""
+    """The maps run the same tile body, so their outputs are identical."""
     x = to_gpu(synth.normal(3000, 16, seed=23))
     a = gpu.edm_packed(x, "lambda")
     assert torch.equal(a, gpu.edm_packed(x, "bbox"))
     assert torch.equal(a, gpu.edm_packed(x, "linear"))
+    assert torch.equal(a, gpu.edm_packed(x, "rb"))
 
 
 # ---------------------------------------------------------------- tensor cores
@@ -88,7 +89,7 @@ def test_edm_maps_agree_bitwise(gpu):
 BF_TOL = 1e-5
 
 
-@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("n,d", [(1, 64), (128, 64), (129, 64), (200, 128), (300, 256), (1000, 64),
                                  (700, 192)])
 def test_edm_bf16x3_small(gpu, oracle, mp, n, d):
@@ -148,4 +149,5 @@ def test_edm_bf16x3_maps_agree(gpu, n, d):
     a = gpu.edm_packed(x, "lambda", "bf16x3")
     assert torch.equal(a, gpu.edm_packed(x, "bbox", "bf16x3"))
     assert torch.equal(a, gpu.edm_packed(x, "linear", "bf16x3"))
+    assert torch.equal(a, gpu.edm_packed(x, "rb", "bf16x3"))
     gpu.simplex_device_errors()

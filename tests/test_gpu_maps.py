@@ -8,7 +8,7 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("nb", [1, 2, 3, 5, 8, 13, 64, 100, 1024, 4096])
 def test_map2_table_device(gpu, oracle, mp, nb):
     if mp != "lambda" and nb > 1024:
@@ -26,7 +26,7 @@ def test_map3_table_device(gpu, oracle, mp, nb):
     assert np.array_equal(t, oracle.table3(nb, mp))
 
 
-@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("n,rho", [(1, 16), (2, 1), (5, 2), (16, 4), (33, 8), (100, 16),
                                    (257, 16), (300, 32), (1000, 7)])
 def test_cover2_device(gpu, oracle, mp, n, rho):
@@ -43,6 +43,18 @@ def test_cover3_device(gpu, oracle, mp, n, rho):
     ref_count, ref_idle = oracle.cover3(n, rho, mp)
     assert np.array_equal(count.cpu().numpy(), ref_count)
     assert int(idle.item()) == ref_idle
+
+
+def test_cover2_full_size_rb(gpu, oracle):
+    """The rectangular box (2-simplex only) at n = 1024: every pair once."""
+    c2, i2 = gpu.map2(1024, 16, "rb")
+    assert c2.numel() == 524800 and bool((c2 == 1).all())
+    assert int(i2.item()) == oracle.cover2(1024, 16, "rb")[1]
+
+
+def test_rb_has_no_3_simplex_form(gpu):
+    with pytest.raises(gpu.SimplexError):
+        gpu.map3(40, 4, "rb")
 
 
 @pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])

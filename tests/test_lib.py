@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_abi_and_strerror(L):
-    assert sx.simplex_abi_version() == 2
+    assert sx.simplex_abi_version() == 3
     for st in range(7):
         assert L.simplex_strerror(st)
     assert L.simplex_last_cuda_error() == 0
@@ -54,7 +54,7 @@ def host_table(m, nb, mp):
     return t.numpy()
 
 
-@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 7, 8, 16, 31, 64, 100, 256, 1024, 4096])
 def test_decode2_host_equals_oracle(oracle, mp, nb):
     if mp != "lambda" and nb > 1024:
@@ -88,6 +88,12 @@ def test_grid_and_workspace_sizes(L):
     assert sx.simplex_grid_blocks(3, 32, "bbox") == 32 ** 3
     assert sx.simplex_grid_blocks(3, 32, "linear") == 32 * 33 * 34 // 6
     assert sx.simplex_grid_blocks(4, 32, "lambda") == -1
+    # the rectangular box: 2-simplex only, exactly the triangle's blocks
+    assert sx.simplex_grid_blocks(2, 32, "rb") == 32 * 33 // 2
+    assert sx.simplex_grid_blocks(2, 33, "rb") == 33 * 34 // 2
+    assert sx.simplex_grid_blocks(3, 32, "rb") == -1
+    assert sx.simplex_workspace_bytes("atm_energy", 1024, 3, "rb") == -1
+    assert sx.simplex_workspace_bytes("edm", 1024, 3, "rb") == 0
     rho = sx.simplex_block_rho("atm_energy")
     nb = -(-1024 // rho)
     # pair tables (16 KB per block pair of the 2-simplex of blocks), then one
@@ -125,6 +131,8 @@ def test_validation_before_gpu_work(L):
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, 12, 0, 0, null, 0, null) == 2    # loss not 8B
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, 16, 0, 0, null, 0, null) == 6    # no workspace
     assert L.simplex_map_blocks_host(2, 4, 0, null) == 1
+    assert L.simplex_map3(10, 4, 3, 16, 16, null) == 1                           # no 3-simplex RB
+    assert L.simplex_atm_energy(8, 3, 16, 1.0, 1e-4, 16, 3, 256, 1 << 20, null) == 1  # RB for m = 3
 
 
 def test_binding_requires_cuda_tensors(L):

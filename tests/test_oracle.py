@@ -128,13 +128,31 @@ def test_lambda2_recursive_equals_closed_form(oracle, k):
 
 
 @pytest.mark.parametrize("nb", [1, 2, 3, 5, 8, 13, 64, 100, 256])
-@pytest.mark.parametrize("m", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("m", ["lambda", "bbox", "linear", "rb"])
 def test_table2_is_bijection(oracle, nb, m):
     """Every block of the lower block triangle {X <= Y < nb} is listed once."""
     blocks = blocks_of(oracle.table2(nb, m), 2)
     want = [(x, y) for y in range(nb) for x in range(y + 1)]
     assert sorted(blocks) == sorted(want)
     assert len(blocks) == nb * (nb + 1) // 2
+
+
+@pytest.mark.parametrize("nb", range(1, 41))
+def test_rb_rows_fold(oracle, nb):
+    """Rectangular box: a grid of exactly nb(nb+1)/2 blocks for every nb (no
+    idle block, unlike lambda off powers of two), grid row k holding only
+    triangle rows floor(nb/2) + k and floor(nb/2) - 1 - k, the longer one
+    first and each row's blocks in column order."""
+    gx, gy = oracle.grid2(nb, "rb")
+    assert gx * gy == nb * (nb + 1) // 2
+    tab = oracle.table2(nb, "rb").reshape(gy, gx, 4)
+    h = nb // 2
+    for k in range(gy):
+        row = [tuple(e[:2]) for e in tab[k]]
+        lo = [(x, h + k) for x in range(h + k + 1)]
+        hi = [(x, h - 1 - k) for x in range(h - k)] if h - 1 - k >= 0 else []
+        assert row == lo + hi
+    assert (tab[:, :, 2] == -1).all()
 
 
 @pytest.mark.parametrize("k", range(1, 11))
@@ -256,7 +274,7 @@ def nb_pow2(nb):
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 16, 33, 64, 100])
 @pytest.mark.parametrize("rho", [1, 2, 4, 8])
-@pytest.mark.parametrize("m", ["lambda", "bbox", "linear"])
+@pytest.mark.parametrize("m", ["lambda", "bbox", "linear", "rb"])
 def test_cover2(oracle, n, rho, m):
     """Every element of Delta_n^2 (n(n+1)/2 of them) is hit exactly once."""
     counts, idle = oracle.cover2(n, rho, m)
@@ -267,7 +285,7 @@ def test_cover2(oracle, n, rho, m):
     if n % rho == 0:
         if m == "bbox":
             assert idle == nb * (nb - 1) // 2 * rho * rho + nb * rho * (rho - 1) // 2
-        if m == "linear":
+        if m in ("linear", "rb"):
             assert idle == nb * rho * (rho - 1) // 2
         if m == "lambda" and nb == nb_pow2(nb):
             assert idle == 0  # the diagonal pairing leaves no thread idle
