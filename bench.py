@@ -132,20 +132,25 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def time_steps(torch, fn, steps, warmup, flush=None):
+def time_steps(torch, fn, steps, warmup, flush=None, label="step"):
     """CUDA-event time of each step (ms) on the current stream, L2 flushed
-    (untimed) before every step when `flush` is given."""
+    (untimed) before every step when `flush` is given.  Each timed step is an
+    NVTX range named `label`, the warm-up one range, for profiler filters."""
+    torch.cuda.nvtx.range_push(f"{label}:warmup")
     for _ in range(warmup):
         fn()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(steps)]
     for a, b in ev:
         if flush is not None:
             flush()
+        torch.cuda.nvtx.range_push(label)
         a.record()
         fn()
         b.record()
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev]
 
@@ -565,7 +570,7 @@ def our_arm(args):
         step()
     torch.cuda.synchronize()
     sx.simplex_profile(True)
-    times = time_steps(torch, step, args.steps, 0, flush)
+    times = time_steps(torch, step, args.steps, 0, flush, label="energy_lambda")
     main_ms, main_k, launches = sx.simplex_profile_read()
     sx.simplex_profile(False)
     torch.cuda.synchronize()
@@ -578,7 +583,7 @@ def our_arm(args):
     # the same step on the other maps (same kernel body, same tile)
     maps = {"lambda": units / (ms_step / 1e3)}
     for mp in ("bbox", "linear"):
-        tt = time_steps(torch, lambda: step(mp), args.steps, 3, flush)
+        tt = time_steps(torch, lambda: step(mp), args.steps, 3, flush, label="energy_" + mp)
         maps[mp] = units / (sum(tt) / len(tt) / 1e3)
     maps["lambda_vs_bbox"] = maps["lambda"] / maps["bbox"]
     maps["lambda_vs_linear"] = maps["lambda"] / maps["linear"]
@@ -594,7 +599,7 @@ def our_arm(args):
         step()
         ep.copy_(e, non_blocking=True)
 
-    te = time_steps(torch, e2e_step, args.steps, 3, flush)
+    te = time_steps(torch, e2e_step, args.steps, 3, flush, label="energy_e2e")
     e2e_value, e2e_ms = job_rate(sum(te) / len(te), units, world, dist, "cuda")
     e2e = {"value": e2e_value, "unit": "triplets/s",
            "h2d_bytes_per_step": int(xp.numel() * xp.element_size()),
