@@ -569,9 +569,17 @@ def our_arm(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # the timed steps run without the library's event pairs (profile(1) then
+    # (0) clears the counters; the launch counter keeps counting), and a
+    # second pass of the same steps with the event pairs on times the main
+    # kernel for the roofline
     sx.simplex_profile(True)
+    sx.simplex_profile(False)
     times = time_steps(torch, step, args.steps, 0, flush, label="energy_lambda")
-    main_ms, main_k, launches = sx.simplex_profile_read()
+    _, _, launches = sx.simplex_profile_read()
+    sx.simplex_profile(True)
+    time_steps(torch, step, min(args.steps, 100), 0, flush, label="energy_lambda_kernel")
+    main_ms, main_k, _ = sx.simplex_profile_read()
     sx.simplex_profile(False)
     torch.cuda.synchronize()
     if world > 1:
