@@ -56,7 +56,7 @@ typedef enum {
     SIMPLEX_EINVAL = 1,       /* bad size, map, precision, or NULL pointer   */
     SIMPLEX_EALIGN = 2,       /* pointer not aligned as documented           */
     SIMPLEX_EOVERFLOW = 3,    /* size exceeds 64-bit indices or grid limits  */
-    SIMPLEX_EUNSUPPORTED = 4, /* valid request this build does not serve     */
+    SIMPLEX_EUNSUPPORTED = 4, /* valid request the library does not serve    */
     SIMPLEX_ECUDA = 5,        /* a CUDA call failed                          */
     SIMPLEX_EWORKSPACE = 6,   /* workspace missing, too small or misaligned  */
     SIMPLEX_ESCRATCH = 7,     /* problem too large for the library's static

@@ -107,8 +107,8 @@ int64_t oracle_table2(int64_t nb, int map, int32_t *tab)
     if (map == MAP_LAMBDA) {
         lam2_place(gy, 0, 0, gx, nb, tab);
         /* grid row 0 is not part of S (Sec. III-A: the diagonal is left out);
-         * this build gives block wx of that row the diagonal blocks 2wx and
-         * 2wx+1. */
+         * the reading used here gives block wx of that row the diagonal
+         * blocks 2wx and 2wx+1. */
         for (int64_t wx = 0; wx < gx; ++wx) {
             put2(tab + 4 * wx, 0, 2 * wx, 2 * wx, nb);
             put2(tab + 4 * wx, 1, 2 * wx + 1, 2 * wx + 1, nb);
@@ -408,7 +408,7 @@ double oracle_atm_energy_slice(int64_t n, const double *x, double nu, double eps
 }
 
 /* Sum of |e| over all triples (the scale against which rounding of a signed
- * sum is judged). */
+ * sum is measured). */
 double oracle_atm_abs_energy(int64_t n, const double *x, double nu, double eps)
 {
     double e = 0.0;

@@ -142,7 +142,7 @@ extern "C" const char *simplex_strerror(int status) {
         case SIMPLEX_EINVAL: return "invalid argument (size, map, precision or NULL pointer)";
         case SIMPLEX_EALIGN: return "pointer not aligned as required";
         case SIMPLEX_EOVERFLOW: return "size exceeds index or grid limits";
-        case SIMPLEX_EUNSUPPORTED: return "request not supported by this build";
+        case SIMPLEX_EUNSUPPORTED: return "request not supported by this library";
         case SIMPLEX_ECUDA: return "CUDA call failed (see simplex_last_cuda_error)";
         case SIMPLEX_EWORKSPACE: return "workspace missing, too small or misaligned";
         case SIMPLEX_ESCRATCH: return "problem too large for the library's static scratch";

@@ -122,7 +122,7 @@ def test_lambda2_recursive_equals_closed_form(oracle, k):
         q = wx // b
         assert np.array_equal(got[1:, :, 0], wx + q * b)
         assert np.array_equal(got[1:, :, 1], wy + 2 * q * b)
-    # grid row 0: the diagonal block pair of this build's reading
+    # grid row 0: the diagonal block pair (the reading used throughout)
     assert np.array_equal(got[0, :, 0], 2 * np.arange(gx))
     assert np.array_equal(got[0, :, 2], 2 * np.arange(gx) + 1)
 
