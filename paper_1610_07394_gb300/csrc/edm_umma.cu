@@ -81,10 +81,9 @@ __device__ __noinline__ float exact_sqdist(const float *__restrict__ x, int64_t 
     return acc;
 }
 
-constexpr int kStages = 2;                     // operand pipeline depth
+constexpr int kStages = 3;                     // operand stages of the d >= 128 kernel
 constexpr int kEpiWarps = 8;                   // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
-constexpr int kAccCols = 2 * TN;               // two accumulators in TMEM
 
 // Epilogue staging of one TMEM lane quarter (the two warps that read it):
 // 32 rows of the tile's 128 columns, row pitch 132 floats.  A row is written
@@ -104,10 +103,8 @@ struct PCtl {
 
 constexpr int kCtlBytes = 3072;
 constexpr int kStageBytes = 4 * 32 * kRowPitch * 4;   // four lane quarters
-constexpr int PSMEM_BYTES = 1024 + kStages * STAGE_BYTES + kStageBytes + kCtlBytes;
 static_assert(sizeof(PCtl) <= kCtlBytes, "control block");
 static_assert(offsetof(PCtl, ncol) % 16 == 0, "float4 reads of the column norms");
-static_assert(PSMEM_BYTES <= 227 * 1024, "shared memory per block");
 
 // Norms of a tile's rows and columns for one epilogue thread: columns
 // col0 + 64 half + lane and + 32 (a, b) and its row row0 + r (ni); 0 past n.
@@ -120,6 +117,24 @@ __device__ __forceinline__ void load_norms(const float *__restrict__ nrm, int64_
     ni = i < n ? __ldg(nrm + i) : 0.0f;
 }
 
+// The kernel for d >= 128 (bound by the operand loads and the MMAs): two-CTA
+// clusters walk the map's grid of 256 x 256 super-blocks in the same order;
+// per super-block (sX, sY) CTA r computes row block Y = 2 sY + r against both
+// column blocks 2 sX and 2 sX + 1 with M = 128, N = 256 MMAs, loading its own
+// row block's tiles and multicasting its column block's tiles into rows
+// 128 r .. 128 r + 127 of both CTAs' B operand, so that per K chunk a CTA
+// reads 64 KB from L2 for 128 x 256 pairs.  K chunks of 32 in the 64-byte
+// swizzle make a stage 48 KB, so three stages fit beside the row staging;
+// the epilogue takes the step's two 128-column halves in turn, like a tile
+// each (a half above the diagonal or past the last block is not written).
+constexpr int KC2 = 32;                        // K chunk: 32 BF16 = one 64-byte swizzle row
+constexpr int SUB = TM * KC2 * 2;              // 8 KB: 128 rows x 32 BF16
+constexpr int PSTAGE = 6 * SUB;                // A hi, A lo (8 KB each), B hi, B lo (16 KB each)
+constexpr int kPAccCols = 4 * TN;              // two 256-column accumulators
+constexpr int PSMEM2_BYTES = 1024 + kStages * PSTAGE + kStageBytes + kCtlBytes;
+static_assert(PSMEM2_BYTES <= 227 * 1024, "shared memory per block");
+constexpr uint32_t kIdesc256 = idesc_bf16(TM, 2 * TN, false, false);
+
 template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
                                                           const __grid_constant__ CUtensorMap map_lo,
@@ -127,22 +142,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                                                           const float *__restrict__ nrm,
                                                           float *__restrict__ out, int64_t n, int d,
                                                           int nb, int nb2, int gx, int64_t total) {
-    using Walk = PairWalk<MAP>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char *stages = base;   // kStages x 64 KB, 1024-aligned tiles
-    float *stg_all = reinterpret_cast<float *>(base + kStages * STAGE_BYTES);
-    PCtl &ctl = *reinterpret_cast<PCtl *>(base + kStages * STAGE_BYTES + kStageBytes);
+    float *stg_all = reinterpret_cast<float *>(base + kStages * PSTAGE);
+    PCtl &ctl = *reinterpret_cast<PCtl *>(base + kStages * PSTAGE + kStageBytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t s_stages = smem_u32(stages);
+    const uint32_t s_stage = smem_u32(base);
     volatile int *fail = &ctl.fail;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&ctl.full[s]), 1);
-            mbar_init(smem_u32(&ctl.empty[s]), 2);   // both CTAs release a shared stage
+            mbar_init(smem_u32(&ctl.empty[s]), 2);   // both CTAs release a stage
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl.tfull[a]), 1);
@@ -157,77 +170,74 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         prefetch_map(&map_hi);
         prefetch_map(&map_lo);
     }
-    if (warp == 1) {
-        tmem_alloc(smem_u32(&ctl.tmem), kAccCols);
-    }
+    if (warp == 1) tmem_alloc(smem_u32(&ctl.tmem), kPAccCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     cluster_sync();   // the peer's barriers exist before any multicast reaches them
     const uint32_t tmem = ctl.tmem;
-    const int nchunks = (d + KC - 1) / KC;
+    const int nchunks = (d + KC2 - 1) / KC2;
+    const uint32_t rank = cluster_rank();
 
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            Walk walk(gx, total, nb2, nb);
-            const uint32_t rank = cluster_rank();
-            int X, Y;
-            bool valid;
+            SuperWalk<MAP> walk(gx, total, nb2);
+            int sX, sY;
             uint32_t it = 0;
-            while (!*fail && walk.next(X, Y, valid)) {
+            bool ok = true;
+            while (ok && !*fail && walk.next(sX, sY)) {
+                const int Y = 2 * sY + (int)rank, Xr = 2 * sX + (int)rank;
                 for (int c = 0; c < nchunks; ++c, ++it) {
-                    const int s = (int)(it % kStages);
-                    const uint32_t ph = (it / kStages) & 1;
-                    if (!mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error)) break;
-                    const uint32_t bar = smem_u32(&ctl.full[s]);
-                    const uint32_t dst = s_stages + s * STAGE_BYTES;
-                    mbar_expect_tx(bar, STAGE_BYTES);
-                    // the row block's tiles once for the pair: hi from rank 0, lo from rank 1
-                    if (rank == 0) tma_load_2d_mc(dst + 0 * TILE_BYTES, &map_hi, c * KC, Y * TM, bar, 3);
-                    else tma_load_2d_mc(dst + 1 * TILE_BYTES, &map_lo, c * KC, Y * TM, bar, 3);
-                    tma_load_2d(dst + 2 * TILE_BYTES, &map_hi, c * KC, X * TN, bar);
-                    tma_load_2d(dst + 3 * TILE_BYTES, &map_lo, c * KC, X * TN, bar);
+                    const uint32_t s = it % kStages, ph = (it / kStages) & 1;
+                    // free once both CTAs' MMAs have read the stage
+                    if (!(ok = mbar_wait(smem_u32(&ctl.empty[s]), ph ^ 1, fail, &g_error))) break;
+                    const uint32_t bar = smem_u32(&ctl.full[s]), dst = s_stage + s * PSTAGE;
+                    mbar_expect_tx(bar, PSTAGE);
+                    tma_load_2d(dst, &map_hi, c * KC2, Y * TM, bar);
+                    tma_load_2d(dst + SUB, &map_lo, c * KC2, Y * TM, bar);
+                    // this CTA's column block, rows 128 r .. 128 r + 127 of both CTAs' B
+                    tma_load_2d_mc(dst + (2 + rank) * SUB, &map_hi, c * KC2, Xr * TN, bar, 3);
+                    tma_load_2d_mc(dst + (4 + rank) * SUB, &map_lo, c * KC2, Xr * TN, bar, 3);
                 }
             }
-            // a failed block waits (bounded) for its loads in flight
-            if (*fail && it > 0) {
-                const uint32_t last = it - 1;
-                mbar_drain(smem_u32(&ctl.full[last % kStages]), (last / kStages) & 1);
-            }
+            // a failed block waits (bounded) for the loads it may have in flight
+            if (*fail)
+                for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0; k < it; ++k)
+                    mbar_drain(smem_u32(&ctl.full[k % kStages]), (k / kStages) & 1);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            Walk walk(gx, total, nb2, nb);
-            int X, Y;
-            bool valid;
+            SuperWalk<MAP> walk(gx, total, nb2);
+            int sX, sY;
             uint32_t it = 0, tt = 0;
-            while (!*fail && walk.next(X, Y, valid)) {
+            bool ok = true;
+            while (ok && !*fail && walk.next(sX, sY)) {
                 const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
-                if (!mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error)) break;
+                if (!(ok = mbar_wait(smem_u32(&ctl.tempty[acc]), aph ^ 1, fail, &g_error))) break;
                 tc_fence_after();
-                const uint32_t dtm = tmem + acc * TN;
+                const uint32_t dtm = tmem + acc * (2 * TN);
                 for (int c = 0; c < nchunks; ++c, ++it) {
-                    const int s = (int)(it % kStages);
-                    if (!mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail, &g_error)) break;
+                    const uint32_t s = it % kStages;
+                    if (!(ok = mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail, &g_error))) break;
                     tc_fence_after();
-                    const uint32_t src = s_stages + s * STAGE_BYTES;
+                    const uint32_t src = s_stage + s * PSTAGE;
 #pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
+                    for (int ks = 0; ks < KC2 / 16; ++ks) {
                         const uint32_t koff = ks * 32;
-                        const uint64_t ah = sw128_desc(src + 0 * TILE_BYTES + koff);
-                        const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
-                        const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
-                        const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
-                        mma_bf16_afill(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast(dtm, ah, bl, kIdesc, 1u);
-                        mma_bf16(dtm, al, bh, kIdesc, 1u);
+                        const uint64_t ah = sw64_desc(src + koff);
+                        const uint64_t al = sw64_desc(src + SUB + koff);
+                        const uint64_t bh = sw64_desc(src + 2 * SUB + koff);
+                        const uint64_t bl = sw64_desc(src + 4 * SUB + koff);
+                        mma_bf16_afill(dtm, ah, bh, kIdesc256, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast(dtm, ah, bl, kIdesc256, 1u);
+                        mma_bf16(dtm, al, bh, kIdesc256, 1u);
                     }
                     // the stage is free once this CTA's MMAs and the peer's have read it
                     mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
                 }
-                mma_commit(smem_u32(&ctl.tfull[acc]));
+                if (ok) mma_commit(smem_u32(&ctl.tfull[acc]));
                 ++tt;
             }
         }
@@ -235,122 +245,133 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         // ---------------- epilogue: 8 warps, two per TMEM lane quarter
         const int ew = warp - 2;                 // 0..7
         const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
-        const int half = ew >> 2;                // columns [64*half, 64*half + 64)
-        const int r = 32 * quarter + lane;       // this thread's row in the tile
+        const int half = ew >> 2;                // columns [64*half, 64*half + 64) of a half-step
+        const int r = 32 * quarter + lane;       // this thread's row in the step
         float *stg = stg_all + quarter * 32 * kRowPitch;   // shared with the other half's warp
-        // this warp's 64 column norms (its own buffer: no cross-warp sync)
-        float *nc = &ctl.ncol[ew][0];
-        Walk walk(gx, total, nb2, nb);
-        int X, Y;
-        bool valid;
-        bool have = walk.next(X, Y, valid);
-        // norms of the current tile, loaded one tile ahead
-        float pa = 0.f, pb = 0.f, pni = 0.f;
-        if (have) load_norms(nrm, n, X, Y, half, r, lane, pa, pb, pni);
-        uint32_t tt = 0, st = 0;   // tiles, and tiles staged and written
-        while (have && !*fail) {
-            int Xn, Yn;
-            bool vn;
-            const bool hn = walk.next(Xn, Yn, vn);
-            float na = 0.f, nbv = 0.f, nni = 0.f;
-            if (hn) load_norms(nrm, n, Xn, Yn, half, r, lane, na, nbv, nni);
+        float *nc = &ctl.ncol[ew][0];            // this warp's 64 column norms
+        SuperWalk<MAP> walk(gx, total, nb2);
+        int sX, sY;
+        uint32_t tt = 0, st = 0;   // steps, and half-steps staged and written
+        bool ok = true;
+        // norms of a step, loaded a step ahead: this warp's two columns in each
+        // half-step (cn[2 u], cn[2 u + 1]) and this thread's row (rn)
+        auto load_step = [&](int sXs, int sYs, float (&cn)[4], float &rn) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                load_norms(nrm, n, 2 * sXs + u, 2 * sYs + (int)rank, half, r, lane, cn[2 * u], cn[2 * u + 1], rn);
+        };
+        bool have = walk.next(sX, sY);
+        float pcn[4] = {0.f, 0.f, 0.f, 0.f}, prn = 0.f;
+        if (have) load_step(sX, sY, pcn, prn);
+        while (have && ok && !*fail) {
+            int sXn, sYn;
+            const bool hn = walk.next(sXn, sYn);
+            float ncn[4] = {0.f, 0.f, 0.f, 0.f}, nrn = 0.f;
+            if (hn) load_step(sXn, sYn, ncn, nrn);
+            const int Y = 2 * sY + (int)rank;
             const uint32_t acc = tt & 1, aph = (tt >> 1) & 1;
-            const int64_t row0 = (int64_t)Y * TM, col0 = (int64_t)X * TN;
-            __syncwarp();   // the previous tile's reads of nc are done
-            nc[lane] = pa;
-            nc[lane + 32] = pb;
-            const int64_t i = row0 + r;
-            const float ni = pni;
-            const bool diag = (X == Y);
-            // packed index of this row's first column in the tile and in this
-            // warp's half; floats from the row start back to the previous
-            // 16-byte boundary of out
-            const int64_t grow = i * (i + 1) / 2 + col0, gbase = grow + 64 * half;
-            const int shift = (int)((reinterpret_cast<uintptr_t>(out + grow) >> 2) & 3);
-            float *myrow = stg + lane * kRowPitch + shift + 64 * half;
-            __syncwarp();
-            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail, &g_error)) break;
+            if (!(ok = mbar_wait(smem_u32(&ctl.tfull[acc]), aph, fail, &g_error))) break;
             tc_fence_after();
-            float v0[32], v1[32];
-            const uint32_t taddr = tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * half);
-            tmem_ld64(taddr, v0, v1);
-            // the accumulator is read: hand it back to the MMA warp
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
-            if (!valid) {   // a lockstep tile outside the simplex: nothing to write
-                X = Xn; Y = Yn; have = hn; valid = vn;
-                pa = na; pb = nbv; pni = nni;
-                ++tt;
-                continue;
-            }
-            // D = |x_i|^2 + |x_j|^2 - 2 g; flag entries with D < (|x_i|^2 + |x_j|^2)/64
-            float lows[4] = {1.0f, 1.0f, 1.0f, 1.0f};   // independent chains
-#pragma unroll
-            for (int q = 0; q < 32; q += 4) {
-                const float4 a = *reinterpret_cast<const float4 *>(nc + q);
-                const float4 b = *reinterpret_cast<const float4 *>(nc + 32 + q);
-                float sa[4] = {ni + a.x, ni + a.y, ni + a.z, ni + a.w};
-                float sb[4] = {ni + b.x, ni + b.y, ni + b.z, ni + b.w};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    v0[q + k] = fmaf(-2.0f, v0[q + k], sa[k]);
-                    v1[q + k] = fmaf(-2.0f, v1[q + k], sb[k]);
-                    lows[k] = fminf(lows[k], fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
-                                                   fmaf(-0.015625f, sb[k], v1[q + k])));
-                }
-            }
-            const float low = fminf(fminf(lows[0], lows[1]), fminf(lows[2], lows[3]));
-            if (__any_sync(0xffffffffu, low < 0.0f)) {
-#pragma unroll
-                for (int q = 0; q < 64; ++q) {
-                    float &vq = q < 32 ? v0[q] : v1[q - 32];
-                    const int64_t j = col0 + 64 * half + q;
-                    const float sj = ni + nc[q];
-                    if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
-                }
-            }
-            // the staging is free once both warps' copies of the previous tile have read it
-            if (st > 0) {
-                bulk_wait_read();
+#pragma unroll 1
+            for (int u = 0; u < 2 && ok; ++u) {
+                // half-step u: column block X = 2 sX + u, accumulator columns 128 u ..
+                const int X = 2 * sX + u;
+                const bool valid = X <= Y && Y < nb;
+                const int64_t row0 = (int64_t)Y * TM, col0 = (int64_t)X * TN;
+                const float pa = pcn[2 * u], pb = pcn[2 * u + 1], ni = prn;
+                __syncwarp();   // the previous half-step's reads of nc are done
+                nc[lane] = pa;
+                nc[lane + 32] = pb;
+                const int64_t i = row0 + r;
+                const bool diag = (X == Y);
+                // packed index of this row's first column in the half-step and in
+                // this warp's half; floats from the row start back to the previous
+                // 16-byte boundary of out
+                const int64_t grow = i * (i + 1) / 2 + col0, gbase = grow + 64 * half;
+                const int shift = (int)((reinterpret_cast<uintptr_t>(out + grow) >> 2) & 3);
+                float *myrow = stg + lane * kRowPitch + shift + 64 * half;
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ctl.sfree[quarter]));
-                if (!mbar_wait(smem_u32(&ctl.sfree[quarter]), (st - 1) & 1, fail, &g_error)) break;
-            }
-#pragma unroll
-            for (int q = 0; q < 32; ++q) { myrow[q] = v0[q]; myrow[32 + q] = v1[q]; }
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&ctl.sfull[quarter]));
-            if (!mbar_wait(smem_u32(&ctl.sfull[quarter]), st & 1, fail, &g_error)) break;
-            if (!diag) {
-                // One bulk copy per row segment of the tile (128 columns, both
-                // halves): lanes 0-15 of this warp take rows 16 half .. +15; the
-                // ragged head and tail (at most 3 floats each) by plain stores.
-                const int rr = 16 * half + lane;
-                const int64_t ir = row0 + 32 * quarter + rr;
-                if (lane < 16 && ir < n) {
-                    const int64_t gb = ir * (ir + 1) / 2 + col0;
-                    const int sh = (int)((reinterpret_cast<uintptr_t>(out + gb) >> 2) & 3);
-                    const float *sr = stg + rr * kRowPitch + sh;   // column c at sr[c]
-                    const int h = (4 - sh) & 3;
-                    const int body = (128 - h) & ~3;
-                    bulk_store(out + gb + h, smem_u32(sr + h), (uint32_t)body * 4);
-                    bulk_commit();
-                    for (int e = 0; e < h; ++e) out[gb + e] = sr[e];
-                    for (int e = h + body; e < 128; ++e) out[gb + e] = sr[e];
+                float v0[32], v1[32];
+                const uint32_t taddr = tmem + acc * (2 * TN) + ((uint32_t)(32 * quarter) << 16) +
+                                       (uint32_t)(TN * u + 64 * half);
+                tmem_ld64(taddr, v0, v1);
+                if (u == 1) {
+                    // the accumulator is read: hand it back to the MMA warp
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
                 }
-            } else if (i < n && 64 * half <= r) {
-                // diagonal tile: columns j <= i only, plain stores
-                const int rc = r - 64 * half;             // diagonal column, local
-                const int last = rc < 63 ? rc : 63;
-                if (rc <= 63) myrow[rc] = 0.0f;           // D_ii = 0 exactly
-                for (int e = 0; e <= last; ++e) out[gbase + e] = myrow[e];
+                if (!valid) continue;   // above the diagonal or past the last block
+                // D = |x_i|^2 + |x_j|^2 - 2 g; flag entries with D < (|x_i|^2 + |x_j|^2)/64
+                float lows[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+#pragma unroll
+                for (int q = 0; q < 32; q += 4) {
+                    const float4 a = *reinterpret_cast<const float4 *>(nc + q);
+                    const float4 b = *reinterpret_cast<const float4 *>(nc + 32 + q);
+                    const float sa[4] = {ni + a.x, ni + a.y, ni + a.z, ni + a.w};
+                    const float sb[4] = {ni + b.x, ni + b.y, ni + b.z, ni + b.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        v0[q + k] = fmaf(-2.0f, v0[q + k], sa[k]);
+                        v1[q + k] = fmaf(-2.0f, v1[q + k], sb[k]);
+                        lows[k] = fminf(lows[k], fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
+                                                       fmaf(-0.015625f, sb[k], v1[q + k])));
+                    }
+                }
+                const float low = fminf(fminf(lows[0], lows[1]), fminf(lows[2], lows[3]));
+                if (__any_sync(0xffffffffu, low < 0.0f)) {
+#pragma unroll
+                    for (int q = 0; q < 64; ++q) {
+                        float &vq = q < 32 ? v0[q] : v1[q - 32];
+                        const int64_t j = col0 + 64 * half + q;
+                        const float sj = ni + nc[q];
+                        if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
+                    }
+                }
+                // the staging is free once both warps' copies of the previous half-step have read it
+                if (st > 0) {
+                    bulk_wait_read();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&ctl.sfree[quarter]));
+                    if (!(ok = mbar_wait(smem_u32(&ctl.sfree[quarter]), (st - 1) & 1, fail, &g_error))) break;
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) { myrow[q] = v0[q]; myrow[32 + q] = v1[q]; }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.sfull[quarter]));
+                if (!(ok = mbar_wait(smem_u32(&ctl.sfull[quarter]), st & 1, fail, &g_error))) break;
+                if (!diag) {
+                    // One bulk copy per row segment of the half-step (128 columns,
+                    // both halves): lanes 0-15 of this warp take rows 16 half .. +15;
+                    // the ragged head and tail (at most 3 floats each) by plain stores.
+                    const int rr = 16 * half + lane;
+                    const int64_t ir = row0 + 32 * quarter + rr;
+                    if (lane < 16 && ir < n) {
+                        const int64_t gb = ir * (ir + 1) / 2 + col0;
+                        const int sh = (int)((reinterpret_cast<uintptr_t>(out + gb) >> 2) & 3);
+                        const float *sr = stg + rr * kRowPitch + sh;   // column c at sr[c]
+                        const int h = (4 - sh) & 3;
+                        const int body = (128 - h) & ~3;
+                        bulk_store(out + gb + h, smem_u32(sr + h), (uint32_t)body * 4);
+                        bulk_commit();
+                        for (int e = 0; e < h; ++e) out[gb + e] = sr[e];
+                        for (int e = h + body; e < 128; ++e) out[gb + e] = sr[e];
+                    }
+                } else if (i < n && 64 * half <= r) {
+                    // diagonal block: columns j <= i only, plain stores
+                    const int rc = r - 64 * half;             // diagonal column, local
+                    const int last = rc < 63 ? rc : 63;
+                    if (rc <= 63) myrow[rc] = 0.0f;           // D_ii = 0 exactly
+                    for (int e = 0; e <= last; ++e) out[gbase + e] = myrow[e];
+                }
+                ++st;
             }
-            X = Xn; Y = Yn; have = hn; valid = vn;
-            pa = na; pb = nbv; pni = nni;
             ++tt;
-            ++st;
+            sX = sXn; sY = sYn; have = hn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pcn[q] = ncn[q];
+            prn = nrn;
         }
     }
     bulk_wait_all();   // staging rows must stay valid until the copies have read them
@@ -358,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, kAccCols);
+        tmem_dealloc(tmem, kPAccCols);
     }
     // neither CTA of a pair leaves while the other may still multicast into
     // its shared memory or arrive on its barriers
@@ -707,10 +728,10 @@ static int smem_optin() {
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_RB>, a, PSMEM_BYTES)) != cudaSuccess ||
+        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM2_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM2_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM2_BYTES)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_edm_umma<MAP_RB>, a, PSMEM2_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LAMBDA>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_BBOX>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LINEAR>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
@@ -738,7 +759,7 @@ static int64_t max_pairs(int sms) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(sms & ~1));
         cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = PSMEM_BYTES;
+        cfg.dynamicSmemBytes = PSMEM2_BYTES;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = 2;
@@ -778,8 +799,13 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
     __nv_bfloat16 *xh = reinterpret_cast<__nv_bfloat16 *>(w);
     __nv_bfloat16 *xl = reinterpret_cast<__nv_bfloat16 *>(w + align_up(n * d * 2, 1024));
     float *nrm = reinterpret_cast<float *>(w + 2 * align_up(n * d * 2, 1024));
+    // 128-byte swizzle, K boxes of 64 for the d < 128 kernel; 64-byte swizzle,
+    // K boxes of 32 for the d >= 128 kernel
     CUtensorMap mh, ml;
-    if (!make_map_bf16(&mh, xh, n, d, d, TM) || !make_map_bf16(&ml, xl, n, d, d, TM)) return SIMPLEX_ECUDA;
+    const bool wide_rows = !use_multicast(d);
+    if (wide_rows ? (!make_map_bf16(&mh, xh, n, d, d, TM) || !make_map_bf16(&ml, xl, n, d, d, TM))
+                  : (!make_map_bf16_sw64(&mh, xh, n, d, d, TM) || !make_map_bf16_sw64(&ml, xl, n, d, d, TM)))
+        return SIMPLEX_ECUDA;
     int st = smem_optin();
     if (st) return st;
     k_split_bf16<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(x, n, (int)d, xh, xl, nrm);
@@ -816,7 +842,7 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(2 * clusters));
         cfg.blockDim = dim3(kThreads);
-        cfg.dynamicSmemBytes = PSMEM_BYTES;
+        cfg.dynamicSmemBytes = PSMEM2_BYTES;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;

@@ -584,37 +584,6 @@ static_assert(sizeof(Ctl2) <= kCtl2Bytes, "control block");
 static_assert(SMEM2 <= 227 * 1024, "shared memory per block");
 static_assert(2 * TN2 <= kTmemCols, "two accumulators of 256 columns");
 
-// The super-blocks of a cluster: the map's grid over nb2 = ceil(nb / 2)
-// blocks of 256, every cluster-th grid block, both CTAs of a cluster in the
-// same order (the multicast of a stage needs both on the same super-block).
-template <int MAP>
-struct SuperWalk {
-    int64_t w, total;
-    int wx, wy, gx, nb2, stride, pend, px, py;
-    __device__ SuperWalk(int gx_, int64_t total_, int nb2_)
-        : total(total_), gx(gx_), nb2(nb2_), pend(0), px(0), py(0) {
-        stride = (int)(gridDim.x >> 1);
-        w = blockIdx.x >> 1;
-        wy = (int)(w / gx_);
-        wx = (int)(w - (int64_t)wy * gx_);
-    }
-    __device__ bool next(int &sX, int &sY) {
-        if (pend) { pend = 0; sX = px; sY = py; return true; }
-        while (w < total) {
-            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
-                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
-            w += stride;
-            wx += stride;
-            while (wx >= gx) { wx -= gx; ++wy; }
-            if (L.cnt == 0) continue;
-            sX = L.x[0]; sY = L.y[0];
-            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
-            return true;
-        }
-        return false;
-    }
-};
-
 template <int MAP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_stress_umma_fwd(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,

@@ -183,6 +183,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo = 16
     return d;
 }
 
+// The same for an operand tile in the 64-byte swizzle layout (8 rows of 64
+// bytes per 512-byte atom, 16-byte chunks of row r XOR-permuted by
+// (r / 2) mod 4; tile base 512-byte aligned): K-major, stride offset 512
+// between 8-row groups, swizzle mode 4 = 64 B.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
 // D (TMEM) (+)= A * B over K = 16, one instruction issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate) {
@@ -321,58 +334,34 @@ __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     return __uint_as_float(r);
 }
 
-// The tiles of one CTA of a two-CTA cluster.  The map runs over the 2-simplex
-// of 256 x 256 super-blocks (nb2 = ceil(nb / 2)); the cluster takes the grid
-// blocks w = c, c + clusters, ... (c its index) and each super-block (sX, sY)
-// gives both CTAs two steps in lockstep: CTA rank r the column block
-// X = 2 sX + r, step s the row block Y = 2 sY + s.  Both CTAs need the same row
-// block at every step, so its operand tiles are loaded once for the pair (TMA
-// multicast).  A step whose tile lies above the diagonal or past the last
-// block (the second column block of a diagonal super-block at s = 0; row
-// blocks past nb when nb is odd) is still computed, to keep the lockstep,
-// and is marked invalid: nothing is written.
+// The super-blocks of a cluster: the map's grid over nb2 = ceil(nb / 2)
+// blocks of 256, every cluster-th grid block, both CTAs of a cluster in the
+// same order (the multicast of a stage needs both on the same super-block).
 template <int MAP>
-struct PairWalk {
+struct SuperWalk {
     int64_t w, total;
-    int wx, wy, gx, nb2, nb, step, sX, sY, pend, px, py;
-    uint32_t rank, stride;
-    __device__ PairWalk(int gx_, int64_t total_, int nb2_, int nb_, int /* chunk: unused */ = 0)
-        : total(total_), gx(gx_), nb2(nb2_), nb(nb_), step(2), sX(0), sY(0), pend(0), px(0),
-          py(0) {
-        rank = cluster_rank();
-        stride = gridDim.x >> 1;
+    int wx, wy, gx, nb2, stride, pend, px, py;
+    __device__ SuperWalk(int gx_, int64_t total_, int nb2_)
+        : total(total_), gx(gx_), nb2(nb2_), pend(0), px(0), py(0) {
+        stride = (int)(gridDim.x >> 1);
         w = blockIdx.x >> 1;
         wy = (int)(w / gx_);
         wx = (int)(w - (int64_t)wy * gx_);
     }
-    __device__ bool next(int &X, int &Y, bool &valid) {
-        if (step >= 2) {
-            if (pend) {
-                pend = 0;
-                sX = px; sY = py;
-            } else {
-                bool found = false;
-                while (w < total) {
-                    const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
-                                                      : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
-                    w += stride;
-                    wx += (int)stride;
-                    while (wx >= gx) { wx -= gx; ++wy; }
-                    if (L.cnt == 0) continue;
-                    sX = L.x[0]; sY = L.y[0];
-                    if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
-                    found = true;
-                    break;
-                }
-                if (!found) return false;
-            }
-            step = 0;
+    __device__ bool next(int &sX, int &sY) {
+        if (pend) { pend = 0; sX = px; sY = py; return true; }
+        while (w < total) {
+            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb2)
+                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb2);
+            w += stride;
+            wx += stride;
+            while (wx >= gx) { wx -= gx; ++wy; }
+            if (L.cnt == 0) continue;
+            sX = L.x[0]; sY = L.y[0];
+            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
+            return true;
         }
-        X = 2 * sX + (int)rank;
-        Y = 2 * sY + step;
-        ++step;
-        valid = X <= Y && Y < nb;
-        return true;
+        return false;
     }
 };
 
@@ -412,6 +401,20 @@ inline bool make_map_bf16(CUtensorMap *m, void *ptr, int64_t rows, int64_t cols,
     const cuuint32_t estr[2] = {1, 1};
     return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The same map with boxes of 32 BF16 (64 bytes) per row in the 64-byte swizzle.
+inline bool make_map_bf16_sw64(CUtensorMap *m, void *ptr, int64_t rows, int64_t cols, int64_t pitch,
+                               int box_rows) {
+    EncodeTiled f = encode_fn();
+    if (!f) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
