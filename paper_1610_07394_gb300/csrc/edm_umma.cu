@@ -13,20 +13,21 @@
 //
 // Persistent and warp-specialised, one CTA per SM, over the chosen map's grid
 // of 256 x 256 super-blocks (the map over ceil(nb / 2) blocks).  Warp 0
-// issues the TMA loads of the 128 x 64 BF16 operand tiles of each K chunk
-// (128-byte swizzle), warp 1 the tcgen05.mma instructions (M = N = 128,
-// K = 16, three products per K step) into 128-column TMEM accumulators, and
-// eight epilogue warps (two per TMEM lane quarter) read a finished
-// accumulator with tcgen05.ld, form D, stage rows through shared memory and
-// write each packed row segment with one bulk copy, while the MMA warp
-// already fills the next accumulator.  Two kernels:
-//  * k_edm_umma_wide (d < 128, bound by the stores): a CTA takes a
-//    super-block as two steps of two horizontally adjacent tiles, so that a
-//    row of a step is one segment of up to 256 outputs (a copy of up to
-//    1 KB);
-//  * k_edm_umma (d >= 128, bound by the operand loads): two-CTA clusters
-//    walk the super-blocks in lockstep, CTA r taking column block 2 sX + r,
-//    and the row block's tiles are loaded once for the pair by multicast.
+// issues the TMA loads of the BF16 operand tiles of each K chunk, warp 1 the
+// tcgen05.mma instructions (M = 128, K = 16, three products per K step) into
+// TMEM accumulators, and eight epilogue warps (two per TMEM lane quarter)
+// read a finished accumulator with tcgen05.ld, form D, stage rows through
+// shared memory and write each packed row segment with one bulk copy, while
+// the MMA warp already fills the next accumulator.  Two kernels:
+//  * k_edm_umma_wide (d < 128, bound by the stores): N = 128 tiles, K chunks
+//    of 64 (128-byte swizzle); a CTA takes a super-block as two steps of two
+//    horizontally adjacent tiles, so that a row of a step is one segment of
+//    up to 256 outputs (a copy of up to 1 KB);
+//  * k_edm_umma (d >= 128, bound by the operand loads and the MMAs): two-CTA
+//    clusters walk the super-blocks in the same order, CTA r computing row
+//    block 2 sY + r against both column blocks with N = 256 MMAs, its
+//    column block's tiles multicast into both CTAs; K chunks of 32
+//    (64-byte swizzle) keep three operand stages beside the row staging.
 // Every mbarrier wait is bounded in time; a wait that runs out sets a device
 // error flag (simplex_device_errors) and the block stops instead of hanging.
 #include <cstddef>
