@@ -50,7 +50,7 @@ NU, EPS = 1.0, 1e-4
 # separately).
 FLOPS_PER_TRIPLE = 20
 ROWS_NAMES = ("cover2_n16384", "cover3_n1024", "edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
-              "stress_n65536_d64", "edm_n16384_d64", "stress_n16384_d64")
+              "stress_n65536_d64", "edm_n16384_d64", "edm_n16384_d256", "stress_n16384_d64")
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one k_atm_energy_tab<lambda> launch on this
 # workload, from the ncu capture summarised in
@@ -342,6 +342,13 @@ def row_edm_n16384_d64(torch, sx, peaks):
     return _edm_big(torch, sx, peaks, x, "bf16x3")
 
 
+def row_edm_n16384_d256(torch, sx, peaks):
+    """EDM n=16384, d=256 on tensor cores (the d >= 128 kernel, 134M outputs):
+    a smaller case of the n=32768 configuration, sized for profiler captures."""
+    x = torch.from_numpy(synth.normal(16384, 256, seed=2)).cuda()
+    return _edm_big(torch, sx, peaks, x, "bf16x3")
+
+
 def row_atm_n4096(torch, sx, peaks):
     """ATM n=4096 (differentiation config): energy, energy+forces."""
     x = torch.from_numpy(synth.make_points("atm_n4096")).cuda()
@@ -505,7 +512,8 @@ ROWS = {
     "stress_n65536_d64": row_stress_n65536_d64,
 }
 # profiling-only cases (not part of the default rows)
-PROFILE_ROWS = {"edm_n16384_d64": row_edm_n16384_d64, "stress_n16384_d64": row_stress_n16384_d64}
+PROFILE_ROWS = {"edm_n16384_d64": row_edm_n16384_d64, "edm_n16384_d256": row_edm_n16384_d256,
+                "stress_n16384_d64": row_stress_n16384_d64}
 
 
 def rows_measure(torch, sx, peaks, names=None):
