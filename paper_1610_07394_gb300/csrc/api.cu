@@ -185,11 +185,7 @@ extern "C" int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map
         case SIMPLEX_OP_MAP3: return 0;
         case SIMPLEX_OP_EDM: return edm_workspace_bytes(n, d, map, prec);
         case SIMPLEX_OP_ATM_ENERGY: return atm_energy_workspace_bytes(n, map);
-        case SIMPLEX_OP_ATM_FORCES: {
-            const int64_t nb = (n + kAtmRho - 1) / kAtmRho;
-            const Grid g = grid3(nb, map);
-            return 8 * (g.gx * g.gy * g.gz + kReduceSlots);
-        }
+        case SIMPLEX_OP_ATM_FORCES: return atm_forces_workspace_bytes(n, map);
         case SIMPLEX_OP_STRESS_FWD: {
             if (stress_use_umma(d, prec)) return stress_umma_workspace_bytes(n, d, false);
             const int64_t nb = (n + kStressRho - 1) / kStressRho;

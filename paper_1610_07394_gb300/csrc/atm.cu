@@ -406,6 +406,7 @@ struct AtmForceSmem {
     float wjk[R_][R_ + 1];   // [k][j]: sum over i of de/db
     float wik[R_][R_ + 1];   // [k][i]: sum over j of de/dc
     float wij[R_][R_ + 1];   // [i][j]: sum over k of de/da
+    uint64_t bar;            // the tile's force tables landed (table-fed kernel)
 };
 
 // (u, r, r^3, r^2) of a pair: r = 1/sqrt(s), r^3 = 1/(s sqrt(s)), all zero
@@ -512,9 +513,65 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
     return v[0];
 }
 
+// ---------------------------------------------------------------- force tables
+
+// The force tables of every block pair (B1 <= B2) of the 2-simplex of
+// blocks, computed once per call instead of once per tile, in the layout of
+// AtmForceSmem's fc and fb so that a tile (I, J, K) copies the tables of
+// (I, K) and (J, K) into shared memory as they are:
+//   fc form [b][3][16]: pairs (a = t, b) and (a = t + 16, b) in the two
+//       lanes of (u.x, u.y), (u.z, r), (r^3, r^2);
+//   fb form [b][2][3][16]: pair (a = t + 16 h, b), each value in both lanes;
+// from pair_terms, zero unless a < b < n.  72 KB per block pair.
+constexpr int kFTabFc = R_ * 3 * 16;               // float4 of the fc form (24 KB)
+constexpr int kFTabFb = R_ * 2 * 3 * 16;           // float4 of the fb form (48 KB)
+constexpr int kFTabPair = kFTabFc + kFTabFb;       // float4 per block pair (72 KB)
+constexpr int64_t kFTabMaxBytes = int64_t(16) << 30;   // larger: per-tile tables instead
+
 template <int MAP>
+__global__ void __launch_bounds__(256) k_atm_forcetab(int64_t n, const float *__restrict__ x,
+                                                      float eps, int nb, float4 *__restrict__ tab) {
+    __shared__ float4 xs[2][R_];
+    const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int t = 0; t < L.cnt; ++t) {
+        const int B1 = t ? L.x[1] : L.x[0], B2 = t ? L.y[1] : L.y[0];
+        if (t) __syncthreads();
+        if (tid < 2 * R_) {
+            const int which = tid / R_, o = tid % R_;
+            const int64_t g = (int64_t)(which ? B2 : B1) * R_ + o;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < n) v = make_float4(__ldg(x + 3 * g), __ldg(x + 3 * g + 1), __ldg(x + 3 * g + 2), 0.f);
+            xs[which][o] = v;
+        }
+        __syncthreads();
+        float4 *fc = tab + pair_slot(B1, B2) * kFTabPair;
+        float4 *fb = fc + kFTabFc;
+        for (int e = tid; e < R_ * 16; e += 256) {
+            const int b = e >> 4, a = e & 15;
+            const int64_t gb = (int64_t)B2 * R_ + b, ga = (int64_t)B1 * R_ + a;
+            const PairTerms c0 = pair_terms(xs[0][a], xs[1][b], ga < gb && gb < n, eps);
+            const PairTerms c1 = pair_terms(xs[0][a + 16], xs[1][b], ga + 16 < gb && gb < n, eps);
+            fc[(3 * b + 0) * 16 + a] = make_float4(c0.ux, c1.ux, c0.uy, c1.uy);
+            fc[(3 * b + 1) * 16 + a] = make_float4(c0.uz, c1.uz, c0.r, c1.r);
+            fc[(3 * b + 2) * 16 + a] = make_float4(c0.r3, c1.r3, c0.r2, c1.r2);
+            fb[((2 * b + 0) * 3 + 0) * 16 + a] = make_float4(c0.ux, c0.ux, c0.uy, c0.uy);
+            fb[((2 * b + 0) * 3 + 1) * 16 + a] = make_float4(c0.uz, c0.uz, c0.r, c0.r);
+            fb[((2 * b + 0) * 3 + 2) * 16 + a] = make_float4(c0.r3, c0.r3, c0.r2, c0.r2);
+            fb[((2 * b + 1) * 3 + 0) * 16 + a] = make_float4(c1.ux, c1.ux, c1.uy, c1.uy);
+            fb[((2 * b + 1) * 3 + 1) * 16 + a] = make_float4(c1.uz, c1.uz, c1.r, c1.r);
+            fb[((2 * b + 1) * 3 + 2) * 16 + a] = make_float4(c1.r3, c1.r3, c1.r2, c1.r2);
+        }
+    }
+}
+
+// TAB: the tile's (i, k) and (j, k) tables arrive by two bulk copies from
+// the force tables of k_atm_forcetab (tab) instead of being built per tile.
+template <int MAP, bool TAB>
 __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *__restrict__ x,
                                                        float nu, float eps, int nb, int p,
+                                                       const float4 *__restrict__ tab,
                                                        double *__restrict__ partials,
                                                        double *__restrict__ forces) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -527,16 +584,32 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         return;
     }
     const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4, lane = tid & 31;
+    const uint32_t bar = umma::smem_u32(&S.bar);
+    if (TAB) {
+        if (tid == 0) {
+            umma::mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
+    bool bad = false;   // a wait of this thread ran out (the block's energy is then NaN)
     float hi = 0.f, lo = 0.f;
 #pragma unroll 1
     for (int t = 0; t < L.cnt; ++t) {
         int I, J, K;
         block_of(L, t, I, J, K);
         if (t) __syncthreads();
+        if (TAB && tid == 0 && !bad) {
+            umma::mbar_expect_tx(bar, (uint32_t)(kFTabPair * 16));
+            umma::bulk_load(umma::smem_u32(&S.fc[0][0][0]), tab + pair_slot(I, K) * kFTabPair,
+                            kFTabFc * 16, bar);
+            umma::bulk_load(umma::smem_u32(&S.fb[0][0][0][0]), tab + pair_slot(J, K) * kFTabPair + kFTabFc,
+                            kFTabFb * 16, bar);
+        }
         load_tiles(x, n, I, J, K, S.xs);
         for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
         __syncthreads();
-        build_force_tables(n, I, J, K, eps, S);
+        if (!TAB) build_force_tables(n, I, J, K, eps, S);
         PairPack pc[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -547,6 +620,19 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
                                             (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
             pc[q].ux = f2(a0.ux, a1.ux); pc[q].uy = f2(a0.uy, a1.uy); pc[q].uz = f2(a0.uz, a1.uz);
             pc[q].ra = f2(a0.r, a1.r); pc[q].ra2 = f2(a0.r2, a1.r2); pc[q].ra3 = f2(a0.r3, a1.r3);
+        }
+        // bounded wait for the tables; a timeout flags the error, drains
+        // (bounded) and lets the block finish with a NaN energy
+        if (TAB && !bad) {
+            const long long t0 = clock64();
+            while (!umma::mbar_try_wait(bar, (uint32_t)t & 1)) {
+                if (clock64() - t0 > umma::kWaitCycles) {
+                    atomicExch(&g_atm_error, 1);
+                    umma::mbar_drain(bar, (uint32_t)t & 1);
+                    bad = true;
+                    break;
+                }
+            }
         }
         __syncthreads();
         float2 acc = f2(0.f, 0.f);
@@ -633,10 +719,11 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         }
     }
     if (partials) {
+        const bool any_bad = __syncthreads_or(bad) != 0;
         const double s = block_sum_ff<256>(hi, lo, red);
         if (tid == 0) {
             const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
-            partials[bid] = (double)nu * s;
+            partials[bid] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)nu * s;
         }
     }
 }
@@ -657,9 +744,12 @@ static int smem_optin() {
     if (!done[dev]) {
         const int fb = (int)sizeof(AtmForceSmem);
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if ((e = cudaFuncSetAttribute(k_atm_forces<MAP_LAMBDA>, a, fb)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_atm_forces<MAP_BBOX>, a, fb)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR>, a, fb)) != cudaSuccess ||
+        if ((e = cudaFuncSetAttribute(k_atm_forces<MAP_LAMBDA, false>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_BBOX, false>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR, false>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LAMBDA, true>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_BBOX, true>, a, fb)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_atm_forces<MAP_LINEAR, true>, a, fb)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_atm_energy<MAP_LAMBDA>, a, kEnergySmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_atm_energy<MAP_BBOX>, a, kEnergySmem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(k_atm_energy<MAP_LINEAR>, a, kEnergySmem)) != cudaSuccess ||
@@ -690,6 +780,19 @@ static int atm_check(int64_t n, int64_t d, const float *x, int map, void *ws, in
 static int64_t energy_table_bytes(int64_t nb) {
     const int64_t t = atm_table_bytes(nb);
     return t <= kTabMaxBytes ? t : 0;
+}
+
+// Bytes of the force tables of simplex_atm_forces (0 where they would exceed
+// kFTabMaxBytes and the tables are built per tile instead).
+static int64_t force_table_bytes(int64_t nb) {
+    const int64_t t = nb * (nb + 1) / 2 * kFTabPair * 16;
+    return t <= kFTabMaxBytes ? t : 0;
+}
+
+int64_t atm_forces_workspace_bytes(int64_t n, int map) {
+    const int64_t nb = (n + R_ - 1) / R_;
+    const Grid g = grid3(nb, map);
+    return force_table_bytes(nb) + 8 * (g.gx * g.gy * g.gz + kReduceSlots);
 }
 
 int64_t atm_energy_workspace_bytes(int64_t n, int map) {
@@ -763,20 +866,39 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
                                   int64_t ws_bytes, void *stream) {
     if (!forces) return SIMPLEX_EINVAL;
     Grid g;
-    int64_t nb;
-    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb);
+    int64_t nb = (n + R_ - 1) / R_;
+    const int64_t ftab = n >= 1 ? force_table_bytes(nb) : 0;
+    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb, ftab);
     if (st) return st;
     if (!aligned(forces, 8) || (energy && !aligned(energy, 8))) return SIMPLEX_EALIGN;
     cudaStream_t s = (cudaStream_t)stream;
-    double *partials = energy ? (double *)workspace : nullptr;
+    // workspace: [force tables][one FP64 partial per grid block][reduction slots]
+    const float4 *tab = (const float4 *)workspace;
+    double *partials = energy ? (double *)((char *)workspace + ftab) : nullptr;
     const int64_t blocks = g.gx * g.gy * g.gz;
     if ((st = cuda_status(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s)))) return st;
     const int smem = (int)sizeof(AtmForceSmem);
     if ((st = smem_optin())) return st;
+    if (ftab) {
+        const Grid g2 = grid2(nb, map);
+        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
+        float4 *wt = (float4 *)workspace;
+        if (map == MAP_LAMBDA) k_atm_forcetab<MAP_LAMBDA><<<dim_of(g2), 256, 0, s>>>(n, x, eps, (int)nb, wt);
+        else if (map == MAP_BBOX) k_atm_forcetab<MAP_BBOX><<<dim_of(g2), 256, 0, s>>>(n, x, eps, (int)nb, wt);
+        else k_atm_forcetab<MAP_LINEAR><<<dim_of(g2), 256, 0, s>>>(n, x, eps, (int)nb, wt);
+        note_launches(1);
+        if ((st = launch_status())) return st;
+    }
     prof_begin(s);
-    if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
-    else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
-    else k_atm_forces<MAP_LINEAR><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, partials, forces);
+    if (ftab) {
+        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, true><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, tab, partials, forces);
+        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, true><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, tab, partials, forces);
+        else k_atm_forces<MAP_LINEAR, true><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, tab, partials, forces);
+    } else {
+        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, false><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, nullptr, partials, forces);
+        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, false><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, nullptr, partials, forces);
+        else k_atm_forces<MAP_LINEAR, false><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, nullptr, partials, forces);
+    }
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;

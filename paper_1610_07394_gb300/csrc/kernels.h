@@ -13,6 +13,7 @@ constexpr int kStressRho = 64;   // stress tile: 64 x 64 pairs, 256 threads
 
 int edm_rho(int64_t d, int prec);
 int64_t atm_energy_workspace_bytes(int64_t n, int map);
+int64_t atm_forces_workspace_bytes(int64_t n, int map);
 int atm_device_errors(cudaStream_t s);
 int64_t edm_workspace_bytes(int64_t n, int64_t d, int map, int prec);
 
