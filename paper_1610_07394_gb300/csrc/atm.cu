@@ -282,6 +282,83 @@ struct AtmEnergyTabSmem {
     uint64_t bar;
 };
 
+// Steps h in [h0, h1) of the packed triple loop of k_atm_energy_tab (two
+// consecutive k per step) for the thread's pairs (i, j) = (ti + 16p, tj + 16q):
+// (0,0) and (1,0) always, (0,1) and (1,1) when Q1.  Pairs in the order
+// (0,0) (0,1) (1,1) (1,0): three of the four loaded (i, k) / (j, k) values
+// are live at a time.  The bounds are uniform over a warp.
+template <bool Q1>
+__device__ __forceinline__ void energy_tab_steps(const AtmEnergyTabSmem &S, int ti, int tj, int h0,
+                                                 int h1, const float2 (&vij)[2][2][3],
+                                                 float2 (&s0)[2][2], float2 (&s1)[2][2]) {
+#pragma unroll 2
+    for (int h = h0; h < h1; ++h) {
+        const float4 C00 = S.ik[h][0][ti], C01 = S.ik[h][1][ti];
+        const float4 B00 = S.jk[h][0][tj], B01 = S.jk[h][1][tj];
+        triple_energy2s(vij[0][0], C00, C01, B00, B01, s0[0][0], s1[0][0]);
+        if (Q1) {
+            const float4 B10 = S.jk[h][0][tj + 16], B11 = S.jk[h][1][tj + 16];
+            triple_energy2s(vij[0][1], C00, C01, B10, B11, s0[0][1], s1[0][1]);
+            const float4 C10 = S.ik[h][0][ti + 16], C11 = S.ik[h][1][ti + 16];
+            triple_energy2s(vij[1][1], C10, C11, B10, B11, s0[1][1], s1[1][1]);
+            triple_energy2s(vij[1][0], C10, C11, B00, B01, s0[1][0], s1[1][0]);
+        } else {
+            const float4 C10 = S.ik[h][0][ti + 16], C11 = S.ik[h][1][ti + 16];
+            triple_energy2s(vij[1][0], C10, C11, B00, B01, s0[1][0], s1[1][0]);
+        }
+    }
+}
+
+// The same loop for a tile with I = J, whose pairs i < j are the thread's
+// two pairs a and b (any i, j of the tile each): steps [ha, h1) for pair a,
+// [hb, h1) for pair b (ha >= hb), each step loading that pair's own values.
+__device__ __forceinline__ void energy_tab_steps2(const AtmEnergyTabSmem &S, int hb, int ha, int h1,
+                                                  int ia, int ja, const float2 (&va)[3], float2 &s0a,
+                                                  float2 &s1a, int ib, int jb, const float2 (&vb)[3],
+                                                  float2 &s0b, float2 &s1b) {
+#pragma unroll 2
+    for (int h = hb; h < ha; ++h)
+        triple_energy2s(vb, S.ik[h][0][ib], S.ik[h][1][ib], S.jk[h][0][jb], S.jk[h][1][jb], s0b, s1b);
+#pragma unroll 2
+    for (int h = ha; h < h1; ++h) {
+        triple_energy2s(vb, S.ik[h][0][ib], S.ik[h][1][ib], S.jk[h][0][jb], S.jk[h][1][jb], s0b, s1b);
+        triple_energy2s(va, S.ik[h][0][ia], S.ik[h][1][ia], S.jk[h][0][ja], S.jk[h][1][ja], s0a, s1a);
+    }
+}
+
+// v_ij of the pair (i, j) of a tile in both lanes, from the (I, J) table
+// (entry a = i, lane j & 1 of the step holding b = j).
+__device__ __forceinline__ void pair_const(const float4 *__restrict__ tij, int i, int j, float2 (&v)[3]) {
+    const float4 *e = tij + (j >> 1) * 2 * R_ + i;
+    const float4 a = __ldg(e), b = __ldg(e + R_);
+    const bool odd = j & 1;
+    const float vx = odd ? a.y : a.x, vy = odd ? a.w : a.z, vz = odd ? b.y : b.x;
+    v[0] = make_float2(vx, vx);
+    v[1] = make_float2(vy, vy);
+    v[2] = make_float2(vz, vz);
+}
+
+// r_ij^3 of the pair (i, j) from the (I, J) table.
+__device__ __forceinline__ float pair_r3(const float4 *__restrict__ tij, int i, int j) {
+    const float4 b = __ldg(tij + (j >> 1) * 2 * R_ + R_ + i);
+    return (j & 1) ? b.w : b.z;
+}
+
+// Bounded wait for a tile's tables; a timeout flags the error and drains
+// (bounded), and the block then finishes with a NaN result.
+__device__ __forceinline__ void wait_tables(uint32_t bar, uint32_t parity, bool &bad) {
+    if (bad) return;
+    const long long t0 = clock64();
+    while (!umma::mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > umma::kWaitCycles) {
+            atomicExch(&g_atm_error, 1);
+            umma::mbar_drain(bar, parity);
+            bad = true;
+            return;
+        }
+    }
+}
+
 // The energy kernel fed by the pair tables: per tile, one thread starts two
 // bulk copies (2 x 16 KB) into shared memory, every thread reads its pair
 // constants (v_ij, r_ij^3) from the (I, J) table meanwhile, then a packed
@@ -323,64 +400,57 @@ __global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restr
             umma::bulk_load(umma::smem_u32(&S.jk[0][0][0]), tab + pair_slot(J, K) * kTabPair,
                             kTabPair * 16, bar);
         }
-        // pair constants of (i, j) = (ti + 16p, tj + 16q): v_ij in both lanes
-        // (r_ij^3 is read again after the loop, to spare registers), from the
-        // (I, J) table at a = i, b = j (lane j & 1)
-        const float4 *pij = tab + pair_slot(I, J) * kTabPair + (tj >> 1) * 2 * R_ + ti;
-        const bool odd = tj & 1;
-        float2 vij[2][2][3];
+        const float4 *tij = tab + pair_slot(I, J) * kTabPair;
+        // Tiles on a diagonal plane skip what lies outside i < j < k (the
+        // tables are zero there, so the sums are unchanged).  J = K: the pairs
+        // j in {2w, 2w + 1} of warp w meet a k > j only from step w on, the
+        // pairs j + 16 from step w + 8.  I = J: of the 32 x 32 pairs only
+        // i < j count, so each thread takes two of them, (ti, tj + 16) and
+        // (ti, tj) when ti < tj, else (tj + 16, ti + 16) (ti = tj: a zero
+        // pair), instead of four.
+        const int w = tj >> 1;
+        const bool jk_diag = J == K;
+        if (I != J) {
+            // pair constants of (i, j) = (ti + 16p, tj + 16q): v_ij in both
+            // lanes (r_ij^3 is read again after the loop, to spare registers)
+            float2 vij[2][2][3];
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp) {
-                const float4 *e = pij + (16 * q) * R_ + 16 * pp;
-                const float4 a = __ldg(e), b = __ldg(e + R_);
-                const float vx = odd ? a.y : a.x, vy = odd ? a.w : a.z;
-                const float vz = odd ? b.y : b.x;
-                vij[pp][q][0] = make_float2(vx, vx);
-                vij[pp][q][1] = make_float2(vy, vy);
-                vij[pp][q][2] = make_float2(vz, vz);
+                for (int pp = 0; pp < 2; ++pp) pair_const(tij, ti + 16 * pp, tj + 16 * q, vij[pp][q]);
+            wait_tables(bar, (uint32_t)t & 1, bad);
+            float2 s0[2][2], s1[2][2];
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) s0[pp][q] = s1[pp][q] = make_float2(0.f, 0.f);
+            if (!jk_diag) {
+                energy_tab_steps<true>(S, ti, tj, 0, R_ / 2, vij, s0, s1);
+            } else {
+                energy_tab_steps<false>(S, ti, tj, w, w + R_ / 4, vij, s0, s1);
+                energy_tab_steps<true>(S, ti, tj, w + R_ / 4, R_ / 2, vij, s0, s1);
             }
-        // bounded wait for the tables; a timeout flags the error, drains
-        // (bounded) and lets the block finish with a NaN result
-        if (!bad) {
-            const long long t0 = clock64();
-            while (!umma::mbar_try_wait(bar, (uint32_t)t & 1)) {
-                if (clock64() - t0 > umma::kWaitCycles) {
-                    atomicExch(&g_atm_error, 1);
-                    umma::mbar_drain(bar, (uint32_t)t & 1);
-                    bad = true;
-                    break;
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float ra3 = pair_r3(tij, ti + 16 * pp, tj + 16 * q);
+                    add_ff(hi, lo, fmaf(ra3, s0[pp][q].x + s0[pp][q].y, -3.0f * (s1[pp][q].x + s1[pp][q].y)),
+                           0.f);
                 }
-            }
+        } else {
+            const int ia = ti, ja = tj + 16;
+            const int ib = ti <= tj ? ti : tj + 16, jb = ti <= tj ? tj : ti + 16;
+            float2 va[3], vb[3];
+            pair_const(tij, ia, ja, va);
+            pair_const(tij, ib, jb, vb);
+            wait_tables(bar, (uint32_t)t & 1, bad);
+            float2 s0a = make_float2(0.f, 0.f), s1a = s0a, s0b = s0a, s1b = s0a;
+            if (!jk_diag) energy_tab_steps2(S, 0, 0, R_ / 2, ia, ja, va, s0a, s1a, ib, jb, vb, s0b, s1b);
+            else energy_tab_steps2(S, w, w + R_ / 4, R_ / 2, ia, ja, va, s0a, s1a, ib, jb, vb, s0b, s1b);
+            add_ff(hi, lo, fmaf(pair_r3(tij, ia, ja), s0a.x + s0a.y, -3.0f * (s1a.x + s1a.y)), 0.f);
+            add_ff(hi, lo, fmaf(pair_r3(tij, ib, jb), s0b.x + s0b.y, -3.0f * (s1b.x + s1b.y)), 0.f);
         }
-        float2 s0[2][2], s1[2][2];
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) s0[pp][q] = s1[pp][q] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int h = 0; h < R_ / 2; ++h) {
-            // pairs in the order (0,0) (0,1) (1,1) (1,0): three of the four
-            // loaded (i, k) / (j, k) values are live at a time
-            const float4 C00 = S.ik[h][0][ti], C01 = S.ik[h][1][ti];
-            const float4 B00 = S.jk[h][0][tj], B01 = S.jk[h][1][tj];
-            triple_energy2s(vij[0][0], C00, C01, B00, B01, s0[0][0], s1[0][0]);
-            const float4 B10 = S.jk[h][0][tj + 16], B11 = S.jk[h][1][tj + 16];
-            triple_energy2s(vij[0][1], C00, C01, B10, B11, s0[0][1], s1[0][1]);
-            const float4 C10 = S.ik[h][0][ti + 16], C11 = S.ik[h][1][ti + 16];
-            triple_energy2s(vij[1][1], C10, C11, B10, B11, s0[1][1], s1[1][1]);
-            triple_energy2s(vij[1][0], C10, C11, B00, B01, s0[1][0], s1[1][0]);
-        }
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float4 b = __ldg(pij + (16 * q + 1) * R_ + 16 * pp);
-                const float ra3 = odd ? b.w : b.z;
-                add_ff(hi, lo, fmaf(ra3, s0[pp][q].x + s0[pp][q].y, -3.0f * (s1[pp][q].x + s1[pp][q].y)),
-                       0.f);
-            }
     }
     const bool any_bad = __syncthreads_or(bad) != 0;
     const double s = block_sum_ff<256>(hi, lo, red);

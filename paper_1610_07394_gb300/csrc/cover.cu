@@ -40,24 +40,15 @@ __global__ void k_map_blocks(int map, Grid g, int nb, int64_t total, int32_t *ou
         table_entry<M>(map, g, nb, w, out + 2 * M * w);
 }
 
-// Adds this warp's idle threads to the block's count: one vote, one atomic
-// per warp (all of the warp's threads reach this point together; a block's
-// last warp may be partial).
-__device__ __forceinline__ void count_idle(bool took, unsigned int *s_idle) {
-    const unsigned active = __activemask();
-    const unsigned idle_lanes = __ballot_sync(active, !took);
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    if ((tid & 31) == __ffs(active) - 1 && idle_lanes) atomicAdd(s_idle, (unsigned)__popc(idle_lanes));
-}
+// The idle threads of a block are counted in the barrier that ends it
+// (__syncthreads_count: one bar.red.popc over the block's predicates; every
+// thread of the block reaches it) and added by one global atomic per block.
 
 // One thread per (r, c) of a rho x rho block; see simplex_map2 in simplex.h.
 template <int MAP>
 __global__ void k_cover2(int64_t n, int rho, int nb, int32_t *count,
                          unsigned long long *idle) {
-    __shared__ unsigned int s_idle;
     const int r = threadIdx.y, c = threadIdx.x;
-    if (r == 0 && c == 0) s_idle = 0;
-    __syncthreads();
     const List2 L = decode2<MAP>(blockIdx.x, blockIdx.y, nb);
     bool took = false;
     if (L.pair) {
@@ -73,34 +64,31 @@ __global__ void k_cover2(int64_t n, int rho, int nb, int32_t *count,
         const int64_t i = (int64_t)L.y[0] * rho + r, j = (int64_t)L.x[0] * rho + c;
         if (j <= i && i < n) { atomicAdd(count + (i * (i + 1) / 2 + j), 1); took = true; }
     }
-    count_idle(took, &s_idle);
-    __syncthreads();
-    if (r == 0 && c == 0 && s_idle) atomicAdd(idle, (unsigned long long)s_idle);
+    const int idle_threads = __syncthreads_count(!took);
+    if (r == 0 && c == 0 && idle_threads) atomicAdd(idle, (unsigned long long)idle_threads);
 }
 
 // One thread per (a, b, c) of a rho^3 block; see simplex_map3 in simplex.h.
 template <int MAP>
 __global__ void k_cover3(int64_t n, int rho, int nb, int p, int32_t *count,
                          unsigned long long *idle) {
-    __shared__ unsigned int s_idle;
     const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z;
-    const bool lead = (a | b | c) == 0;
-    if (lead) s_idle = 0;
-    __syncthreads();
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, blockIdx.z, p, nb);
     bool took = false;
     for (int t = 0; t < L.cnt; ++t) {
-        const int64_t i = (int64_t)L.i[t] * rho + a;
-        const int64_t j = (int64_t)L.j[t] * rho + b;
-        const int64_t k = (int64_t)L.k[t] * rho + c;
+        // n <= 3,000,000 (checked by simplex_map3): the coordinates fit in
+        // 32 bits; the tetrahedral number k(k+1)/2 * (k+2) / 3 stays below
+        // 2^64 in unsigned 64-bit arithmetic
+        const int i = L.i[t] * rho + a, j = L.j[t] * rho + b, k = L.k[t] * rho + c;
         if (i <= j && j <= k && k < n) {
-            atomicAdd(count + (k * (k + 1) * (k + 2) / 6 + j * (j + 1) / 2 + i), 1);
+            const uint64_t kk = (uint32_t)k, jj = (uint32_t)j;
+            const uint64_t tet_k = kk * (kk + 1) / 2 * (kk + 2) / 3;
+            atomicAdd(count + (tet_k + jj * (jj + 1) / 2 + (uint32_t)i), 1);
             took = true;
         }
     }
-    count_idle(took, &s_idle);
-    __syncthreads();
-    if (lead && s_idle) atomicAdd(idle, (unsigned long long)s_idle);
+    const int idle_threads = __syncthreads_count(!took);
+    if ((a | b | c) == 0 && idle_threads) atomicAdd(idle, (unsigned long long)idle_threads);
 }
 
 // Every map has an m = 2 form; the rectangular box has no m = 3 form.
