@@ -91,7 +91,16 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;  // producer, MMA, epilogue warps
 // at an offset of (its global address mod 16 bytes) / 4 floats, so that the
 // 16-byte-aligned body of the global row segment starts at a 16-byte-aligned
 // shared address and one cp.async.bulk of up to 512 bytes copies it.
+// Rows sit at stg_row(r): 8 floats of padding after every 8 rows.  The
+// offset of row r = i - i0 (i0 a multiple of 32) is T(i) mod 4 = T(r) mod 4
+// plus a constant, with period 8 in r (0 1 3 2 2 3 1 0), and the pitch is
+// 4 words mod 32, so without the padding rows r, r + 8, r + 16, r + 24 hit
+// the same bank when a warp's 32 lanes each write their own row; with it
+// the 32 lanes hit 32 banks for any column, and row starts stay 16-byte
+// aligned.
 constexpr int kRowPitch = 132;
+constexpr int kQuarterFloats = 32 * kRowPitch + 24;   // 32 staging rows + padding
+__device__ __forceinline__ int stg_row(int r, int pitch) { return r * pitch + 8 * (r >> 3); }
 
 struct PCtl {
     uint64_t full[kStages], empty[kStages];   // operand stages: TMA -> MMA -> TMA
@@ -103,7 +112,7 @@ struct PCtl {
 };
 
 constexpr int kCtlBytes = 3072;
-constexpr int kStageBytes = 4 * 32 * kRowPitch * 4;   // four lane quarters
+constexpr int kStageBytes = 4 * kQuarterFloats * 4;   // four lane quarters
 static_assert(sizeof(PCtl) <= kCtlBytes, "control block");
 static_assert(offsetof(PCtl, ncol) % 16 == 0, "float4 reads of the column norms");
 
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
         const int half = ew >> 2;                // columns [64*half, 64*half + 64) of a half-step
         const int r = 32 * quarter + lane;       // this thread's row in the step
-        float *stg = stg_all + quarter * 32 * kRowPitch;   // shared with the other half's warp
+        float *stg = stg_all + quarter * kQuarterFloats;   // shared with the other half's warp
         float *nc = &ctl.ncol[ew][0];            // this warp's 64 column norms
         SuperWalk<MAP> walk(gx, total, nb2);
         int sX, sY;
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 // 16-byte boundary of out
                 const int64_t grow = i * (i + 1) / 2 + col0, gbase = grow + 64 * half;
                 const int shift = (int)((reinterpret_cast<uintptr_t>(out + grow) >> 2) & 3);
-                float *myrow = stg + lane * kRowPitch + shift + 64 * half;
+                float *myrow = stg + stg_row(lane, kRowPitch) + shift + 64 * half;
                 __syncwarp();
                 float v0[32], v1[32];
                 const uint32_t taddr = tmem + acc * (2 * TN) + ((uint32_t)(32 * quarter) << 16) +
@@ -351,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                     if (lane < 16 && ir < n) {
                         const int64_t gb = ir * (ir + 1) / 2 + col0;
                         const int sh = (int)((reinterpret_cast<uintptr_t>(out + gb) >> 2) & 3);
-                        const float *sr = stg + rr * kRowPitch + sh;   // column c at sr[c]
+                        const float *sr = stg + stg_row(rr, kRowPitch) + sh;   // column c at sr[c]
                         const int h = (4 - sh) & 3;
                         const int body = (128 - h) & ~3;
                         bulk_store(out + gb + h, smem_u32(sr + h), (uint32_t)body * 4);
@@ -403,7 +412,8 @@ namespace wide {
 
 constexpr int kWStages = 1;
 constexpr int kWPitch = 260;                          // 256 columns + the shift to 16 bytes
-constexpr int kWStageBytes = 4 * 32 * kWPitch * 4;    // four lane quarters
+constexpr int kWQuarterFloats = 32 * kWPitch + 24;    // rows at stg_row(r, kWPitch)
+constexpr int kWStageBytes = 4 * kWQuarterFloats * 4; // four lane quarters
 constexpr int kWAccCols = 4 * TN;                     // four accumulators
 
 struct WCtl {
@@ -580,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
         const int quarter = warp & 3;
         const int h = ew >> 2;
         const int r = 32 * quarter + lane;       // this thread's row in the step
-        float *stg = stg_all + quarter * 32 * kWPitch;   // shared with the other tile's warp
+        float *stg = stg_all + quarter * kWQuarterFloats;   // shared with the other tile's warp
         float *nc = &ctl.ncol[ew][0];
         StepWalk<MAP> walk(gx, total, nb2, nb);
         int X0, Y;
@@ -612,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
             // floats from the row start back to the previous 16-byte boundary of out
             const int64_t grow = i * (i + 1) / 2 + col0;
             const int shift = (int)((reinterpret_cast<uintptr_t>(out + grow) >> 2) & 3);
-            float *myrow = stg + lane * kWPitch + shift;
+            float *myrow = stg + stg_row(lane, kWPitch) + shift;
             __syncwarp();
             if (!mbar_wait(smem_u32(&ctl.tfull[acc]), use & 1, fail, &g_error)) break;
             tc_fence_after();
@@ -690,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
                 const int len = lim <= 0 ? 0 : (lim >= 2 * TN ? 2 * TN : (int)lim);
                 const int64_t gb = ir * (ir + 1) / 2 + col0;
                 const int sh = (int)((reinterpret_cast<uintptr_t>(out + gb) >> 2) & 3);
-                const float *sr = stg + rr * kWPitch + sh;   // column c at sr[c]
+                const float *sr = stg + stg_row(rr, kWPitch) + sh;   // column c at sr[c]
                 const int hd = ((4 - sh) & 3) < len ? ((4 - sh) & 3) : len;
                 const int body = (len - hd) & ~3;
                 if (body > 0) {
