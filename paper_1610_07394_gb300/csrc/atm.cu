@@ -681,15 +681,28 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         __syncthreads();
         if (!TAB) build_force_tables(n, I, J, K, eps, S);
         PairPack pc[2];
+        if (TAB) {
+            // the pairs (i = ti, ti + 16; j = tj + 16 q) from the fc form of the
+            // (I, J) force table: both i-slots in the two lanes, as used here
+            const float4 *tij = tab + pair_slot(I, J) * kFTabPair + ti;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int64_t gj = (int64_t)J * R_ + tj + 16 * q;
-            const PairTerms a0 = pair_terms(S.xs[0][ti], S.xs[1][tj + 16 * q],
-                                            (int64_t)I * R_ + ti < gj && gj < n, eps);
-            const PairTerms a1 = pair_terms(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
-                                            (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
-            pc[q].ux = f2(a0.ux, a1.ux); pc[q].uy = f2(a0.uy, a1.uy); pc[q].uz = f2(a0.uz, a1.uz);
-            pc[q].ra = f2(a0.r, a1.r); pc[q].ra2 = f2(a0.r2, a1.r2); pc[q].ra3 = f2(a0.r3, a1.r3);
+            for (int q = 0; q < 2; ++q) {
+                const float4 *e = tij + 3 * (tj + 16 * q) * 16;
+                const float4 C0 = __ldg(e), C1 = __ldg(e + 16), C2 = __ldg(e + 32);
+                pc[q].ux = f2(C0.x, C0.y); pc[q].uy = f2(C0.z, C0.w); pc[q].uz = f2(C1.x, C1.y);
+                pc[q].ra = f2(C1.z, C1.w); pc[q].ra3 = f2(C2.x, C2.y); pc[q].ra2 = f2(C2.z, C2.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int64_t gj = (int64_t)J * R_ + tj + 16 * q;
+                const PairTerms a0 = pair_terms(S.xs[0][ti], S.xs[1][tj + 16 * q],
+                                                (int64_t)I * R_ + ti < gj && gj < n, eps);
+                const PairTerms a1 = pair_terms(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
+                                                (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
+                pc[q].ux = f2(a0.ux, a1.ux); pc[q].uy = f2(a0.uy, a1.uy); pc[q].uz = f2(a0.uz, a1.uz);
+                pc[q].ra = f2(a0.r, a1.r); pc[q].ra2 = f2(a0.r2, a1.r2); pc[q].ra3 = f2(a0.r3, a1.r3);
+            }
         }
         // bounded wait for the tables; a timeout flags the error, drains
         // (bounded) and lets the block finish with a NaN energy
