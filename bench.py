@@ -49,7 +49,7 @@ NU, EPS = 1.0, 1e-4
 # vectors the same energy takes 22 (R^3 and the bracket 1 + 3 cos cos cos
 # separately).
 FLOPS_PER_TRIPLE = 20
-ROWS_NAMES = ("cover2_n16384", "cover3_n1024", "edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
+ROWS_NAMES = ("cover2_n16384", "cover3_n1024", "cover4_n256", "edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
               "stress_n65536_d64", "edm_n16384_d64", "edm_n16384_d256", "stress_n16384_d64")
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one k_atm_energy_tab<lambda> launch on this
@@ -474,17 +474,18 @@ def _cover_row(torch, sx, m, n, rho):
     (an atomic increment) or itself as idle.  The per-element work is one
     atomic, so here the threads a map launches outside the simplex weigh as
     much as the work itself (the parallel space of Sec. III)."""
-    vol = n * (n + 1) // 2 if m == 2 else n * (n + 1) * (n + 2) // 6
+    vol = math.comb(n + m - 1, m)
     count = torch.empty(vol, dtype=torch.int32, device="cuda")
     idle = torch.empty(1, dtype=torch.int64, device="cuda")
-    fn = sx.simplex_map2 if m == 2 else sx.simplex_map3
+    fn = {2: sx.simplex_map2, 3: sx.simplex_map3, 4: sx.simplex_map4}[m]
     r = {"unit": "elements/s", "elements": vol, "rho": rho}
-    maps = ("lambda", "bbox", "linear", "rb") if m == 2 else ("lambda", "bbox", "linear")
+    maps = {2: ("lambda", "bbox", "linear", "rb"), 3: ("lambda", "bbox", "linear"), 4: ("lambda", "bbox")}[m]
     for mp in maps:
         ms = _median_ms(torch, lambda: fn(n, rho, mp, count, idle), 5)
         r[mp] = vol / (ms / 1e3)
         r[mp + "_ms"] = ms
         r[mp + "_idle_threads"] = int(idle.item())
+        r[mp + "_threads_per_element"] = (int(idle.item()) + vol) / vol
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
     if m == 2:
         r["lambda_vs_rb"] = r["lambda"] / r["rb"]
@@ -501,9 +502,17 @@ def row_cover3_n1024(torch, sx, peaks):
     return _cover_row(torch, sx, 3, 1024, 8)
 
 
+def row_cover4_n256(torch, sx, peaks):
+    """Coverage of the 4-simplex, n=256, 4^4 threads per block: the lambda
+    map of the r = 1/2, beta = 2 set (plus the m = 3 map for the plane
+    K = L) against the bounding box's 64^4 blocks."""
+    return _cover_row(torch, sx, 4, 256, 4)
+
+
 ROWS = {
     "cover2_n16384": row_cover2_n16384,
     "cover3_n1024": row_cover3_n1024,
+    "cover4_n256": row_cover4_n256,
     "edm_n1024_d3": row_edm_n1024_d3,
     "edm_n32768_d256": row_edm_n32768_d256,
     "edm_n65536_d64": row_edm_n65536_d64,

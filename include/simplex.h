@@ -84,7 +84,8 @@ typedef enum {
 } simplex_op;
 
 /* ABI version of this header (bumped on any signature change or added entry
- * point or map; 2 added simplex_stress_fwd_bwd, 3 SIMPLEX_MAP_RB). */
+ * point or map; 2 added simplex_stress_fwd_bwd, 3 SIMPLEX_MAP_RB, 4
+ * simplex_map4 and the m = 4 tables). */
 int simplex_abi_version(void);
 
 /* Human-readable text of a status code (static storage). */
@@ -100,19 +101,23 @@ int simplex_block_rho(int op, int64_t d, int prec);
 
 /*
  * Number of grid blocks a map launches over nb data blocks per side for an
- * m-simplex (m = 2 or 3), or -1 on bad arguments.  Grid shapes: LAMBDA m=2
- * (p/2) x p, m=3 (p/2) x (p/2) x (p/2 + p/4 + 2) with p the power of two
+ * m-simplex (m = 2, 3 or 4), or -1 on bad arguments.  Grid shapes: LAMBDA
+ * m=2 (p/2) x p, m=3 (p/2) x (p/2) x (p/2 + p/4 + 2) with p the power of two
  * >= max(nb, 2) (the last two z-layers are the plane J = K, mapped by the
- * 2-simplex map); BBOX nb^m; LINEAR nb(nb+1)/2 or nb(nb+1)(nb+2)/6; RB
- * (m=2) (nb + 1 - nb mod 2) x ceil(nb/2) = nb(nb+1)/2.
+ * 2-simplex map), m=4 (p/2)^3 x (p/2 + p/8) (p >= 8; + 1 layer at p = 4,
+ * none at p = 2) for the blocks I <= J <= K < L only (the plane K = L takes
+ * the m = 3 grid, see simplex_map4); BBOX nb^m; LINEAR nb(nb+1)/2 or
+ * nb(nb+1)(nb+2)/6; RB (m=2) (nb + 1 - nb mod 2) x ceil(nb/2) = nb(nb+1)/2.
+ * m = 4 takes LAMBDA and BBOX only, nb <= 4096.
  */
 int64_t simplex_grid_blocks(int m, int64_t nb, int map);
 
 /*
- * Decode table of a map (Sec. III-A eq. (map2d) / Sec. III-C): for every
- * grid block w (x fastest, then y, then z) the data blocks it is sent to,
- * (X0, Y0, X1, Y1) for m=2 (X = column block <= Y = row block) or
- * (I0, J0, K0, I1, J1, K1) for m=3, with -1 in unused slots.  The second
+ * Decode table of a map (Sec. III-A eq. (map2d) / Sec. III-C / Sec. III-D):
+ * for every grid block w (x fastest, then y, then z, then w for m = 4) the
+ * data blocks it is sent to, (X0, Y0, X1, Y1) for m=2 (X = column block <=
+ * Y = row block), (I0, J0, K0, I1, J1, K1) for m=3 or (I0, J0, K0, L0, -1,
+ * -1, -1, -1) for m=4, with -1 in unused slots.  The second
  * slot is used only by grid row 0 of the 2-simplex map, which takes the
  * diagonal blocks 2w and 2w+1 (the paper leaves the diagonal out; this is
  * the library's reading).
@@ -147,6 +152,32 @@ int simplex_map2(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
  * count: device, n(n+1)(n+2)/6 int32 (zeroed by the call); idle: device, 1 int64.
  */
 int simplex_map3(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
+                 void *stream);
+
+/*
+ * Coverage of Delta_n^4 = {i <= j <= k <= l < n} (Sec. III-D: the recursive
+ * set with r = 1/2 and beta = 2, V(S_n^4) = (n^4 - n)/14; the paper gives
+ * the set and its volume but no map, so the map is this library's reading:
+ * the blocks I <= J <= K < L of one level, split at half size h, are the
+ * copies L L L L and H H H H (recursion) and the cross terms, which one h^4
+ * orthotope covers with idle points: local (a, b, c, d) goes to
+ *   (a, b, h+d, h+c)   if a <= b, d < c;
+ *   (a, b, c, h+d)     if a <= b, b <= c <= d;
+ *   (a, h+c, h+d, h+b) if a <= b, c <= d, a <= c, d < b;
+ *   (c, d, a, h+b)     if b < a, c <= d <= a;
+ *   (a, h+b, h+d, h+c) if b < a, b <= d < c;
+ * and nowhere otherwise).  rho^4 threads per block, blockDim (rho, rho,
+ * rho^2); thread (a, b, c + rho d) takes element (I rho + a, J rho + b,
+ * K rho + c, L rho + d) when i <= j <= k <= l < n.  LAMBDA launches two
+ * grids: the m = 4 grid of simplex_grid_blocks(4, ...) and, for the plane
+ * K = L, the m = 3 lambda grid with block (I, J, K) taken as (I, J, K, K).
+ * BBOX launches nb^4 blocks.  Packed index of (i, j, k, l):
+ * l(l+1)(l+2)(l+3)/24 + k(k+1)(k+2)/6 + j(j+1)/2 + i.
+ * n in [1, 65536]; rho in [1, 5] (0 = 4); map LAMBDA or BBOX (else EINVAL).
+ * count: device, n(n+1)(n+2)(n+3)/24 int32 (zeroed by the call); idle:
+ * device, 1 int64.
+ */
+int simplex_map4(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
                  void *stream);
 
 /*

@@ -13,8 +13,13 @@ Parity status of each function (what pins it, see ``tests/test_oracle.py``):
   and III-C), ``bbox``/``linear`` tables: pinned by brute-force bijection
   checks, the closed-form volumes of Eq. 2 and eq. (m2)/(m3), the extra-volume
   limits of Sec. III-C, and the paper's closed-form lambda of eq. (map2d).
-* ``cover2`` / ``cover3``: pinned by V(Delta_n^2) = n(n+1)/2 and
-  V(Delta_n^3) = n(n+1)(n+2)/6 and by brute-force idle counts.
+* ``table4`` (S_n^4 with r = 1/2, beta = 2, Sec. III-D, built from its cross
+  terms): pinned by a brute-force check that every block I <= J <= K < L
+  appears once and no grid point twice, V(S_n^4) = (n^4 - n)/14 and the
+  extra-volume limit 5/7 of Sec. III-D.
+* ``cover2`` / ``cover3`` / ``cover4``: pinned by V(Delta_n^2) = n(n+1)/2,
+  V(Delta_n^3) = n(n+1)(n+2)/6, V(Delta_n^4) = C(n+3, 4) and by brute-force
+  idle counts.
 * ``edm_packed`` / ``edm_pairs``: pinned by closed forms on a line and a
   lattice, scaling, translation and permutation invariance.
 * ``atm_energy`` / ``atm_atom_energy`` / ``atm_grad`` / ``atm_grad_atoms``:
@@ -67,6 +72,10 @@ def lib():
             "oracle_table3": (_i64, [_i64, ctypes.c_int, _i32p]),
             "oracle_cover2": (_i64, [_i64, _i64, ctypes.c_int, _i32p]),
             "oracle_cover3": (_i64, [_i64, _i64, ctypes.c_int, _i32p]),
+            "oracle_grid4": (_i64, [_i64, ctypes.c_int, _i64p, _i64p, _i64p, _i64p]),
+            "oracle_table4": (_i64, [_i64, ctypes.c_int, _i32p]),
+            "oracle_volume4": (_i64, [_i64]),
+            "oracle_cover4": (_i64, [_i64, _i64, ctypes.c_int, _i32p]),
             "oracle_edm_packed": (None, [_i64, _i64, _dp, _dp]),
             "oracle_edm_pairs": (None, [_i64, _dp, _i64p, _i64, _dp]),
             "oracle_atm_energy": (_d, [_i64, _dp, _d, _d]),
@@ -126,6 +135,36 @@ def table3(nb: int, m) -> np.ndarray:
     t = np.empty((gx * gy * gz, 6), dtype=np.int32)
     lib().oracle_table3(nb, _map(m), _p(t, ctypes.c_int32))
     return t
+
+
+def grid4(nb: int, m) -> tuple[int, int, int, int]:
+    g = [ctypes.c_int64() for _ in range(4)]
+    lib().oracle_grid4(nb, _map(m), *[ctypes.byref(v) for v in g])
+    return tuple(v.value for v in g)
+
+
+def table4(nb: int, m) -> np.ndarray:
+    """(grid, 8) int32: per grid block (I, J, K, L, -1, -1, -1, -1), -1 where
+    unused; lambda holds the blocks I <= J <= K < L.  Raises if two cross
+    terms land on one grid point."""
+    gx, gy, gz, gw = grid4(nb, m)
+    t = np.empty((gx * gy * gz * gw, 8), dtype=np.int32)
+    if lib().oracle_table4(nb, _map(m), _p(t, ctypes.c_int32)) < 0:
+        raise RuntimeError("m = 4 placement collision")
+    return t
+
+
+def volume4(s: int) -> int:
+    """Grid points of the recursive set S_s^4 (mapped or idle)."""
+    return int(lib().oracle_volume4(s))
+
+
+def cover4(n: int, rho: int, m) -> tuple[np.ndarray, int]:
+    c = np.zeros(n * (n + 1) * (n + 2) * (n + 3) // 24, dtype=np.int32)
+    idle = lib().oracle_cover4(n, rho, _map(m), _p(c, ctypes.c_int32))
+    if idle < 0:
+        raise RuntimeError("m = 4 placement collision")
+    return c, int(idle)
 
 
 def cover2(n: int, rho: int, m) -> tuple[np.ndarray, int]:

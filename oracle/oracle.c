@@ -11,12 +11,14 @@
  * What is here, each written from its definition:
  *   - block-space map tables built by *recursive construction* of the sets
  *     S_n^2 (Sec. III-A, Eq. 5-9) and the two-branch S_n^3 (Sec. III-C,
- *     "Alternative Map for 3-Simplices"), the bounding box (Sec. I, f(x)=x),
+ *     "Alternative Map for 3-Simplices"), the r = 1/2, beta = 2 set S_n^4
+ *     (Sec. III-D, built from its cross terms), the bounding box (Sec. I, f(x)=x),
  *     the linear enumeration g (Sec. I, Eq. 2 expanded) and, for m = 2, the
  *     rectangular box (Sec. II: the RB strategy for packed triangular
  *     matrices, applied to the parallel space) laid out row by row;
  *   - thread-level coverage counts over the discrete orthogonal simplices
- *     Delta_n^2 and Delta_n^3 (Eq. 1-2, volumes of Sec. III-A / III-B);
+ *     Delta_n^2, Delta_n^3 and Delta_n^4 (Eq. 1-2, volumes of Sec. III-A /
+ *     III-B / III-D);
  *   - the packed Euclidean distance matrix (Sec. I: EDM as a 2-simplex
  *     problem), the Axilrod-Teller-Muto triple-dipole energy and its
  *     gradient (Sec. I: triple-interaction n-body as a 3-simplex problem),
@@ -29,7 +31,8 @@
  *   - 3-simplex: triples i <= j <= k < n, packed
  *     idx = k(k+1)(k+2)/6 + j(j+1)/2 + i.  Blocks (I, J, K).
  *   - Map tables: for every grid block w, a list of up to two data blocks;
- *     m=2 entries are (X0,Y0,X1,Y1), m=3 entries (I0,J0,K0,I1,J1,K1); unused
+ *     m=2 entries are (X0,Y0,X1,Y1), m=3 entries (I0,J0,K0,I1,J1,K1), m=4
+ *     entries (I,J,K,L,-1,-1,-1,-1); unused
  *     slots are -1; a data block with any coordinate >= nb is dropped.
  * All floating point is double; the build disables FP contraction so the
  * results are the same on every host.
@@ -240,6 +243,112 @@ int64_t oracle_table3(int64_t nb, int map, int32_t *tab)
     return g;
 }
 
+/* ======================= 4-simplex tables ======================= */
+
+/*
+ * Recursive set S_s^4 with r = 1/2, beta = 2 (Sec. III-D): V(S_s) =
+ * (s/2)^4 + 2 V(S_{s/2}) = (s^4 - s)/14.  It holds the blocks
+ * {off <= I <= J <= K < L < off+s} (the hyperplane K = L is a 3-simplex of
+ * blocks, covered by the m = 3 set).  Split the index range into halves L
+ * and H of h = s/2 blocks: L L L L and H H H H are the two recursive copies;
+ * the cross terms (I < off+h <= L) go into one h^4 orthotope, which has room
+ * to spare (the paper gives the volume, not the assignment; this is the
+ * library's reading, written here in the other direction: from each cross
+ * term to its orthotope point).  With local indices x1 <= x2 <= x3 < x4
+ * and x' = x - h for an index in H:
+ *   L L L H, x4' >= x3: point (x1, x2, x3, x4');
+ *   L L L H, x4' <  x3: point (x3, x4', x1, x2);
+ *   L L H H:            point (x1, x2, x4', x3');
+ *   L H H H, x1 <= x2': point (x1, x4', x2', x3');
+ *   L H H H, x1 >  x2': point (x1, x2', x4', x3').
+ * Placement in the 4-D grid (x, y, z, w) of shape (p/2)^3 x (p/2 + slab):
+ * the top orthotope (s = p) fills w < p/2 with (x, y, z, w) = the point;
+ * the orthotope (a, b, c, d) of a sub-problem of size s < p at offset off
+ * goes to x = off/2 + a, y = s/2 + b, and m = c s/2 + d to z = m mod p/2,
+ * w = p/2 + floor(m / (p/2)) (the shared b, q of the 2-simplex map).
+ * Returns 0, or -1 when two cross terms land on one grid point.
+ */
+static int64_t slab4(int64_t p) { return p >= 8 ? p / 8 : (p == 4 ? 1 : 0); }
+
+int64_t oracle_grid4(int64_t nb, int map, int64_t *gx, int64_t *gy, int64_t *gz, int64_t *gw)
+{
+    if (map == MAP_LAMBDA) {
+        int64_t p = pow2_at_least(nb);
+        *gx = p / 2; *gy = p / 2; *gz = p / 2; *gw = p / 2 + slab4(p);
+    } else {
+        *gx = nb; *gy = nb; *gz = nb; *gw = nb;
+    }
+    return (*gx) * (*gy) * (*gz) * (*gw);
+}
+
+static int lam4_place(int64_t s, int64_t off, int64_t p, int64_t nb, int32_t *tab)
+{
+    if (s < 2) return 0;
+    int64_t h = s / 2, g = p / 2;
+    for (int64_t x4 = h; x4 < s; ++x4)
+        for (int64_t x3 = 0; x3 < x4; ++x3)
+            for (int64_t x2 = 0; x2 <= x3; ++x2)
+                for (int64_t x1 = 0; x1 <= x2 && x1 < h; ++x1) {
+                    int64_t a, b, c, d;
+                    if (x3 < h) {                       /* L L L H */
+                        if (x4 - h >= x3) { a = x1; b = x2; c = x3; d = x4 - h; }
+                        else { a = x3; b = x4 - h; c = x1; d = x2; }
+                    } else if (x2 < h) {                /* L L H H */
+                        a = x1; b = x2; c = x4 - h; d = x3 - h;
+                    } else if (x1 <= x2 - h) {          /* L H H H */
+                        a = x1; b = x4 - h; c = x2 - h; d = x3 - h;
+                    } else {
+                        a = x1; b = x2 - h; c = x4 - h; d = x3 - h;
+                    }
+                    int64_t wx, wy, wz, ww;
+                    if (s == p) { wx = a; wy = b; wz = c; ww = d; }
+                    else {
+                        int64_t m = c * h + d;
+                        wx = off / 2 + a; wy = h + b; wz = m % g; ww = g + m / g;
+                    }
+                    int32_t *e = tab + 8 * (((ww * g + wz) * g + wy) * g + wx);
+                    if (off + x4 >= nb) continue;    /* past the last block: dropped */
+                    if (e[0] >= 0) return -1;
+                    e[0] = (int32_t)(off + x1); e[1] = (int32_t)(off + x2);
+                    e[2] = (int32_t)(off + x3); e[3] = (int32_t)(off + x4);
+                }
+    if (lam4_place(h, off, p, nb, tab)) return -1;
+    return lam4_place(h, off + h, p, nb, tab);
+}
+
+/* Map table of a 4-simplex map over nb blocks; tab has grid*8 int32
+ * (I, J, K, L, then four unused -1).  LAMBDA: the blocks I <= J <= K < L
+ * (the plane K = L takes the 3-simplex map); BBOX: every I <= J <= K <= L.
+ * Returns the grid size, or -1 if the lambda placement collides. */
+int64_t oracle_table4(int64_t nb, int map, int32_t *tab)
+{
+    int64_t gx, gy, gz, gw;
+    int64_t g = oracle_grid4(nb, map, &gx, &gy, &gz, &gw);
+    for (int64_t t = 0; t < 8 * g; ++t) tab[t] = -1;
+    if (map == MAP_LAMBDA) {
+        int64_t p = pow2_at_least(nb);
+        if (lam4_place(p, 0, p, nb, tab)) return -1;
+    } else {
+        for (int64_t l = 0; l < nb; ++l)
+            for (int64_t k = 0; k <= l; ++k)
+                for (int64_t j = 0; j <= k; ++j)
+                    for (int64_t i = 0; i <= j; ++i) {
+                        int32_t *e = tab + 8 * (((l * gz + k) * gy + j) * gx + i);
+                        e[0] = (int32_t)i; e[1] = (int32_t)j; e[2] = (int32_t)k; e[3] = (int32_t)l;
+                    }
+    }
+    return g;
+}
+
+/* Volume of the recursive set S_s^4: the orthotope points of every level
+ * (mapped or idle), summed over the recursion. */
+int64_t oracle_volume4(int64_t s)
+{
+    if (s < 2) return 0;
+    int64_t h = s / 2;
+    return h * h * h * h + 2 * oracle_volume4(h);
+}
+
 /* ======================= coverage ======================= */
 
 /*
@@ -321,6 +430,67 @@ int64_t oracle_cover3(int64_t n, int64_t rho, int map, int32_t *count)
                 }
     }
     free(tab);
+    return idle;
+}
+
+/*
+ * Thread-level coverage of Delta_n^4 = {(i, j, k, l): i <= j <= k <= l < n},
+ * packed idx = l(l+1)(l+2)(l+3)/24 + k(k+1)(k+2)/6 + j(j+1)/2 + i.  Each
+ * grid block has rho^4 threads (a, b, c, d) and takes element (I rho + a,
+ * J rho + b, K rho + c, L rho + d), kept when i <= j <= k <= l < n.  LAMBDA
+ * walks the 4-simplex table (K < L) and then the 3-simplex lambda table
+ * with each block (I, J, K) read as (I, J, K, K); BBOX the nb^4 table.
+ * count[] zeroed by the caller; returns the idle threads (-1 on a
+ * placement collision).
+ */
+int64_t oracle_cover4(int64_t n, int64_t rho, int map, int32_t *count)
+{
+    int64_t nb = (n + rho - 1) / rho, gx, gy, gz, gw;
+    int64_t g = oracle_grid4(nb, map, &gx, &gy, &gz, &gw);
+    int32_t *tab = (int32_t *)malloc(sizeof(int32_t) * 8 * g);
+    if (oracle_table4(nb, map, tab) < 0) { free(tab); return -1; }
+    int64_t g3 = 0, hx, hy, hz;
+    int32_t *tab3 = NULL;
+    if (map == MAP_LAMBDA) {
+        g3 = oracle_grid3(nb, MAP_LAMBDA, &hx, &hy, &hz);
+        tab3 = (int32_t *)malloc(sizeof(int32_t) * 6 * g3);
+        oracle_table3(nb, MAP_LAMBDA, tab3);
+    }
+    int64_t idle = 0;
+    for (int64_t w = 0; w < g + g3; ++w) {
+        int64_t blk[2][4];
+        int nblk = 0;
+        if (w < g) {
+            int32_t *e = tab + 8 * w;
+            if (e[0] >= 0) { for (int t = 0; t < 4; ++t) blk[0][t] = e[t]; nblk = 1; }
+        } else {
+            int32_t *e = tab3 + 6 * (w - g);
+            for (int s = 0; s < 2; ++s)
+                if (e[3 * s] >= 0) {
+                    blk[nblk][0] = e[3 * s]; blk[nblk][1] = e[3 * s + 1];
+                    blk[nblk][2] = e[3 * s + 2]; blk[nblk][3] = e[3 * s + 2];
+                    ++nblk;
+                }
+        }
+        for (int64_t d = 0; d < rho; ++d)
+            for (int64_t c = 0; c < rho; ++c)
+                for (int64_t b = 0; b < rho; ++b)
+                    for (int64_t a = 0; a < rho; ++a) {
+                        int took = 0;
+                        for (int s = 0; s < nblk; ++s) {
+                            int64_t i = blk[s][0] * rho + a, j = blk[s][1] * rho + b;
+                            int64_t k = blk[s][2] * rho + c, l = blk[s][3] * rho + d;
+                            if (i <= j && j <= k && k <= l && l < n) {
+                                count[l * (l + 1) * (l + 2) * (l + 3) / 24 + k * (k + 1) * (k + 2) / 6
+                                      + j * (j + 1) / 2 + i]++;
+                                took = 1;
+                            }
+                        }
+                        if (!took) ++idle;
+                    }
+    }
+    free(tab);
+    free(tab3);
     return idle;
 }
 

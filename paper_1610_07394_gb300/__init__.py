@@ -34,7 +34,7 @@ OPS = {"map2": 0, "map3": 1, "edm": 2, "atm_energy": 3, "atm_forces": 4,
 EXPORTS = [
     "simplex_abi_version", "simplex_strerror", "simplex_last_cuda_error", "simplex_block_rho",
     "simplex_grid_blocks", "simplex_map_blocks", "simplex_map_blocks_host", "simplex_map2",
-    "simplex_map3", "simplex_edm_packed", "simplex_atm_energy", "simplex_atm_forces",
+    "simplex_map3", "simplex_map4", "simplex_edm_packed", "simplex_atm_energy", "simplex_atm_forces",
     "simplex_stress_fwd", "simplex_stress_bwd", "simplex_workspace_bytes", "simplex_profile",
     "simplex_profile_read", "simplex_atm_energy_noalloc", "simplex_device_errors",
     "simplex_stress_fwd_bwd",
@@ -64,6 +64,7 @@ def _signatures(L):
         "simplex_map_blocks_host": (_i32, [_i32, _i64, _i32, _vp]),
         "simplex_map2": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp]),
         "simplex_map3": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp]),
+        "simplex_map4": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp]),
         "simplex_edm_packed": (_i32, [_i64, _i64, _vp, _vp, _i32, _i32, _vp, _i64, _vp]),
         "simplex_atm_energy": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _i32, _vp, _i64, _vp]),
         "simplex_atm_forces": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _vp, _i32, _vp, _i64, _vp]),
@@ -171,6 +172,12 @@ def simplex_map3(n: int, rho: int, map, count: torch.Tensor, idle: torch.Tensor,
         _stream(stream)))
 
 
+def simplex_map4(n: int, rho: int, map, count: torch.Tensor, idle: torch.Tensor, stream=None):
+    _check("simplex_map4", lib().simplex_map4(
+        n, rho, _map(map), _cuda(count, torch.int32, "count"), _cuda(idle, torch.int64, "idle"),
+        _stream(stream)))
+
+
 def simplex_edm_packed(x, out, map="lambda", prec="fp32", workspace=None, stream=None):
     n, d = x.shape
     ws = _ptr_or_null(workspace, torch.uint8, "workspace")
@@ -272,6 +279,14 @@ def map3(n: int, rho: int = 0, map="lambda"):
     count = torch.empty(n * (n + 1) * (n + 2) // 6, dtype=torch.int32, device="cuda")
     idle = torch.empty(1, dtype=torch.int64, device="cuda")
     simplex_map3(n, rho, map, count, idle)
+    return count, idle
+
+
+def map4(n: int, rho: int = 0, map="lambda"):
+    """Coverage of Delta_n^4: (count[n(n+1)(n+2)(n+3)/24] int32, idle threads)."""
+    count = torch.empty(n * (n + 1) * (n + 2) * (n + 3) // 24, dtype=torch.int32, device="cuda")
+    idle = torch.empty(1, dtype=torch.int64, device="cuda")
+    simplex_map4(n, rho, map, count, idle)
     return count, idle
 
 

@@ -1,11 +1,11 @@
 // cover.cu -- decode tables and coverage counts of the block-space maps.
 //
 // simplex_map_blocks / simplex_map_blocks_host evaluate the maps of maps.cuh
-// for every grid block (Sec. III-A eq. (map2d), Sec. III-C); simplex_map2 and
-// simplex_map3 launch each map's grid and count, per element of the simplex,
-// how many threads reach it (it must be exactly one: the map is a bijection
-// onto Delta_n^m, volumes of Sec. III-A/III-B) and how many threads reach
-// none.
+// for every grid block (Sec. III-A eq. (map2d), Sec. III-C, Sec. III-D);
+// simplex_map2, simplex_map3 and simplex_map4 launch each map's grid and
+// count, per element of the simplex, how many threads reach it (it must be
+// exactly one: the map covers Delta_n^m once, volumes of Sec. III-A/III-B)
+// and how many threads reach none.
 #include "common.cuh"
 
 namespace sx {
@@ -31,6 +31,23 @@ SX_HD void table_entry(int map, const Grid &g, int nb, int64_t w, int32_t *e) {
             e[3 * t] = L.i[t]; e[3 * t + 1] = L.j[t]; e[3 * t + 2] = L.k[t];
         }
     }
+}
+
+// One m = 4 table entry (8 int32: (I, J, K, L) and an unused slot of -1).
+SX_HD void table_entry4(int map, const Grid4 &g, int nb, int64_t w, int32_t *e) {
+    const uint32_t x = (uint32_t)(w % g.gx);
+    const uint32_t y = (uint32_t)((w / g.gx) % g.gy);
+    const uint32_t z = (uint32_t)((w / (g.gx * g.gy)) % g.gz);
+    const uint32_t ww = (uint32_t)(w / (g.gx * g.gy * g.gz));
+    for (int t = 0; t < 8; ++t) e[t] = -1;
+    const Blk4 B = map == MAP_LAMBDA ? decode4_lambda(x, y, z, ww, g.p, nb) : decode4_bbox(x, y, z, ww, nb);
+    if (B.ok) { e[0] = B.i; e[1] = B.j; e[2] = B.k; e[3] = B.l; }
+}
+
+__global__ void k_map_blocks4(int map, Grid4 g, int nb, int64_t total, int32_t *out) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
+         w += (int64_t)gridDim.x * blockDim.x)
+        table_entry4(map, g, nb, w, out + 8 * w);
 }
 
 template <int M>
@@ -91,8 +108,58 @@ __global__ void k_cover3(int64_t n, int rho, int nb, int p, int32_t *count,
     if ((a | b | c) == 0 && idle_threads) atomicAdd(idle, (unsigned long long)idle_threads);
 }
 
+// Packed index of (i <= j <= k <= l): C(l+3, 4) + C(k+2, 3) + C(j+1, 2) + i,
+// the first term as T(l) T(l+2) / 6 (T the triangular numbers) so that no
+// product exceeds 2^63 for l < 2^16.
+__device__ __forceinline__ int64_t index4(int i, int j, int k, int l) {
+    const int64_t tl = (int64_t)l * (l + 1) / 2, tl2 = (int64_t)(l + 2) * (l + 3) / 2;
+    return tl * tl2 / 6 + (int64_t)k * (k + 1) * (k + 2) / 6 + (int64_t)j * (j + 1) / 2 + i;
+}
+
+// One thread per (a, b, c, d) of a rho^4 block (blockDim (rho, rho, rho^2),
+// threadIdx.z = c + rho d) on the 4-D grid of grid4 (blockIdx.x = x + gx z,
+// blockIdx.y = y, blockIdx.z = w); see simplex_map4 in simplex.h.
+template <int MAP>
+__global__ void k_cover4(int64_t n, int rho, int nb, int p, uint32_t gx, int32_t *count,
+                         unsigned long long *idle) {
+    const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z % rho, d = threadIdx.z / rho;
+    const uint32_t x = blockIdx.x % gx, z = blockIdx.x / gx;
+    const Blk4 B = MAP == MAP_LAMBDA ? decode4_lambda(x, blockIdx.y, z, blockIdx.z, p, nb)
+                                     : decode4_bbox(x, blockIdx.y, z, blockIdx.z, nb);
+    bool took = false;
+    if (B.ok) {
+        const int i = B.i * rho + a, j = B.j * rho + b, k = B.k * rho + c, l = B.l * rho + d;
+        if (i <= j && j <= k && k <= l && l < n) {
+            atomicAdd(count + index4(i, j, k, l), 1);
+            took = true;
+        }
+    }
+    const int idle_threads = __syncthreads_count(!took);
+    if ((a | b | threadIdx.z) == 0 && idle_threads) atomicAdd(idle, (unsigned long long)idle_threads);
+}
+
+// The plane K = L of the lambda map: the 3-simplex of blocks {I <= J <= K},
+// launched on the m = 3 lambda grid, block (I, J, K) taken as (I, J, K, K).
+__global__ void k_cover4_plane(int64_t n, int rho, int nb, int p3, int32_t *count,
+                               unsigned long long *idle) {
+    const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z % rho, d = threadIdx.z / rho;
+    const List3 L = decode3<MAP_LAMBDA>(blockIdx.x, blockIdx.y, blockIdx.z, p3, nb);
+    bool took = false;
+    for (int t = 0; t < L.cnt; ++t) {
+        const int i = L.i[t] * rho + a, j = L.j[t] * rho + b, k = L.k[t] * rho + c, l = L.k[t] * rho + d;
+        if (i <= j && j <= k && k <= l && l < n) {
+            atomicAdd(count + index4(i, j, k, l), 1);
+            took = true;
+        }
+    }
+    const int idle_threads = __syncthreads_count(!took);
+    if ((a | b | threadIdx.z) == 0 && idle_threads) atomicAdd(idle, (unsigned long long)idle_threads);
+}
+
 // Every map has an m = 2 form; the rectangular box has no m = 3 form.
+// m = 4: the lambda map and the bounding box.
 static bool valid_map(int m, int map) {
+    if (m == 4) return map == MAP_LAMBDA || map == MAP_BBOX;
     return map >= MAP_LAMBDA && (map <= MAP_LINEAR || (m == 2 && map == MAP_RB));
 }
 
@@ -101,7 +168,12 @@ static bool valid_map(int m, int map) {
 using namespace sx;
 
 extern "C" int64_t simplex_grid_blocks(int m, int64_t nb, int map) {
-    if ((m != 2 && m != 3) || nb < 1 || nb > (1 << 20) || !valid_map(m, map)) return -1;
+    if (m < 2 || m > 4 || nb < 1 || nb > (1 << 20) || !valid_map(m, map)) return -1;
+    if (m == 4) {
+        if (nb > 4096) return -1;
+        const Grid4 g = grid4(nb, map);
+        return g.gx * g.gy * g.gz * g.gw;
+    }
     Grid g = m == 2 ? grid2(nb, map) : grid3(nb, map);
     return g.gx * g.gy * g.gz;
 }
@@ -110,6 +182,11 @@ extern "C" int simplex_map_blocks_host(int m, int64_t nb, int map, int32_t *out)
     int64_t total = simplex_grid_blocks(m, nb, map);
     if (total < 0 || !out) return SIMPLEX_EINVAL;
     if (nb > 65535) return SIMPLEX_EOVERFLOW;
+    if (m == 4) {
+        const Grid4 g4 = grid4(nb, map);
+        for (int64_t w = 0; w < total; ++w) table_entry4(map, g4, (int)nb, w, out + 8 * w);
+        return SIMPLEX_OK;
+    }
     Grid g = m == 2 ? grid2(nb, map) : grid3(nb, map);
     for (int64_t w = 0; w < total; ++w) {
         if (m == 2) table_entry<2>(map, g, (int)nb, w, out + 4 * w);
@@ -123,14 +200,18 @@ extern "C" int simplex_map_blocks(int m, int64_t nb, int map, int32_t *out, void
     if (total < 0 || !out) return SIMPLEX_EINVAL;
     if (nb > 65535) return SIMPLEX_EOVERFLOW;
     if (!aligned(out, 4)) return SIMPLEX_EALIGN;
-    Grid g = m == 2 ? grid2(nb, map) : grid3(nb, map);
     cudaStream_t s = (cudaStream_t)stream;
     const int threads = 256;
     int64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
     prof_begin(s);
-    if (m == 2) k_map_blocks<2><<<(unsigned)blocks, threads, 0, s>>>(map, g, (int)nb, total, out);
-    else k_map_blocks<3><<<(unsigned)blocks, threads, 0, s>>>(map, g, (int)nb, total, out);
+    if (m == 4) {
+        k_map_blocks4<<<(unsigned)blocks, threads, 0, s>>>(map, grid4(nb, map), (int)nb, total, out);
+    } else {
+        Grid g = m == 2 ? grid2(nb, map) : grid3(nb, map);
+        if (m == 2) k_map_blocks<2><<<(unsigned)blocks, threads, 0, s>>>(map, g, (int)nb, total, out);
+        else k_map_blocks<3><<<(unsigned)blocks, threads, 0, s>>>(map, g, (int)nb, total, out);
+    }
     prof_end(s);
     note_launches(1);
     return launch_status();
@@ -182,5 +263,37 @@ extern "C" int simplex_map3(int64_t n, int rho, int map, int32_t *count, int64_t
     else k_cover3<MAP_LINEAR><<<dim_of(g), blk, 0, s>>>(n, rho, (int)nb, g.p, count, id);
     prof_end(s);
     note_launches(1);
+    return launch_status();
+}
+
+extern "C" int simplex_map4(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
+                            void *stream) {
+    if (rho == 0) rho = 4;
+    if (n < 1 || rho < 1 || rho > 5 || !valid_map(4, map) || !count || !idle) return SIMPLEX_EINVAL;
+    if (!aligned(count, 4) || !aligned(idle, 8)) return SIMPLEX_EALIGN;
+    if (n > 65536) return SIMPLEX_EOVERFLOW;   // keeps the packed index below 2^63
+    const int64_t nb = (n + rho - 1) / rho;
+    const Grid4 g = grid4(nb, map);
+    if (g.gx * g.gz > 0x7fffffffLL || g.gy > 65535 || g.gw > 65535) return SIMPLEX_EOVERFLOW;
+    const int64_t vol = (n * (n + 1) / 2) * ((n + 2) * (n + 3) / 2) / 6;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = cuda_status(cudaMemsetAsync(count, 0, sizeof(int32_t) * (size_t)vol, s));
+    if (st) return st;
+    if ((st = cuda_status(cudaMemsetAsync(idle, 0, sizeof(int64_t), s)))) return st;
+    const dim3 blk(rho, rho, rho * rho);
+    const dim3 grd((unsigned)(g.gx * g.gz), (unsigned)g.gy, (unsigned)g.gw);
+    unsigned long long *id = (unsigned long long *)idle;
+    prof_begin(s);
+    if (map == MAP_LAMBDA) {
+        k_cover4<MAP_LAMBDA><<<grd, blk, 0, s>>>(n, rho, (int)nb, g.p, (uint32_t)g.gx, count, id);
+        if ((st = launch_status())) return st;
+        const Grid g3 = grid3(nb, MAP_LAMBDA);
+        k_cover4_plane<<<dim_of(g3), blk, 0, s>>>(n, rho, (int)nb, g3.p, count, id);
+        note_launches(2);
+    } else {
+        k_cover4<MAP_BBOX><<<grd, blk, 0, s>>>(n, rho, (int)nb, 0, (uint32_t)g.gx, count, id);
+        note_launches(1);
+    }
+    prof_end(s);
     return launch_status();
 }

@@ -27,6 +27,16 @@
 //    authors' earlier work, Sec. II): a 1-D grid over the row-major
 //    enumeration, inverted with sqrtf / cbrtf and then fixed up exactly in
 //    integer arithmetic.
+//  * lambda, m = 4 (Sec. III-D: the recursive set with r = 1/2, beta = 2,
+//    V(S_n^4) = (n^4 - n)/14; the paper gives the set and its volume, not a
+//    map): the blocks I <= J <= K < L split at half size h into L L L L and
+//    H H H H (the two recursive copies) and the cross terms, which one h^4
+//    orthotope covers with idle points (ortho4).  Grid (p/2)^3 x (p/2 + p/8):
+//    w < p/2 is the top orthotope; the orthotopes of the recursive levels
+//    sit in grid rows y in [b, 2b) (b = 2^floor(log2 y), sub-problem
+//    q = floor(x / b) at data offset 2 q b, as for m = 2 and 3) with their
+//    last two coordinates (u, v) stored as m = u b + v in z + (w - p/2) p/2.
+//    The plane K = L is the 3-simplex {I <= J <= K} and takes the m = 3 map.
 //  * rectangular box, m = 2 only (Sec. II: the RB strategy for packed
 //    triangular matrices, applied to the parallel space): the lower triangle
 //    of nb blocks per side is cut at half height h = floor(nb / 2) and its top
@@ -202,6 +212,77 @@ SX_HD List3 decode3_linear(int64_t l, int nb) {
     return L;
 }
 
+// ---------------------------------------------------------------- m = 4
+
+// A data block (I, J, K, L) of the 4-simplex of blocks, or none (ok false).
+struct Blk4 {
+    int i, j, k, l;
+    bool ok;
+};
+
+// The orthotope of one level: local point (a, b, c, d) in [0, h)^4 to the
+// cross terms {x1 <= x2 <= x3 < x4 : x1 < h <= x4} over [0, 2h) at data
+// offset off, or none.  Fold (a, b) and (c, d) each into a pair "a <= b" or
+// "b < a" (and likewise for c, d); then
+//   a <= b, d <  c:                      L L H H  (a, b, h+d, h+c)
+//   a <= b, c <= d, b <= c:               L L L H  (a, b, c, h+d), x4' >= x3
+//   a <= b, c <= d, a <= c, d < b:        L H H H  (a, h+c, h+d, h+b), x1 <= x2'
+//   b <  a, c <= d, d <= a:               L L L H  (c, d, a, h+b), x4' < x3
+//   b <  a, d <  c, b <= d:               L H H H  (a, h+b, h+d, h+c), x2' < x1
+// and every other point is idle.  The five images are disjoint and their
+// union is all cross terms (checked against an enumeration of the cross
+// terms by the oracle).
+SX_HD Blk4 ortho4(int h, int off, int a, int b, int c, int d, int nb) {
+    Blk4 B;
+    B.ok = false; B.i = B.j = B.k = B.l = -1;
+    int x1, x2, x3, x4;
+    if (a <= b) {
+        if (d < c) { x1 = a; x2 = b; x3 = h + d; x4 = h + c; }
+        else if (b <= c) { x1 = a; x2 = b; x3 = c; x4 = h + d; }
+        else if (a <= c && d < b) { x1 = a; x2 = h + c; x3 = h + d; x4 = h + b; }
+        else return B;
+    } else {
+        if (c <= d) {
+            if (d > a) return B;
+            x1 = c; x2 = d; x3 = a; x4 = h + b;
+        } else {
+            if (b > d) return B;
+            x1 = a; x2 = h + b; x3 = h + d; x4 = h + c;
+        }
+    }
+    if (off + x4 >= nb) return B;
+    B.i = off + x1; B.j = off + x2; B.k = off + x3; B.l = off + x4;
+    B.ok = true;
+    return B;
+}
+
+// Depth of the grid's slab (w >= p/2) that holds the recursive levels: the
+// largest level (b = p/4) stores b^2 = p^2/16 points (u, v) in rows of p/2.
+SX_HD int slab4(int64_t p) { return p >= 8 ? (int)(p / 8) : (p == 4 ? 1 : 0); }
+
+SX_HD Blk4 decode4_lambda(uint32_t x, uint32_t y, uint32_t z, uint32_t w, int p, int nb) {
+    const uint32_t h0 = (uint32_t)p >> 1;
+    if (w < h0) return ortho4((int)h0, 0, (int)x, (int)y, (int)z, (int)w, nb);
+    Blk4 B;
+    B.ok = false; B.i = B.j = B.k = B.l = -1;
+    if (y == 0) return B;
+    const int l = floor_log2(y);            // level: orthotope side b = 2^l
+    const uint32_t b = 1u << l;
+    const uint32_t m = (w - h0) * h0 + z;   // (u, v) of the level's orthotope
+    if (m >= b * b) return B;
+    const uint32_t q = x >> l;              // sub-problem of the level
+    return ortho4((int)b, (int)(q << (l + 1)), (int)(x - (q << l)), (int)(y - b), (int)(m >> l),
+                  (int)(m & (b - 1)), nb);
+}
+
+SX_HD Blk4 decode4_bbox(uint32_t x, uint32_t y, uint32_t z, uint32_t w, int nb) {
+    Blk4 B;
+    B.ok = x <= y && y <= z && z <= w && (int)w < nb;
+    B.i = B.ok ? (int)x : -1; B.j = B.ok ? (int)y : -1;
+    B.k = B.ok ? (int)z : -1; B.l = B.ok ? (int)w : -1;
+    return B;
+}
+
 // ---------------------------------------------------------------- grids
 
 struct Grid { int64_t gx, gy, gz; int p; };
@@ -232,6 +313,22 @@ SX_HD Grid grid3(int64_t nb, int map) {
         g.gx = 0; g.gy = 0; g.gz = 0;   // no 3-simplex form (callers reject it)
     } else {
         g.gx = nb * (nb + 1) * (nb + 2) / 6; g.gy = 1; g.gz = 1;
+    }
+    return g;
+}
+
+// 4-D grid of the m = 4 maps (x fastest, then y, z, w).  LAMBDA: the blocks
+// I <= J <= K < L only (the plane K = L takes grid3); BBOX: nb^4, all of
+// I <= J <= K <= L.
+struct Grid4 { int64_t gx, gy, gz, gw; int p; };
+
+SX_HD Grid4 grid4(int64_t nb, int map) {
+    Grid4 g; g.p = 0;
+    if (map == MAP_LAMBDA) {
+        int64_t p = pow2_at_least(nb);
+        g.p = (int)p; g.gx = g.gy = g.gz = p / 2; g.gw = p / 2 + slab4(p);
+    } else {
+        g.gx = g.gy = g.gz = g.gw = nb;
     }
     return g;
 }

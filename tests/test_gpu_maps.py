@@ -1,6 +1,6 @@
 """GPU parity of the block-space maps: decode tables bit-exact against the
 oracle's recursive construction, coverage counts and idle threads equal to
-the oracle's thread-level enumeration (Sec. III-A, III-C)."""
+the oracle's thread-level enumeration (Sec. III-A, III-C, III-D)."""
 import numpy as np
 import pytest
 import torch
@@ -72,3 +72,31 @@ def test_cover_full_size(gpu, oracle, mp):
     torch.cuda.empty_cache()
     _, ref_idle = oracle.cover3(n, 8, mp)
     assert int(i3.item()) == ref_idle
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox"])
+@pytest.mark.parametrize("nb", [1, 2, 3, 8, 13, 32, 64])
+def test_map4_table_device(gpu, oracle, mp, nb):
+    if mp != "lambda" and nb > 32:
+        pytest.skip("large box tables add nothing")
+    t = gpu.map_blocks(4, nb, mp).cpu().numpy()
+    assert np.array_equal(t, oracle.table4(nb, mp))
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox"])
+@pytest.mark.parametrize("n,rho", [(1, 4), (2, 1), (5, 2), (17, 4), (33, 4), (40, 5), (64, 3)])
+def test_cover4_device(gpu, oracle, mp, n, rho):
+    count, idle = gpu.map4(n, rho, mp)
+    ref_count, ref_idle = oracle.cover4(n, rho, mp)
+    assert np.array_equal(count.cpu().numpy(), ref_count)
+    assert int(idle.item()) == ref_idle
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox"])
+def test_cover4_n128(gpu, oracle, mp):
+    """n = 128 points, 4^4 threads per block: every one of the C(131, 4) =
+    11,716,640 quadruples is reached exactly once."""
+    count, idle = gpu.map4(128, 4, mp)
+    assert count.numel() == 11716640
+    assert int(count.min()) == 1 and int(count.max()) == 1
+    assert int(idle.item()) == oracle.cover4(128, 4, mp)[1]

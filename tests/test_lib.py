@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_abi_and_strerror(L):
-    assert sx.simplex_abi_version() == 3
+    assert sx.simplex_abi_version() == 4
     for st in range(7):
         assert L.simplex_strerror(st)
     assert L.simplex_last_cuda_error() == 0
@@ -72,6 +72,18 @@ def test_decode3_host_equals_oracle(oracle, mp, nb):
     assert np.array_equal(host_table(3, nb, mp), oracle.table3(nb, mp))
 
 
+@pytest.mark.parametrize("mp", ["lambda", "bbox"])
+@pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 7, 8, 9, 16, 17, 31, 32, 33, 64])
+def test_decode4_host_equals_oracle(oracle, mp, nb):
+    """The library's closed-form m = 4 decode equals the oracle's table, which
+    places each cross term of each level at its orthotope point (the inverse
+    direction) and recurses."""
+    if mp != "lambda" and nb > 32:
+        pytest.skip("box tables of this size add nothing")
+    assert sx.simplex_grid_blocks(4, nb, mp) == np.prod(oracle.grid4(nb, mp))
+    assert np.array_equal(host_table(4, nb, mp), oracle.table4(nb, mp))
+
+
 def test_linear_decode_large_indices(oracle):
     """The root-based inverse with its integer fix-up stays exact where FP32
     roots alone are off (8l+1 and 6l beyond 2^24): whole tables of a large
@@ -87,7 +99,15 @@ def test_grid_and_workspace_sizes(L):
     assert sx.simplex_grid_blocks(3, 32, "lambda") == 16 * 16 * (16 + 8 + 2)
     assert sx.simplex_grid_blocks(3, 32, "bbox") == 32 ** 3
     assert sx.simplex_grid_blocks(3, 32, "linear") == 32 * 33 * 34 // 6
-    assert sx.simplex_grid_blocks(4, 32, "lambda") == -1
+    # m = 4: (p/2)^3 x (p/2 + p/8) for lambda (the plane K = L is the m = 3
+    # grid's), nb^4 for the box, no linear or RB form
+    assert sx.simplex_grid_blocks(4, 32, "lambda") == 16 ** 3 * (16 + 4)
+    assert sx.simplex_grid_blocks(4, 4, "lambda") == 2 ** 3 * (2 + 1)
+    assert sx.simplex_grid_blocks(4, 2, "lambda") == 1
+    assert sx.simplex_grid_blocks(4, 32, "bbox") == 32 ** 4
+    assert sx.simplex_grid_blocks(4, 32, "linear") == -1
+    assert sx.simplex_grid_blocks(4, 32, "rb") == -1
+    assert sx.simplex_grid_blocks(5, 32, "lambda") == -1
     # the rectangular box: 2-simplex only, exactly the triangle's blocks
     assert sx.simplex_grid_blocks(2, 32, "rb") == 32 * 33 // 2
     assert sx.simplex_grid_blocks(2, 33, "rb") == 33 * 34 // 2
@@ -126,6 +146,10 @@ def test_validation_before_gpu_work(L):
     assert L.simplex_atm_energy(8, 3, 16, 1.0, 1e-4, 16, 0, 256, 16, null) == 6  # too small
     assert L.simplex_map2(10, 33, 0, 16, 16, null) == 1                          # rho > 32
     assert L.simplex_map3(10, 11, 0, 16, 16, null) == 1                          # rho^3 > 1024
+    assert L.simplex_map4(10, 6, 0, 16, 16, null) == 1                           # rho^4 > 1024
+    assert L.simplex_map4(10, 4, 2, 16, 16, null) == 1                           # no m = 4 linear map
+    assert L.simplex_map4(10, 4, 3, 16, 16, null) == 1                           # no m = 4 RB
+    assert L.simplex_map4(65537, 4, 0, 16, 16, null) == 3                        # index overflow
     assert L.simplex_stress_bwd(8, 4, 16, 16, 1.0, 20, 0, 0, null, 0, null) == 2  # grad not 16B
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, null, 0, 0, null, 0, null) == 1  # NULL loss
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, null, 16, 0, 0, null, 0, null) == 1  # NULL grad

@@ -229,6 +229,47 @@ def test_lambda3_volume_and_extra(oracle, k):
         assert alpha == pytest.approx(paper()["lambda3_extra_volume"]["value"], abs=1e-4)
 
 
+# ---------------------------------------------------------------- 4-simplex maps
+
+@pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 7, 8, 9, 13, 16, 24])
+@pytest.mark.parametrize("m", ["lambda", "bbox"])
+def test_table4_is_bijection(oracle, nb, m):
+    """lambda lists every block of {I <= J <= K < L < nb} exactly once (the
+    plane K = L is left to the 3-simplex map) and no grid point twice (the
+    construction raises on a collision); the box lists every block of
+    {I <= J <= K <= L}."""
+    blocks = blocks_of(oracle.table4(nb, m), 4)
+    strict = m == "lambda"
+    want = [(i, j, k, l) for l in range(nb) for k in range(l if strict else l + 1)
+            for j in range(k + 1) for i in range(j + 1)]
+    assert len(blocks) == len(want) == math.comb(nb + (2 if strict else 3), 4)
+    assert sorted(blocks) == sorted(want)
+
+
+@pytest.mark.parametrize("k", range(1, 8))
+def test_lambda4_volume_and_extra(oracle, k):
+    """The recursive set S_n^4 (r = 1/2, beta = 2) holds (n^4 - n)/14 grid
+    points (Sec. III-D), at least the C(n+2, 4) blocks I <= J <= K < L it
+    covers (the paper's strict inequality holds from n = 4; at n = 2 both
+    are 1), inside a grid of (n/2)^3 (n/2 + n/8) blocks."""
+    p = 2 ** k
+    V = oracle.volume4(p)
+    assert V * 14 == p ** 4 - p
+    D = math.comb(p + 2, 4)
+    assert V >= D and (V > D or p == 2)
+    assert len(blocks_of(oracle.table4(p, "lambda"), 4)) == D
+    assert int(np.prod(oracle.grid4(p, "lambda"))) >= V
+
+
+def test_lambda4_extra_volume_limit(oracle):
+    """Sec. III-D: the extra volume of the r = 1/2, beta = 2 set tends to
+    m!/(2^m - 2) - 1 = 5/7 for m = 4."""
+    p = 2 ** 13
+    V = oracle.volume4(p)
+    assert V / math.comb(p + 2, 4) - 1 == pytest.approx(
+        paper()["general_m_r_half_beta_2"]["m4_extra_limit"], abs=1e-3)
+
+
 def test_bbox3_extra_volume(oracle):
     g = paper()
     nb = 1024
@@ -308,6 +349,27 @@ def test_cover3(oracle, n, rho, m):
             tab = oracle.table3(nb, m)
             pairs = int((tab[:, 3] >= 0).sum())
         assert idle == g * rho ** 3 - V + pairs * busy_pair
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 13, 17])
+@pytest.mark.parametrize("rho", [1, 2, 4])
+@pytest.mark.parametrize("m", ["lambda", "bbox"])
+def test_cover4(oracle, n, rho, m):
+    """Every element of Delta_n^4 (C(n+3, 4) of them) is reached once; with
+    n a multiple of rho the idle threads are the launched threads less the
+    elements, plus the threads that take an element in both blocks of a
+    diagonal pair of the m = 3 grid that carries the plane K = L."""
+    counts, idle = oracle.cover4(n, rho, m)
+    assert counts.size == math.comb(n + 3, 4)
+    assert (counts == 1).all()
+    nb = -(-n // rho)
+    if n % rho == 0:
+        g = int(np.prod(oracle.grid4(nb, m)))
+        pairs = 0
+        if m == "lambda":
+            g += int(np.prod(oracle.grid3(nb, "lambda")))
+            pairs = int((oracle.table3(nb, "lambda")[:, 3] >= 0).sum())
+        assert idle == g * rho ** 4 - math.comb(n + 3, 4) + pairs * math.comb(rho + 3, 4)
 
 
 # ---------------------------------------------------------------- EDM
