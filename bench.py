@@ -296,9 +296,9 @@ def row_edm_n1024_d3(torch, sx, peaks):
     return r
 
 
-def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox", "rb")):
+def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox", "rb"), out=None):
     n, d = x.shape
-    o = torch.empty(n * (n + 1) // 2, device="cuda")
+    o = out if out is not None else torch.empty(n * (n + 1) // 2, device="cuda")
     pairs = o.numel()
     ws = {mp: sx.workspace("edm", n, d, mp, prec) for mp in maps}
     r = {"unit": "pairs/s", "pairs": pairs, "prec": prec}
@@ -319,20 +319,61 @@ def _edm_big(torch, sx, peaks, x, prec, maps=("lambda", "bbox", "rb")):
     return r
 
 
+def _edm_error(torch, o, xh, seed, count=1_000_000, tile=128):
+    """Relative error of packed EDM entries against the squared distance in
+    FP64 (computed here from the FP32 inputs, by the definition): `count`
+    seeded pairs over the whole triangle and as many pairs inside diagonal
+    tiles of `tile` points (where the Gram form cancels most), plus the
+    exact-zero diagonal.  Reported, not asserted (the tests assert)."""
+    n = len(xh)
+    x64 = xh.astype(np.float64)
+    pr = synth.sample_pairs(count, n, seed)
+    near = synth.sample_pairs(count, tile, seed + 1)
+    base = (synth.splitmix64(seed + 2, count) % np.uint64(max(n // tile, 1))).astype(np.int64) * tile
+    near = np.minimum(near + base[:, None], n - 1)
+    near = np.stack([np.maximum(near[:, 0], near[:, 1]), np.minimum(near[:, 0], near[:, 1])], axis=1)
+    out = {}
+    for name, p in (("sampled", pr), ("diagonal_tiles", near)):
+        i, j = p[:, 0], p[:, 1]
+        got = o[torch.from_numpy(i * (i + 1) // 2 + j).cuda()].double().cpu().numpy()
+        rel = np.empty(len(i))
+        for c in range(0, len(i), 100_000):
+            sl = slice(c, c + 100_000)
+            ref = ((x64[i[sl]] - x64[j[sl]]) ** 2).sum(axis=1)
+            off = i[sl] != j[sl]
+            rel[sl] = np.where(off, np.abs(got[sl] - ref) / np.maximum(ref, 1e-30), 0.0)
+        out[name] = {"pairs": int(len(i)), "max_rel": float(rel.max()),
+                     "p99_rel": float(np.percentile(rel, 99))}
+    d = np.arange(0, n, max(n // 4096, 1), dtype=np.int64)
+    out["diagonal_exact_zero"] = bool((o[torch.from_numpy(d * (d + 1) // 2 + d).cuda()] == 0).all())
+    out["reference"] = "FP64 squared distance of the FP32 inputs"
+    out["tolerance"] = 1e-5
+    return out
+
+
 def row_edm_n32768_d256(torch, sx, peaks):
     """EDM n=32768, d=256 on tensor cores (BF16 hi+lo split): 536,887,296
     outputs, 2.15 GB written; FP32 SIMT path alongside."""
-    x = torch.from_numpy(synth.make_points("edm_n32768_d256")).cuda()
-    r = _edm_big(torch, sx, peaks, x, "bf16x3")
-    r["fp32_simt_lambda"] = _edm_big(torch, sx, peaks, x, "fp32", ("lambda", "bbox"))["lambda"]
+    xh = synth.make_points("edm_n32768_d256")
+    x = torch.from_numpy(xh).cuda()
+    o = torch.empty(len(xh) * (len(xh) + 1) // 2, device="cuda")
+    r = _edm_big(torch, sx, peaks, x, "bf16x3", out=o)
+    sx.simplex_edm_packed(x, o, "lambda", "bf16x3", sx.workspace("edm", x.shape[0], x.shape[1], "lambda", "bf16x3"))
+    r["error_lambda"] = _edm_error(torch, o, xh, seed=21)
+    r["fp32_simt_lambda"] = _edm_big(torch, sx, peaks, x, "fp32", ("lambda", "bbox"), out=o)["lambda"]
     return r
 
 
 def row_edm_n65536_d64(torch, sx, peaks):
     """EDM n=65536, d=64 on tensor cores: 2,147,516,416 outputs, 8.6 GB."""
     w = synth.WORKLOADS["stress_n65536_d64"]
-    x = torch.from_numpy(synth.normal(w["n"], w["d"], w["seed"])).cuda()
-    return _edm_big(torch, sx, peaks, x, "bf16x3")
+    xh = synth.normal(w["n"], w["d"], w["seed"])
+    x = torch.from_numpy(xh).cuda()
+    o = torch.empty(len(xh) * (len(xh) + 1) // 2, device="cuda")
+    r = _edm_big(torch, sx, peaks, x, "bf16x3", out=o)
+    sx.simplex_edm_packed(x, o, "lambda", "bf16x3", sx.workspace("edm", x.shape[0], x.shape[1], "lambda", "bf16x3"))
+    r["error_lambda"] = _edm_error(torch, o, xh, seed=22)
+    return r
 
 
 def row_edm_n16384_d64(torch, sx, peaks):

@@ -116,19 +116,40 @@ __device__ __forceinline__ int64_t index4(int i, int j, int k, int l) {
     return tl * tl2 / 6 + (int64_t)k * (k + 1) * (k + 2) / 6 + (int64_t)j * (j + 1) / 2 + i;
 }
 
-// One thread per (a, b, c, d) of a rho^4 block (blockDim (rho, rho, rho^2),
-// threadIdx.z = c + rho d) on the 4-D grid of grid4 (blockIdx.x = x + gx z,
+// Division by a divisor fixed at launch: floor(x / d) = (umulhi(x, m) + x) >> s
+// with s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1, exact for
+// x < 2^31 (the round-up multiplier of Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994).
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+static FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    f.s = 0;
+    while ((1ull << f.s) < d) ++f.s;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << f.s) - d)) / d) + 1);
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t x, const FastDiv &f) {
+    return (__umulhi(x, f.m) + x) >> f.s;
+}
+
+// One thread per (a, b, c, d) of a RHO^4 block (blockDim (RHO, RHO, RHO^2),
+// threadIdx.z = c + RHO d) on the 4-D grid of grid4 (blockIdx.x = x + gx z,
 // blockIdx.y = y, blockIdx.z = w); see simplex_map4 in simplex.h.
-template <int MAP>
-__global__ void k_cover4(int64_t n, int rho, int nb, int p, uint32_t gx, int32_t *count,
+template <int MAP, int RHO>
+__global__ void k_cover4(int64_t n, int nb, int p, FastDiv gx, int32_t *count,
                          unsigned long long *idle) {
-    const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z % rho, d = threadIdx.z / rho;
-    const uint32_t x = blockIdx.x % gx, z = blockIdx.x / gx;
+    const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z % RHO, d = threadIdx.z / RHO;
+    const uint32_t z = fast_div(blockIdx.x, gx), x = blockIdx.x - z * gx.d;
     const Blk4 B = MAP == MAP_LAMBDA ? decode4_lambda(x, blockIdx.y, z, blockIdx.z, p, nb)
                                      : decode4_bbox(x, blockIdx.y, z, blockIdx.z, nb);
     bool took = false;
     if (B.ok) {
-        const int i = B.i * rho + a, j = B.j * rho + b, k = B.k * rho + c, l = B.l * rho + d;
+        const int i = B.i * RHO + a, j = B.j * RHO + b, k = B.k * RHO + c, l = B.l * RHO + d;
         if (i <= j && j <= k && k <= l && l < n) {
             atomicAdd(count + index4(i, j, k, l), 1);
             took = true;
@@ -140,13 +161,13 @@ __global__ void k_cover4(int64_t n, int rho, int nb, int p, uint32_t gx, int32_t
 
 // The plane K = L of the lambda map: the 3-simplex of blocks {I <= J <= K},
 // launched on the m = 3 lambda grid, block (I, J, K) taken as (I, J, K, K).
-__global__ void k_cover4_plane(int64_t n, int rho, int nb, int p3, int32_t *count,
-                               unsigned long long *idle) {
-    const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z % rho, d = threadIdx.z / rho;
+template <int RHO>
+__global__ void k_cover4_plane(int64_t n, int nb, int p3, int32_t *count, unsigned long long *idle) {
+    const int a = threadIdx.x, b = threadIdx.y, c = threadIdx.z % RHO, d = threadIdx.z / RHO;
     const List3 L = decode3<MAP_LAMBDA>(blockIdx.x, blockIdx.y, blockIdx.z, p3, nb);
     bool took = false;
     for (int t = 0; t < L.cnt; ++t) {
-        const int i = L.i[t] * rho + a, j = L.j[t] * rho + b, k = L.k[t] * rho + c, l = L.k[t] * rho + d;
+        const int i = L.i[t] * RHO + a, j = L.j[t] * RHO + b, k = L.k[t] * RHO + c, l = L.k[t] * RHO + d;
         if (i <= j && j <= k && k <= l && l < n) {
             atomicAdd(count + index4(i, j, k, l), 1);
             took = true;
@@ -154,6 +175,21 @@ __global__ void k_cover4_plane(int64_t n, int rho, int nb, int p3, int32_t *coun
     }
     const int idle_threads = __syncthreads_count(!took);
     if ((a | b | threadIdx.z) == 0 && idle_threads) atomicAdd(idle, (unsigned long long)idle_threads);
+}
+
+template <int RHO>
+static void launch_cover4(int map, int64_t n, int nb, const Grid4 &g, int32_t *count,
+                          unsigned long long *idle, cudaStream_t s) {
+    const dim3 blk(RHO, RHO, RHO * RHO);
+    const dim3 grd((unsigned)(g.gx * g.gz), (unsigned)g.gy, (unsigned)g.gw);
+    const FastDiv gx = make_fastdiv((uint32_t)g.gx);
+    if (map == MAP_LAMBDA) {
+        k_cover4<MAP_LAMBDA, RHO><<<grd, blk, 0, s>>>(n, nb, g.p, gx, count, idle);
+        const Grid g3 = grid3(nb, MAP_LAMBDA);
+        k_cover4_plane<RHO><<<dim_of(g3), blk, 0, s>>>(n, nb, g3.p, count, idle);
+    } else {
+        k_cover4<MAP_BBOX, RHO><<<grd, blk, 0, s>>>(n, nb, 0, gx, count, idle);
+    }
 }
 
 // Every map has an m = 2 form; the rectangular box has no m = 3 form.
@@ -280,20 +316,16 @@ extern "C" int simplex_map4(int64_t n, int rho, int map, int32_t *count, int64_t
     int st = cuda_status(cudaMemsetAsync(count, 0, sizeof(int32_t) * (size_t)vol, s));
     if (st) return st;
     if ((st = cuda_status(cudaMemsetAsync(idle, 0, sizeof(int64_t), s)))) return st;
-    const dim3 blk(rho, rho, rho * rho);
-    const dim3 grd((unsigned)(g.gx * g.gz), (unsigned)g.gy, (unsigned)g.gw);
     unsigned long long *id = (unsigned long long *)idle;
     prof_begin(s);
-    if (map == MAP_LAMBDA) {
-        k_cover4<MAP_LAMBDA><<<grd, blk, 0, s>>>(n, rho, (int)nb, g.p, (uint32_t)g.gx, count, id);
-        if ((st = launch_status())) return st;
-        const Grid g3 = grid3(nb, MAP_LAMBDA);
-        k_cover4_plane<<<dim_of(g3), blk, 0, s>>>(n, rho, (int)nb, g3.p, count, id);
-        note_launches(2);
-    } else {
-        k_cover4<MAP_BBOX><<<grd, blk, 0, s>>>(n, rho, (int)nb, 0, (uint32_t)g.gx, count, id);
-        note_launches(1);
+    switch (rho) {
+        case 1: launch_cover4<1>(map, n, (int)nb, g, count, id, s); break;
+        case 2: launch_cover4<2>(map, n, (int)nb, g, count, id, s); break;
+        case 3: launch_cover4<3>(map, n, (int)nb, g, count, id, s); break;
+        case 4: launch_cover4<4>(map, n, (int)nb, g, count, id, s); break;
+        default: launch_cover4<5>(map, n, (int)nb, g, count, id, s); break;
     }
     prof_end(s);
+    note_launches(map == MAP_LAMBDA ? 2 : 1);
     return launch_status();
 }
