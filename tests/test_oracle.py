@@ -246,7 +246,7 @@ def test_table4_is_bijection(oracle, nb, m):
     assert sorted(blocks) == sorted(want)
 
 
-@pytest.mark.parametrize("k", range(1, 8))
+@pytest.mark.parametrize("k", range(1, 7))
 def test_lambda4_volume_and_extra(oracle, k):
     """The recursive set S_n^4 (r = 1/2, beta = 2) holds (n^4 - n)/14 grid
     points (Sec. III-D), at least the C(n+2, 4) blocks I <= J <= K < L it
