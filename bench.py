@@ -49,6 +49,13 @@ NU, EPS = 1.0, 1e-4
 # vectors the same energy takes 22 (R^3 and the bracket 1 + 3 cos cos cos
 # separately).
 FLOPS_PER_TRIPLE = 20
+# The same count (an FMA is 2 flops) for a triple of the forces kernel, which
+# forms e and its three derivatives by the squared sides: the three unit-vector
+# dot products (15), the cosine products p1, p2, c_ik, C_p (4), X, Y, Z with
+# their r products (6), R^3 (2), e accumulated (4), H = 1 + 5 C_p (2), 1.5 R^3
+# (1), S = Y - X - Z (2), the three derivatives (15) and their sums into the
+# (i,j), (i,k) and (j,k) accumulators (2.5): 53.5.
+FORCE_FLOPS_PER_TRIPLE = 53.5
 ROWS_NAMES = ("cover2_n16384", "cover3_n1024", "cover4_n256", "edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
               "stress_n65536_d64", "edm_n16384_d64", "edm_n16384_d256", "stress_n16384_d64")
 FP32_LANES_PER_SM = 128
@@ -407,6 +414,8 @@ def row_atm_n4096(torch, sx, peaks):
         ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws), 3)
         r["energy_forces_" + mp] = triples(n) / (ms / 1e3)
     r["energy_forces_lambda_vs_bbox"] = r["energy_forces_lambda"] / r["energy_forces_bbox"]
+    r["energy_fp32_frac"] = FLOPS_PER_TRIPLE * r["energy_lambda"] / 1e12 / _fp32_peak(torch)
+    r["energy_forces_fp32_frac"] = FORCE_FLOPS_PER_TRIPLE * r["energy_forces_lambda"] / 1e12 / _fp32_peak(torch)
     return r
 
 
@@ -425,6 +434,7 @@ def row_atm_n16384(torch, sx, peaks):
     ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, "lambda", ws), 1, 0)
     r["energy_forces_lambda"] = triples(n) / (ms / 1e3)
     r["energy_fp32_frac"] = FLOPS_PER_TRIPLE * r["energy_lambda"] / 1e12 / _fp32_peak(torch)
+    r["energy_forces_fp32_frac"] = FORCE_FLOPS_PER_TRIPLE * r["energy_forces_lambda"] / 1e12 / _fp32_peak(torch)
     return r
 
 
