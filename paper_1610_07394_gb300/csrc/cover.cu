@@ -283,7 +283,7 @@ extern "C" int simplex_map3(int64_t n, int rho, int map, int32_t *count, int64_t
     if (rho == 0) rho = 8;
     if (n < 1 || rho < 1 || rho > 10 || !valid_map(3, map) || !count || !idle) return SIMPLEX_EINVAL;
     if (!aligned(count, 4) || !aligned(idle, 8)) return SIMPLEX_EALIGN;
-    if (n > 3000000) return SIMPLEX_EOVERFLOW;   // keeps k(k+1)(k+2) < 2^63
+    if (n > 3000000) return SIMPLEX_EOVERFLOW;   // keeps the packed index and its products in 64 bits
     const int64_t nb = (n + rho - 1) / rho;
     Grid g = grid3(nb, map);
     if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;

@@ -150,6 +150,15 @@ def test_validation_before_gpu_work(L):
     assert L.simplex_map4(10, 4, 2, 16, 16, null) == 1                           # no m = 4 linear map
     assert L.simplex_map4(10, 4, 3, 16, 16, null) == 1                           # no m = 4 RB
     assert L.simplex_map4(65537, 4, 0, 16, 16, null) == 3                        # index overflow
+    # size limits, reported before any device work
+    assert L.simplex_map2((1 << 31) + 1, 16, 0, 16, 16, null) == 3               # n > 2^31
+    assert L.simplex_map3(3000001, 8, 0, 16, 16, null) == 3                      # 64-bit index bound
+    assert L.simplex_edm_packed((1 << 31) + 1, 3, 16, 16, 0, 0, null, 0, null) == 3   # n > 2^31
+    assert L.simplex_edm_packed(1 << 20, (1 << 24) + 1, 16, 16, 0, 0, null, 0, null) == 3  # d > 2^24
+    assert L.simplex_atm_energy((1 << 22) + 1, 3, 16, 1.0, 1e-4, 16, 0, null, 0, null) == 3  # n > 2^22
+    assert L.simplex_atm_energy(0, 3, 16, 1.0, 1e-4, 16, 0, null, 0, null) == 1               # empty
+    assert L.simplex_map2(0, 16, 0, 16, 16, null) == 1                                         # empty
+    assert L.simplex_map4(0, 4, 0, 16, 16, null) == 1                                          # empty
     assert L.simplex_stress_bwd(8, 4, 16, 16, 1.0, 20, 0, 0, null, 0, null) == 2  # grad not 16B
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, null, 0, 0, null, 0, null) == 1  # NULL loss
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, null, 16, 0, 0, null, 0, null) == 1  # NULL grad
