@@ -367,7 +367,7 @@ __device__ __forceinline__ void wait_tables(uint32_t bar, uint32_t parity, bool 
 // pairs, the pair constants of (i, j) are the same in both lanes, and each
 // thread's 2 x 2 pairs (i, j) reuse every load twice.
 template <int MAP>
-__global__ void __launch_bounds__(256, 4) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
+__global__ void __launch_bounds__(256, 3) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
                                                            int nb, int p,
                                                            double *__restrict__ partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
