@@ -1,0 +1,54 @@
+"""The benchmark's output contract, checked on the CPU: the reference arm
+(the FP64 oracle timed on the host cores) prints one JSON line with the
+fields every line of bench.py carries, and the workload it names is the one
+the seeded input recipe builds."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _reference_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = _reference_line()
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["unit"] == "triplets/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_headline_workload_matches_recipe():
+    import bench
+    import synth
+    w = synth.WORKLOADS[bench.WORKLOAD]
+    cfg = bench.config_block()
+    assert cfg["n"] == w["n"] == 1024 and w["side"] == 10.0 and w["seed"] == 1
+    assert cfg["triples"] == bench.triples(w["n"]) == 1024 * 1023 * 1022 // 6
+    x = synth.make_points(bench.WORKLOAD)
+    assert x.shape == (1024, 3) and x.dtype.name == "float32"
+    assert float(x.min()) >= 0.0 and float(x.max()) < 10.0
+
+
+@pytest.mark.parametrize("name", ["cover2_n16384", "cover3_n1024", "cover4_n256", "edm_n65536_d64",
+                                  "atm_n4096", "stress_n65536_d64"])
+def test_rows_are_registered(name):
+    import bench
+    assert name in bench.ROWS and name in bench.ROWS_NAMES
