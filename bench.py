@@ -63,7 +63,7 @@ FP32_LANES_PER_SM = 128
 # workload, from the ncu capture summarised in
 # profiles/k_atm_energy_lambda_n1024.md (set to None whenever the kernel
 # changes and the capture has not been repeated).
-ENERGY_KERNEL_DRAM_BYTES = 10.030848e6
+ENERGY_KERNEL_DRAM_BYTES = 10.031360e6
 L2_FLUSH_BYTES = 512 << 20
 
 
