@@ -366,6 +366,9 @@ __device__ __forceinline__ void wait_tables(uint32_t bar, uint32_t parity, bool 
 // two consecutive k: the (i, k) and (j, k) values are loaded as packed
 // pairs, the pair constants of (i, j) are the same in both lanes, and each
 // thread's 2 x 2 pairs (i, j) reuse every load twice.
+// Three blocks per SM (80 registers, no spills): four at 64 registers
+// spilled around the k loop and ran 1% slower, the FMA pipe being the first
+// stall either way.
 template <int MAP>
 __global__ void __launch_bounds__(256, 3) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
                                                            int nb, int p,
