@@ -52,3 +52,30 @@ def test_headline_workload_matches_recipe():
 def test_rows_are_registered(name):
     import bench
     assert name in bench.ROWS and name in bench.ROWS_NAMES
+
+
+def test_edm_error_report(monkeypatch):
+    """The benchmark's EDM error report on a known output: the FP32 rounding
+    of the exact squared distances reports at most 2^-24 relative error and
+    an exactly-zero diagonal; a perturbed entry shows up as the maximum."""
+    import numpy as np
+    import torch
+    import bench
+    import synth
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    xh = synth.normal(300, 16, 7)
+    x64 = xh.astype(np.float64)
+    i, j = np.tril_indices(len(xh))          # row-major lower: index i(i+1)/2 + j
+    exact = ((x64[i] - x64[j]) ** 2).sum(axis=1)
+    o = torch.from_numpy(exact.astype(np.float32))
+    r = bench._edm_error(torch, o, xh, seed=5, count=20000, tile=32)
+    assert r["diagonal_exact_zero"]
+    for part in ("sampled", "diagonal_tiles"):
+        assert r[part]["pairs"] == 20000
+        assert r[part]["max_rel"] <= 2.0 ** -24 and r[part]["p99_rel"] <= r[part]["max_rel"]
+    bad = o.clone()
+    pr = synth.sample_pairs(20000, len(xh), 5)
+    k = int(pr[0, 0] * (pr[0, 0] + 1) // 2 + pr[0, 1])
+    if pr[0, 0] != pr[0, 1]:
+        bad[k] *= 1.001
+        assert bench._edm_error(torch, bad, xh, seed=5, count=20000, tile=32)["sampled"]["max_rel"] > 9e-4
