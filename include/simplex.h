@@ -279,8 +279,10 @@ int64_t simplex_workspace_bytes(int op, int64_t n, int64_t d, int map, int prec)
  * Scratch is a fixed 4 MiB array inside the library (one FP64 per grid block
  * plus 1024 reduction slots), held by every GPU that loads the library until
  * the process exits.  Problems whose grid needs more return SIMPLEX_ESCRATCH
- * before any work: with the lambda map that is n > 4096 points (BBOX:
- * n > 2048; LINEAR: n > 4096).  The first call on each device looks up the
+ * before any work.  The rule is simplex_grid_blocks(3, ceil(n/32), map) +
+ * 1024 <= 524288; in points that accepts n <= 4096 with the lambda map,
+ * n <= 2560 with BBOX and n <= 4640 with LINEAR.  The first call on each
+ * device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  The array needs no
  * clearing: every slot a call reads is written earlier in that call.  All

@@ -26,6 +26,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle.py``):
   pinned by closed-form triangles (equilateral, collinear, right angle), a
   pure-Python brute force using angles, invariances, Euler's theorem for a
   homogeneous function and FD of the energy.
+* ``atm_abs_energy`` (sum of |e|): pinned by the closed-form triangles in
+  absolute value, a pure-Python brute force of sum |e| on a cloud with terms
+  of both signs, and equality with E on a regular tetrahedron.
 * ``stress_loss`` / ``stress_grad_rows``: pinned by the two-point closed form,
   the zero at y = x, translation invariance and FD.
 """

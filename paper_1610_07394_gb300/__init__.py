@@ -384,8 +384,10 @@ class StressLoss(torch.autograd.Function):
     def backward(ctx, g):
         x, y = ctx.saved_tensors
         map, prec = ctx.args
-        grad = stress_bwd(x, y, float(g), map, prec)
-        return grad, None, None, None
+        # the upstream gradient stays on the device: the kernel's scale
+        # argument is a host double, so it runs at 1 and g is applied after
+        grad = stress_bwd(x, y, 1.0, map, prec)
+        return grad.mul_(g.to(grad.dtype)), None, None, None
 
 
 def stress_loss(x, y, map="lambda", prec="fp32"):

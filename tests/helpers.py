@@ -45,3 +45,35 @@ def stress_moments(x, y):
     rs = n * a + a.sum() - S @ De.sum(0) - De @ S.sum(0)
     rx = np.outer(a, x.sum(0)) + a @ x - S @ (De.T @ x) - De @ (S.T @ x)
     return L, 4 * (x * rs[:, None] - rx)
+
+
+def _pool_map(fn, items):
+    """Runs fn over items on host threads (the oracle's ctypes calls release
+    the GIL, so the FP64 loops run on all host cores)."""
+    import concurrent.futures as cf
+    import os
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        return list(ex.map(fn, items))
+
+
+def fd_grad_atoms(oracle, x, atoms, h=1e-4, nu=1.0, eps=1e-4):
+    """FP64 central differences (x_a +- h e_t) of the oracle's partial energy
+    E_a (the triples holding atom a, O(n^2)), which has the same gradient in
+    x_a as the total energy.  Rows follow `atoms`."""
+    xd = np.asarray(x, dtype=np.float64)
+
+    def one(task):
+        a, t = task
+        xp, xm = xd.copy(), xd.copy()
+        xp[a, t] += h
+        xm[a, t] -= h
+        return (oracle.atm_atom_energy(xp, a, nu, eps) - oracle.atm_atom_energy(xm, a, nu, eps)) / (2 * h)
+
+    tasks = [(int(a), t) for a in atoms for t in range(3)]
+    return np.array(_pool_map(one, tasks)).reshape(len(atoms), 3)
+
+
+def grad_atoms_threads(oracle, x, atoms, nu=1.0, eps=1e-4):
+    """The oracle's analytic gradient rows of `atoms`, one atom per thread."""
+    rows = _pool_map(lambda a: oracle.atm_grad_atoms(x, [int(a)], nu, eps)[0], list(atoms))
+    return np.array(rows)

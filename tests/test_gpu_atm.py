@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import synth
-from helpers import rel_err, to_gpu
+from helpers import fd_grad_atoms, grad_atoms_threads, rel_err, to_gpu
 
 pytestmark = pytest.mark.gpu
 E_TOL = 1e-6
@@ -69,28 +69,22 @@ def test_energy_config_n1024(gpu, oracle, mp):
 
 def test_differentiation_config_n4096(gpu, oracle):
     """n = 4096 in a cube of side 20, seed 3: autograd backward (adjoint
-    kernel) on 64 sampled atoms against the oracle's analytic gradient, and
-    on 4 of them against FP64 central differences (h = 1e-4) of the
-    oracle's partial energy."""
+    kernel) on 64 sampled atoms against the oracle's analytic gradient and
+    against FP64 central differences (h = 1e-4) of the oracle's partial
+    energy, all 64 atoms both ways, max relative error <= 1e-4."""
     x = synth.make_points("atm_n4096")
     xt = to_gpu(x).requires_grad_(True)
     E = gpu.atm_energy(xt)
     E.backward()
     g = xt.grad.double().cpu().numpy()
     atoms = synth.sample_indices(64, 4096, seed=3 + 10 ** 6)
-    G = oracle.atm_grad_atoms(x, atoms)
+    G = grad_atoms_threads(oracle, x, atoms)
     err = np.linalg.norm(g[atoms] - G, axis=1) / np.linalg.norm(G, axis=1)
+    fd = fd_grad_atoms(oracle, x, atoms, h=1e-4)
+    err_fd = np.linalg.norm(g[atoms] - fd, axis=1) / np.linalg.norm(fd, axis=1)
+    print(f"n=4096 forces, 64 atoms: max rel err {err.max():.3e} (analytic), {err_fd.max():.3e} (FD)")
     assert err.max() <= F_TOL
-    h = 1e-4
-    xd = x.astype(np.float64)
-    for a in atoms[:4]:
-        fd = np.zeros(3)
-        for t in range(3):
-            xp, xm = xd.copy(), xd.copy()
-            xp[a, t] += h
-            xm[a, t] -= h
-            fd[t] = (oracle.atm_atom_energy(xp, a) - oracle.atm_atom_energy(xm, a)) / (2 * h)
-        assert np.linalg.norm(g[a] - fd) / np.linalg.norm(fd) <= F_TOL
+    assert err_fd.max() <= F_TOL
     # the three maps give the same energy (no oracle run of 1.1e10 triples)
     e = [energy(gpu, x, mp) for mp in ("lambda", "bbox", "linear")]
     assert e[1] == pytest.approx(e[0], rel=1e-9) and e[2] == pytest.approx(e[0], rel=1e-9)
@@ -116,11 +110,19 @@ def test_properties_full_size(gpu):
 
 def test_scale_config_n16384(gpu, oracle):
     """n = 16384 (7.33e11 triples), seed 6: forces on 8 sampled atoms against
-    the oracle, energy equal across lambda and bounding box."""
+    the oracle's analytic gradient and on 4 of them against FP64 central
+    differences (h = 1e-4) of the partial energy; energy equal across lambda
+    and bounding box."""
     x = synth.make_points("atm_n16384")
     F, E = gpu.atm_forces(to_gpu(x), 1.0, 1e-4, "lambda")
+    F = F.cpu().numpy()
     atoms = synth.sample_indices(8, 16384, seed=6 + 10 ** 6)
-    G = oracle.atm_grad_atoms(x, atoms)
-    assert atom_err(F.cpu().numpy()[atoms], G).max() <= F_TOL
+    G = grad_atoms_threads(oracle, x, atoms)
+    err = atom_err(F[atoms], G)
+    fd = fd_grad_atoms(oracle, x, atoms[:4], h=1e-4)
+    err_fd = atom_err(F[atoms[:4]], fd)
+    print(f"n=16384 forces: max rel err {err.max():.3e} (analytic, 8 atoms), {err_fd.max():.3e} (FD, 4 atoms)")
+    assert err.max() <= F_TOL
+    assert err_fd.max() <= F_TOL
     e_bb = energy(gpu, x, "bbox")
     assert e_bb == pytest.approx(E.item(), rel=1e-6)

@@ -17,26 +17,6 @@ def row_err(g, G):
     return np.linalg.norm(g - G, axis=1) / np.linalg.norm(G, axis=1)
 
 
-def loss_bound(x, y):
-    """Error bound of the FP32 loss from its arithmetic: each residual
-    r_ij = sum_t (S_it - S_jt)(Delta_it - Delta_jt), S = x + y, Delta = x - y,
-    carries at most eps_ij = (d + 3) u sum_t (|S_i|+|S_j|)(|Delta_i|+|Delta_j|)
-    (u = 2^-24: one rounding per staged value, difference, product and sum);
-    the loss then moves by at most sum_{i<j} 2 |r_ij| eps_ij + eps_ij^2, plus
-    u L for the FP32 squares and per-tile sums.  Where r is not small against
-    the staged values this is far below 1e-5 L; the tolerance is the larger."""
-    x = x.astype(np.float64)
-    y = y.astype(np.float64)
-    n, d = x.shape
-    S, De = np.abs(x + y), np.abs(x - y)
-    u = 2.0 ** -24
-    i, j = np.tril_indices(n, -1)
-    eps = (d + 3) * u * ((S[i] + S[j]) * (De[i] + De[j])).sum(axis=1)
-    r = ((x[i] - x[j]) ** 2).sum(1) - ((y[i] - y[j]) ** 2).sum(1)
-    L = (r * r).sum()
-    return (2 * np.abs(r) * eps + eps * eps).sum() + 4 * u * L
-
-
 @pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("n,d", [(2, 1), (33, 3), (100, 8), (257, 64), (700, 33)])
 def test_stress_small(gpu, oracle, mp, n, d):
@@ -45,7 +25,9 @@ def test_stress_small(gpu, oracle, mp, n, d):
     xt, yt = to_gpu(x), to_gpu(y)
     loss, D = gpu.stress_fwd(xt, yt, mp, store_d=True)
     ref = oracle.stress_loss(x, y)
-    assert abs(loss.item() - ref) <= max(L_TOL * ref, loss_bound(x, y))
+    err = abs(loss.item() - ref) / ref
+    print(f"stress loss {mp} n={n} d={d}: rel err {err:.2e}")
+    assert err <= L_TOL
     ref_D = oracle.edm_packed(x)
     off = ref_D > 0
     assert rel_err(D.cpu().numpy()[off], ref_D[off]).max() <= 1e-5
@@ -220,8 +202,9 @@ def test_stress_fwd_bwd_one_pass(gpu, oracle, mp, prec, n, d):
     if n == 1:
         assert loss.item() == 0.0 and bool((g == 0).all())
         return
-    tol = TC_L_TOL * ref if prec == "bf16x3" else max(L_TOL * ref, loss_bound(x, y))
-    assert abs(loss.item() - ref) <= tol
+    err = abs(loss.item() - ref) / ref
+    print(f"stress fwd_bwd loss {mp} {prec} n={n} d={d}: rel err {err:.2e}")
+    assert err <= (TC_L_TOL if prec == "bf16x3" else L_TOL)
     G = 2.5 * oracle.stress_grad_rows(x, y, range(n))
     gd = g.double().cpu().numpy()
     assert row_err(gd, G).max() <= (TC_G_TOL if prec == "bf16x3" else G_TOL)

@@ -467,6 +467,36 @@ def test_atm_bruteforce_law_of_cosines(oracle):
     assert oracle.atm_energy(x, 1.0, 0.0) == pytest.approx(tot, rel=1e-11)
 
 
+def test_atm_abs_energy(oracle):
+    """Sum of |e| over the triples: on one triangle it is |E| of the closed
+    forms (equilateral e > 0, collinear e < 0); on a cloud it matches a
+    pure-Python brute force of sum |e| with law-of-cosines cosines at
+    eps = 0, exceeds |E| when the terms have both signs, and equals E on a
+    set whose terms are all positive (acute triangles only: a regular
+    tetrahedron)."""
+    L, a = 1.3, 0.9
+    tri = np.array([[0, 0, 0], [L, 0, 0], [L / 2, L * math.sqrt(3) / 2, 0]])
+    line = np.array([[0, 0, 0], [0, a, 0], [0, 2 * a, 0]])
+    assert oracle.atm_abs_energy(tri, 1.0, 0.0) == pytest.approx(11 / (8 * L ** 9), rel=1e-13)
+    assert oracle.atm_abs_energy(line, 1.0, 0.0) == pytest.approx(1 / (4 * a ** 9), rel=1e-12)
+    x = synth.uniform_cube(9, 3, 2.0, seed=5).astype(np.float64)
+    tot, signs = 0.0, set()
+    for i, j, k in itertools.combinations(range(9), 3):
+        rij = math.dist(x[i], x[j]); rjk = math.dist(x[j], x[k]); rki = math.dist(x[k], x[i])
+        ci = (rij ** 2 + rki ** 2 - rjk ** 2) / (2 * rij * rki)
+        cj = (rij ** 2 + rjk ** 2 - rki ** 2) / (2 * rij * rjk)
+        ck = (rjk ** 2 + rki ** 2 - rij ** 2) / (2 * rjk * rki)
+        e = (1 + 3 * ci * cj * ck) / (rij * rjk * rki) ** 3
+        signs.add(e > 0)
+        tot += abs(e)
+    assert signs == {True, False}
+    A = oracle.atm_abs_energy(x, 1.0, 0.0)
+    assert A == pytest.approx(tot, rel=1e-11)
+    assert A > abs(oracle.atm_energy(x, 1.0, 0.0)) * (1 + 1e-9)
+    tet = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], np.float64)
+    assert oracle.atm_abs_energy(tet, 0.5, 1e-3) == pytest.approx(oracle.atm_energy(tet, 0.5, 1e-3), rel=1e-14)
+
+
 def random_rotation(seed):
     q, r = np.linalg.qr(synth.normal(3, 3, seed=seed).astype(np.float64))
     return q * np.sign(np.diag(r))
