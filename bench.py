@@ -380,6 +380,35 @@ def row_edm_n65536_d64(torch, sx, peaks):
     r = _edm_big(torch, sx, peaks, x, "bf16x3", out=o)
     sx.simplex_edm_packed(x, o, "lambda", "bf16x3", sx.workspace("edm", x.shape[0], x.shape[1], "lambda", "bf16x3"))
     r["error_lambda"] = _edm_error(torch, o, xh, seed=22)
+    del o
+    torch.cuda.empty_cache()
+    r["tiles"] = _edm_tiles(torch, sx, peaks, x)
+    return r
+
+
+def _edm_tiles(torch, sx, peaks, x, prec="bf16x3", maps=("lambda", "bbox", "rb")):
+    """The tile-packed layout (simplex_edm_tiles: each 128 x 128 tile one
+    contiguous 64 KB block, written by TMA tensor stores of 4 KB boxes).
+    Rates count the n(n+1)/2 pairs; the HBM figure counts the bytes the call
+    writes (the whole diagonal tiles and the padding: 0.2% more than the
+    packed rows at n = 65536)."""
+    n, d = x.shape
+    o = torch.empty(sx.simplex_edm_tiles_len(n), device="cuda")
+    pairs = n * (n + 1) // 2
+    ws = {mp: sx.workspace("edm", n, d, mp, prec) for mp in maps}
+    r = {"unit": "pairs/s", "pairs": pairs, "bytes_written": 4 * o.numel(), "prec": prec}
+    for mp in maps:
+        ms = _kernel_ms(torch, sx, lambda: sx.simplex_edm_tiles(x, o, mp, prec, ws[mp]))
+        r[mp] = pairs / (ms / 1e3)
+        r[mp + "_ms"] = ms
+    r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    if "rb" in r:
+        r["lambda_vs_rb"] = r["lambda"] / r["rb"]
+    t = r["lambda_ms"] / 1e3
+    r["hbm_gbs_lambda"] = 4.0 * o.numel() / t / 1e9
+    r["hbm_frac_lambda"] = r["hbm_gbs_lambda"] / peaks["hbm_gbs"]
+    sx.simplex_device_errors()
+    del o
     return r
 
 
@@ -387,7 +416,9 @@ def row_edm_n16384_d64(torch, sx, peaks):
     """EDM n=16384, d=64 on tensor cores (134M outputs, 537 MB): a smaller
     case of the same kernel, sized for profiler captures."""
     x = torch.from_numpy(synth.normal(16384, 64, seed=4)).cuda()
-    return _edm_big(torch, sx, peaks, x, "bf16x3")
+    r = _edm_big(torch, sx, peaks, x, "bf16x3")
+    r["tiles"] = _edm_tiles(torch, sx, peaks, x)
+    return r
 
 
 def row_edm_n16384_d256(torch, sx, peaks):

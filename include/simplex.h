@@ -85,7 +85,8 @@ typedef enum {
 
 /* ABI version of this header (bumped on any signature change or added entry
  * point or map; 2 added simplex_stress_fwd_bwd, 3 SIMPLEX_MAP_RB, 4
- * simplex_map4 and the m = 4 tables). */
+ * simplex_map4 and the m = 4 tables, 5 simplex_edm_tiles and
+ * simplex_edm_tiles_len). */
 int simplex_abi_version(void);
 
 /* Human-readable text of a status code (static storage). */
@@ -197,6 +198,38 @@ int simplex_map4(int64_t n, int rho, int map, int32_t *count, int64_t *idle,
  */
 int simplex_edm_packed(int64_t n, int64_t d, const float *x, float *out, int map,
                        int prec, void *workspace, int64_t ws_bytes, void *stream);
+
+/*
+ * The same squared distances in a tile-packed layout, where every 128 x 128
+ * tile of the matrix is one contiguous block of 64 KB.  Sec. II cites the
+ * rectangular-box (RB) packing of a triangular matrix into whole rectangles;
+ * this is that idea on the data side, at tile granularity: the triangle of
+ * tiles is stored without gaps, each tile a dense rectangle, so a kernel
+ * writes a tile (or a 32-row quarter of it, 16 KB) with a few large copies
+ * instead of one copy per row segment of the row-major packing.
+ * Layout: nt = ceil(n / 128) tile rows; tile (I, J), 0 <= J <= I < nt, holds
+ * rows 128 I .. 128 I + 127 and columns 128 J .. 128 J + 127, stored row-major
+ * at floats [s * 16384, (s + 1) * 16384) with s = I(I+1)/2 + J (the tiles in
+ * packed lower order, the same for every map).  So pair (i, j), j <= i, is at
+ *   ((i/128)(i/128 + 1)/2 + j/128) * 16384 + (i mod 128) * 128 + (j mod 128).
+ * A diagonal tile (I = J) holds the whole square: its entry (a, b) with b > a
+ * is |x_i - x_j|^2 for (i, j) = (128 I + a, 128 I + b), formed the same way as
+ * the lower entries (so equal to its mirror within the stated tolerance);
+ * the diagonal is exactly 0.  Entries whose row or column is >= n (the
+ * padding of the last tile row when n is not a multiple of 128) are 0.
+ * out: device, simplex_edm_tiles_len(n) FP32 (nt(nt+1)/2 * 16384 floats,
+ * 0.2% more than n(n+1)/2 at n = 65536), every float written by the call;
+ * 16-byte aligned on the tensor-core path (its tiles leave by TMA tensor
+ * stores; SIMPLEX_EALIGN otherwise), 4-byte aligned on the FP32 path.  The
+ * other arguments, precisions, workspace and errors are those of
+ * simplex_edm_packed; SIMPLEX_EOVERFLOW also when nt(nt+1)/2 >= 2^31.
+ */
+int simplex_edm_tiles(int64_t n, int64_t d, const float *x, float *out, int map,
+                      int prec, void *workspace, int64_t ws_bytes, void *stream);
+
+/* Floats of the tile-packed EDM of n points, nt(nt+1)/2 * 16384 with
+ * nt = ceil(n / 128); -1 when n < 1 or n > 2^31. */
+int64_t simplex_edm_tiles_len(int64_t n);
 
 /*
  * Axilrod-Teller-Muto triple-dipole energy over the 3-simplex (Sec. I:

@@ -22,6 +22,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle.py``):
   idle counts.
 * ``edm_packed`` / ``edm_pairs``: pinned by closed forms on a line and a
   lattice, scaling, translation and permutation invariance.
+* ``edm_tiles``: pinned by points on a line, where each entry's value
+  (i - j)^2 names its pair: the tiles, walked in the triangle's order by
+  nested loops, equal the blocks of the full square matrix; padding 0.
 * ``atm_energy`` / ``atm_atom_energy`` / ``atm_grad`` / ``atm_grad_atoms``:
   pinned by closed-form triangles (equilateral, collinear, right angle), a
   pure-Python brute force using angles, invariances, Euler's theorem for a
@@ -80,6 +83,7 @@ def lib():
             "oracle_volume4": (_i64, [_i64]),
             "oracle_cover4": (_i64, [_i64, _i64, ctypes.c_int, _i32p]),
             "oracle_edm_packed": (None, [_i64, _i64, _dp, _dp]),
+            "oracle_edm_tiles": (None, [_i64, _i64, _dp, _dp]),
             "oracle_edm_pairs": (None, [_i64, _dp, _i64p, _i64, _dp]),
             "oracle_atm_energy": (_d, [_i64, _dp, _d, _d]),
             "oracle_atm_energy_slice": (_d, [_i64, _dp, _d, _d, _i64, _i64]),
@@ -189,6 +193,17 @@ def edm_packed(x: np.ndarray) -> np.ndarray:
     n, d = x.shape
     out = np.empty(n * (n + 1) // 2, dtype=np.float64)
     lib().oracle_edm_packed(n, d, _p(x, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
+
+
+def edm_tiles(x: np.ndarray) -> np.ndarray:
+    """Tile-packed EDM: tiles (I, J), J <= I, of 128 x 128 in packed lower
+    order, each row-major; diagonal tiles whole, padding 0."""
+    x = _f64(x)
+    n, d = x.shape
+    nt = (n + 127) // 128
+    out = np.empty(nt * (nt + 1) // 2 * 128 * 128, dtype=np.float64)
+    lib().oracle_edm_tiles(n, d, _p(x, ctypes.c_double), _p(out, ctypes.c_double))
     return out
 
 

@@ -515,6 +515,28 @@ void oracle_edm_packed(int64_t n, int64_t d, const double *x, double *out)
             out[i * (i + 1) / 2 + j] = sqdist(x + i * d, x + j * d, d);
 }
 
+/*
+ * The same distances in the tile-packed layout (each 128 x 128 tile of the
+ * matrix one contiguous block; the data-side counterpart of the RB packing of
+ * Sec. II).  Tiles (I, J), J <= I, follow one another in packed lower order;
+ * inside a tile, row a and column b are at a * 128 + b.  A diagonal tile
+ * holds its whole square, and rows or columns >= n are 0.
+ */
+void oracle_edm_tiles(int64_t n, int64_t d, const double *x, double *out)
+{
+    const int64_t T = 128, nt = (n + T - 1) / T;
+    double *tile = out;
+    for (int64_t I = 0; I < nt; ++I)
+        for (int64_t J = 0; J <= I; ++J) {
+            for (int64_t a = 0; a < T; ++a)
+                for (int64_t b = 0; b < T; ++b) {
+                    int64_t i = I * T + a, j = J * T + b;
+                    tile[a * T + b] = (i < n && j < n) ? sqdist(x + i * d, x + j * d, d) : 0.0;
+                }
+            tile += T * T;
+        }
+}
+
 /* Squared distances of the listed pairs (i, j). */
 void oracle_edm_pairs(int64_t d, const double *x, const int64_t *pairs,
                       int64_t count, double *out)

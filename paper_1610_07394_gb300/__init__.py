@@ -37,7 +37,7 @@ EXPORTS = [
     "simplex_map3", "simplex_map4", "simplex_edm_packed", "simplex_atm_energy", "simplex_atm_forces",
     "simplex_stress_fwd", "simplex_stress_bwd", "simplex_workspace_bytes", "simplex_profile",
     "simplex_profile_read", "simplex_atm_energy_noalloc", "simplex_device_errors",
-    "simplex_stress_fwd_bwd",
+    "simplex_stress_fwd_bwd", "simplex_edm_tiles", "simplex_edm_tiles_len",
 ]
 
 
@@ -66,6 +66,8 @@ def _signatures(L):
         "simplex_map3": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp]),
         "simplex_map4": (_i32, [_i64, _i32, _i32, _vp, _vp, _vp]),
         "simplex_edm_packed": (_i32, [_i64, _i64, _vp, _vp, _i32, _i32, _vp, _i64, _vp]),
+        "simplex_edm_tiles": (_i32, [_i64, _i64, _vp, _vp, _i32, _i32, _vp, _i64, _vp]),
+        "simplex_edm_tiles_len": (_i64, [_i64]),
         "simplex_atm_energy": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _i32, _vp, _i64, _vp]),
         "simplex_atm_forces": (_i32, [_i64, _i64, _vp, _f32, _f32, _vp, _vp, _i32, _vp, _i64, _vp]),
         "simplex_stress_fwd": (_i32, [_i64, _i64, _vp, _vp, _vp, _vp, _i32, _i32, _vp, _i64, _vp]),
@@ -184,6 +186,18 @@ def simplex_edm_packed(x, out, map="lambda", prec="fp32", workspace=None, stream
     _check("simplex_edm_packed", lib().simplex_edm_packed(
         n, d, _cuda(x, torch.float32, "x"), _cuda(out, torch.float32, "out"), _map(map),
         _prec(prec), ws, 0 if workspace is None else workspace.numel(), _stream(stream)))
+
+
+def simplex_edm_tiles(x, out, map="lambda", prec="fp32", workspace=None, stream=None):
+    n, d = x.shape
+    ws = _ptr_or_null(workspace, torch.uint8, "workspace")
+    _check("simplex_edm_tiles", lib().simplex_edm_tiles(
+        n, d, _cuda(x, torch.float32, "x"), _cuda(out, torch.float32, "out"), _map(map),
+        _prec(prec), ws, 0 if workspace is None else workspace.numel(), _stream(stream)))
+
+
+def simplex_edm_tiles_len(n: int) -> int:
+    return lib().simplex_edm_tiles_len(n)
 
 
 def simplex_atm_energy(x, nu, eps, energy, map="lambda", workspace=None, stream=None):
@@ -306,6 +320,16 @@ def edm_packed(x: torch.Tensor, map="lambda", prec="fp32") -> torch.Tensor:
     n, d = x.shape
     out = torch.empty(n * (n + 1) // 2, dtype=torch.float32, device=x.device)
     simplex_edm_packed(x, out, map, prec, workspace("edm", n, d, map, prec))
+    return out
+
+
+def edm_tiles(x: torch.Tensor, map="lambda", prec="fp32") -> torch.Tensor:
+    """Tile-packed EDM of squared distances: simplex_edm_tiles_len(n) FP32,
+    tile (I, J) of 128 x 128 at floats [s * 16384, (s + 1) * 16384),
+    s = I(I+1)/2 + J."""
+    n, d = x.shape
+    out = torch.empty(simplex_edm_tiles_len(n), dtype=torch.float32, device=x.device)
+    simplex_edm_tiles(x, out, map, prec, workspace("edm", n, d, map, prec))
     return out
 
 

@@ -105,7 +105,7 @@ int reduce_partials(const double *partials, int64_t count, double *tmp, double *
 
 using namespace sx;
 
-extern "C" int simplex_abi_version(void) { return 4; }
+extern "C" int simplex_abi_version(void) { return 5; }
 
 extern "C" int simplex_profile(int on) {
     std::lock_guard<std::mutex> lk(g_prof.mu);

@@ -31,6 +31,7 @@
 // Every mbarrier wait is bounded in time; a wait that runs out sets a device
 // error flag (simplex_device_errors) and the block stops instead of hanging.
 #include <cstddef>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -145,9 +146,10 @@ constexpr int PSMEM2_BYTES = 1024 + kStages * PSTAGE + kStageBytes + kCtlBytes;
 static_assert(PSMEM2_BYTES <= 227 * 1024, "shared memory per block");
 constexpr uint32_t kIdesc256 = idesc_bf16(TM, 2 * TN, false, false);
 
-template <int MAP>
+template <int MAP, bool TILES>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant__ CUtensorMap map_hi,
                                                           const __grid_constant__ CUtensorMap map_lo,
+                                                          const __grid_constant__ CUtensorMap map_out,
                                                           const float *__restrict__ x,
                                                           const float *__restrict__ nrm,
                                                           float *__restrict__ out, int64_t n, int d,
@@ -259,6 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         const int r = 32 * quarter + lane;       // this thread's row in the step
         float *stg = stg_all + quarter * kQuarterFloats;   // shared with the other half's warp
         float *nc = &ctl.ncol[ew][0];            // this warp's 64 column norms
+        // tile-packed output: this warp's two 32 x 32 boxes (its 64 columns of
+        // rows 32 quarter .. +31 of a tile), 128-byte swizzle, 1024-byte aligned
+        unsigned char *boxes = reinterpret_cast<unsigned char *>(stg_all) + (quarter * 2 + half) * 8192;
+        bool inflight = false;
         SuperWalk<MAP> walk(gx, total, nb2);
         int sX, sY;
         uint32_t tt = 0, st = 0;   // steps, and half-steps staged and written
@@ -337,6 +343,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                         const float sj = ni + nc[q];
                         if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
                     }
+                }
+                if constexpr (TILES) {
+                    // the whole tile, padding and diagonal masked, as two boxes
+                    // of the tile-packed output (TMA tensor stores)
+                    if (row0 + TM > n || col0 + TN > n || diag) {
+#pragma unroll
+                        for (int q = 0; q < 64; ++q) {
+                            float &vq = q < 32 ? v0[q] : v1[q - 32];
+                            const int64_t j = col0 + 64 * half + q;
+                            if (i >= n || j >= n || i == j) vq = 0.0f;
+                        }
+                    }
+                    if (inflight) {
+                        if (lane == 0) bulk_wait_read();
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        *reinterpret_cast<float4 *>(boxes + box_chunk_off(lane, c)) =
+                            make_float4(v0[4 * c], v0[4 * c + 1], v0[4 * c + 2], v0[4 * c + 3]);
+                        *reinterpret_cast<float4 *>(boxes + 4096 + box_chunk_off(lane, c)) =
+                            make_float4(v1[4 * c], v1[4 * c + 1], v1[4 * c + 2], v1[4 * c + 3]);
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        const int slot = (int)((int64_t)Y * (Y + 1) / 2 + X);
+                        tma_store_3d(&map_out, smem_u32(boxes), 64 * half, 32 * quarter, slot);
+                        tma_store_3d(&map_out, smem_u32(boxes + 4096), 64 * half + 32, 32 * quarter, slot);
+                        bulk_commit();
+                    }
+                    inflight = true;
+                    continue;
                 }
                 // the staging is free once both warps' copies of the previous half-step have read it
                 if (st > 0) {
@@ -477,9 +516,10 @@ struct StepWalk {
     }
 };
 
-template <int MAP>
+template <int MAP, bool TILES>
 __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_constant__ CUtensorMap map_hi,
                                                                const __grid_constant__ CUtensorMap map_lo,
+                                                               const __grid_constant__ CUtensorMap map_out,
                                                                const float *__restrict__ x,
                                                                const float *__restrict__ nrm,
                                                                float *__restrict__ out, int64_t n, int d,
@@ -582,6 +622,128 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
                     if (ok) mma_commit(smem_u32(&ctl.tfull[acc]));
                 }
             }
+        }
+    } else if constexpr (TILES) {
+        // ---------------- epilogue, tile-packed output: warp (quarter, h) owns
+        // rows 32 quarter .. +31 of the step's tile h, one contiguous 16 KB
+        // block of the output; it stages them as four 32 x 32 boxes in the
+        // 128-byte swizzle (conflict-free: lane = row) and writes each with a
+        // TMA tensor store as soon as it is staged (one bulk group per box),
+        // so that a box waits only for its own previous store to have read it
+        // and three boxes stay in flight while the fourth is written
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int h = ew >> 2;
+        const int r = 32 * quarter + lane;
+        unsigned char *boxes = reinterpret_cast<unsigned char *>(stg_all) + ew * 16384;
+        const uint32_t sbox = smem_u32(boxes);
+        float *nc = &ctl.ncol[ew][0];
+        StepWalk<MAP> walk(gx, total, nb2, nb);
+        int X0, Y;
+        uint32_t tt = 0;
+        auto load_step = [&](int X0s, int Ys, float (&cn)[4], float &rn) {
+            const int64_t cb = (int64_t)X0s * TN + TN * h + lane, ii = (int64_t)Ys * TM + r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cn[q] = cb + 32 * q < n ? __ldg(nrm + cb + 32 * q) : 0.0f;
+            rn = ii < n ? __ldg(nrm + ii) : 0.0f;
+        };
+        bool have = walk.next(X0, Y);
+        float pcn[4] = {0.f, 0.f, 0.f, 0.f}, prn = 0.f;
+        if (have) load_step(X0, Y, pcn, prn);
+        while (have && !*fail) {
+            int X0n, Yn;
+            const bool hn = walk.next(X0n, Yn);
+            float ncn[4] = {0.f, 0.f, 0.f, 0.f}, nrn = 0.f;
+            if (hn) load_step(X0n, Yn, ncn, nrn);
+            const uint32_t acc = (tt + h) & 3, use = (tt + h) >> 2;
+            const int X = X0 + h;
+            const bool valid = X <= Y;             // X < nb follows from Y < nb
+            const int64_t row0 = (int64_t)Y * TM, colh = (int64_t)X * TN;
+            __syncwarp();   // the previous step's reads of nc are done
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nc[32 * q + lane] = pcn[q];
+            const int64_t i = row0 + r;
+            const float ni = prn;
+            __syncwarp();
+            if (!mbar_wait(smem_u32(&ctl.tfull[acc]), use & 1, fail, &g_error)) break;
+            tc_fence_after();
+            if (valid) {
+                // padding rows / columns (last tile row) and the diagonal are masked
+                const bool mask = row0 + TM > n || colh + TN > n || X == Y;
+#pragma unroll 1
+                for (int part = 0; part < 2; ++part) {
+                    float v0[32], v1[32];
+                    tmem_ld64(tmem + acc * TN + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(64 * part), v0, v1);
+                    const float *ncp = nc + 64 * part;
+                    float lows[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(ncp + q);
+                        const float4 b = *reinterpret_cast<const float4 *>(ncp + 32 + q);
+                        const float sa[4] = {ni + a.x, ni + a.y, ni + a.z, ni + a.w};
+                        const float sb[4] = {ni + b.x, ni + b.y, ni + b.z, ni + b.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            v0[q + k] = fmaf(-2.0f, v0[q + k], sa[k]);
+                            v1[q + k] = fmaf(-2.0f, v1[q + k], sb[k]);
+                            lows[k] = fminf(lows[k], fminf(fmaf(-0.015625f, sa[k], v0[q + k]),
+                                                           fmaf(-0.015625f, sb[k], v1[q + k])));
+                        }
+                    }
+                    const float low = fminf(fminf(lows[0], lows[1]), fminf(lows[2], lows[3]));
+                    if (__any_sync(0xffffffffu, low < 0.0f)) {
+#pragma unroll
+                        for (int q = 0; q < 64; ++q) {
+                            float &vq = q < 32 ? v0[q] : v1[q - 32];
+                            const int64_t j = colh + 64 * part + q;
+                            const float sj = ni + ncp[q];
+                            if (vq < 0.015625f * sj && i < n && j < n && i != j) vq = exact_sqdist(x, i, j, d);
+                        }
+                    }
+                    if (mask) {
+#pragma unroll
+                        for (int q = 0; q < 64; ++q) {
+                            float &vq = q < 32 ? v0[q] : v1[q - 32];
+                            const int64_t j = colh + 64 * part + q;
+                            if (i >= n || j >= n || i == j) vq = 0.0f;
+                        }
+                    }
+                    if (part == 1) {
+                        // the accumulator is read: hand it back to the MMA warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+                    }
+                    const int slot = (int)((int64_t)Y * (Y + 1) / 2 + X);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int b = 2 * part + k;
+                        const float *v = k == 0 ? v0 : v1;
+                        // box b's previous store (four bulk groups ago) has read it
+                        if (lane == 0) bulk_wait_read_le<3>();
+                        __syncwarp();
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            *reinterpret_cast<float4 *>(boxes + b * 4096 + box_chunk_off(lane, c)) =
+                                make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+                        fence_proxy_async();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_3d(&map_out, sbox + b * 4096, 32 * b, 32 * quarter, slot);
+                            bulk_commit();
+                        }
+                    }
+                }
+            } else {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
+            }
+            tt += 2;
+            X0 = X0n; Y = Yn; have = hn;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pcn[q] = ncn[q];
+            prn = nrn;
         }
     } else {
         // ---------------- epilogue: 8 warps; warp (quarter, h) reads TMEM lanes
@@ -729,6 +891,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
 
 }  // namespace wide
 
+template <bool TILES>
+static cudaError_t optin_layout() {
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA, TILES>, a, PSMEM2_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX, TILES>, a, PSMEM2_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR, TILES>, a, PSMEM2_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_edm_umma<MAP_RB, TILES>, a, PSMEM2_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LAMBDA, TILES>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_BBOX, TILES>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LINEAR, TILES>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_RB, TILES>, a, wide::WSMEM_BYTES)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
 static int smem_optin() {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -738,15 +916,7 @@ static int smem_optin() {
     if (dev < 0 || dev >= 64) return SIMPLEX_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(mu);
     if (!done[dev]) {
-        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        if ((e = cudaFuncSetAttribute(k_edm_umma<MAP_LAMBDA>, a, PSMEM2_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_BBOX>, a, PSMEM2_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_LINEAR>, a, PSMEM2_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edm_umma<MAP_RB>, a, PSMEM2_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LAMBDA>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_BBOX>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_LINEAR>, a, wide::WSMEM_BYTES)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(wide::k_edm_umma_wide<MAP_RB>, a, wide::WSMEM_BYTES)) != cudaSuccess)
+        if ((e = optin_layout<false>()) != cudaSuccess || (e = optin_layout<true>()) != cudaSuccess)
             return cuda_status(e);
         done[dev] = true;
     }
@@ -779,7 +949,7 @@ static int64_t max_pairs(int sms) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int num = 0;
-        if (cudaOccupancyMaxActiveClusters(&num, k_edm_umma<MAP_LAMBDA>, &cfg) != cudaSuccess || num < 1) {
+        if (cudaOccupancyMaxActiveClusters(&num, k_edm_umma<MAP_LAMBDA, false>, &cfg) != cudaSuccess || num < 1) {
             cudaGetLastError();
             num = sms / 2;
         }
@@ -796,15 +966,52 @@ int64_t edm_umma_workspace_bytes(int64_t n, int64_t d) {
     return 1024 + 2 * umma::align_up(n * d * 2, 1024) + umma::align_up(n * 4, 1024);
 }
 
-int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void *ws,
+namespace umma {
+
+// One launch of the d < 128 kernel (one CTA per SM) for a map and layout.
+template <bool TILES>
+static void launch_wide(int map, unsigned ctas, cudaStream_t s, const CUtensorMap &mh, const CUtensorMap &ml,
+                        const CUtensorMap &mo, const float *x, const float *nrm, float *out, int64_t n, int d,
+                        int nb, int nb2, int gx, int64_t total) {
+    const int sm = wide::WSMEM_BYTES;
+    if (map == MAP_LAMBDA)
+        wide::k_edm_umma_wide<MAP_LAMBDA, TILES><<<ctas, kThreads, sm, s>>>(mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+    else if (map == MAP_BBOX)
+        wide::k_edm_umma_wide<MAP_BBOX, TILES><<<ctas, kThreads, sm, s>>>(mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+    else if (map == MAP_RB)
+        wide::k_edm_umma_wide<MAP_RB, TILES><<<ctas, kThreads, sm, s>>>(mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+    else
+        wide::k_edm_umma_wide<MAP_LINEAR, TILES><<<ctas, kThreads, sm, s>>>(mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+}
+
+// One launch of the d >= 128 kernel (two-CTA clusters) for a map and layout.
+template <bool TILES>
+static cudaError_t launch_pairs(int map, const cudaLaunchConfig_t &cfg, const CUtensorMap &mh,
+                                const CUtensorMap &ml, const CUtensorMap &mo, const float *x,
+                                const float *nrm, float *out, int64_t n, int d, int nb, int nb2, int gx,
+                                int64_t total) {
+    if (map == MAP_LAMBDA)
+        return cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LAMBDA, TILES>, mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+    if (map == MAP_BBOX)
+        return cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_BBOX, TILES>, mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+    if (map == MAP_RB)
+        return cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_RB, TILES>, mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+    return cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LINEAR, TILES>, mh, ml, mo, x, nrm, out, n, d, nb, nb2, gx, total);
+}
+
+}  // namespace umma
+
+int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, bool tiles, void *ws,
                  int64_t ws_bytes, cudaStream_t s) {
     using namespace umma;
     if (d % KC != 0) return SIMPLEX_EUNSUPPORTED;
     if (!ws || ws_bytes < edm_umma_workspace_bytes(n, d) || !aligned(ws, 256))
         return SIMPLEX_EWORKSPACE;
+    if (tiles && !aligned(out, 16)) return SIMPLEX_EALIGN;   // TMA tensor stores
     const int64_t nb = (n + TM - 1) / TM;
     const Grid g = grid2(nb, map);
     if (!grid_fits(g)) return SIMPLEX_EOVERFLOW;
+    if (tiles && nb * (nb + 1) / 2 > INT32_MAX) return SIMPLEX_EOVERFLOW;   // tile coordinate of a store
     unsigned char *w = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
     __nv_bfloat16 *xh = reinterpret_cast<__nv_bfloat16 *>(w);
@@ -812,11 +1019,13 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
     float *nrm = reinterpret_cast<float *>(w + 2 * align_up(n * d * 2, 1024));
     // 128-byte swizzle, K boxes of 64 for the d < 128 kernel; 64-byte swizzle,
     // K boxes of 32 for the d >= 128 kernel
-    CUtensorMap mh, ml;
+    CUtensorMap mh, ml, mo;
+    std::memset(&mo, 0, sizeof(mo));
     const bool wide_rows = !use_multicast(d);
     if (wide_rows ? (!make_map_bf16(&mh, xh, n, d, d, TM) || !make_map_bf16(&ml, xl, n, d, d, TM))
                   : (!make_map_bf16_sw64(&mh, xh, n, d, d, TM) || !make_map_bf16_sw64(&ml, xl, n, d, d, TM)))
         return SIMPLEX_ECUDA;
+    if (tiles && !make_map_tiles_f32(&mo, out, nb * (nb + 1) / 2)) return SIMPLEX_ECUDA;
     int st = smem_optin();
     if (st) return st;
     k_split_bf16<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(x, n, (int)d, xh, xl, nrm);
@@ -826,28 +1035,19 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
     int dev = 0, sms = 0;
     if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
     if ((st = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return st;
-    if (!use_multicast(d)) {
-        // one CTA per SM over the map's grid of 256 x 256 super-blocks, rows of 256 columns
-        const int64_t nb2 = (nb + 1) / 2;
-        const Grid g2 = grid2(nb2, map);
-        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
-        const int64_t total2 = g2.gx * g2.gy;
+    // the map's grid of 256 x 256 super-blocks
+    const int64_t nb2 = (nb + 1) / 2;
+    const Grid g2 = grid2(nb2, map);
+    if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
+    const int64_t total2 = g2.gx * g2.gy;
+    if (wide_rows) {
+        // one CTA per SM, steps of two horizontally adjacent tiles
         const unsigned ctas = (unsigned)(total2 < sms ? total2 : sms);
         prof_begin(s);
-        if (map == MAP_LAMBDA)
-            wide::k_edm_umma_wide<MAP_LAMBDA><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
-        else if (map == MAP_BBOX)
-            wide::k_edm_umma_wide<MAP_BBOX><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
-        else if (map == MAP_RB)
-            wide::k_edm_umma_wide<MAP_RB><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
-        else
-            wide::k_edm_umma_wide<MAP_LINEAR><<<ctas, kThreads, wide::WSMEM_BYTES, s>>>(mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        if (tiles) launch_wide<true>(map, ctas, s, mh, ml, mo, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        else launch_wide<false>(map, ctas, s, mh, ml, mo, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
     } else {
-        // two-CTA clusters over the map's grid of 256 x 256 super-blocks
-        const int64_t nb2 = (nb + 1) / 2;
-        const Grid g2 = grid2(nb2, map);
-        if (!grid_fits(g2)) return SIMPLEX_EOVERFLOW;
-        const int64_t total2 = g2.gx * g2.gy;
+        // two-CTA clusters
         int64_t clusters = max_pairs(sms);
         if (clusters > total2) clusters = total2;
         cudaLaunchConfig_t cfg = {};
@@ -863,15 +1063,8 @@ int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void
         cfg.attrs = at;
         cfg.numAttrs = 1;
         prof_begin(s);
-        cudaError_t e;
-        if (map == MAP_LAMBDA)
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LAMBDA>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
-        else if (map == MAP_BBOX)
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_BBOX>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
-        else if (map == MAP_RB)
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_RB>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
-        else
-            e = cudaLaunchKernelEx(&cfg, k_edm_umma<MAP_LINEAR>, mh, ml, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
+        const cudaError_t e = tiles ? launch_pairs<true>(map, cfg, mh, ml, mo, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2)
+                                    : launch_pairs<false>(map, cfg, mh, ml, mo, x, nrm, out, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2);
         if (e != cudaSuccess) { prof_end(s); return cuda_status(e); }
     }
     prof_end(s);

@@ -20,7 +20,9 @@ int64_t edm_workspace_bytes(int64_t n, int64_t d, int map, int prec);
 // Tensor-core EDM (edm_umma.cu): tiles of 128 x 128 pairs, d % 64 == 0.
 constexpr int kEdmUmmaRho = 128;
 int64_t edm_umma_workspace_bytes(int64_t n, int64_t d);
-int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, void *ws,
+// tiles: the tile-packed output layout (simplex_edm_tiles) instead of the
+// packed rows (simplex_edm_packed)
+int edm_umma_run(int64_t n, int64_t d, const float *x, float *out, int map, bool tiles, void *ws,
                  int64_t ws_bytes, cudaStream_t s);
 int umma_device_errors(cudaStream_t s);
 

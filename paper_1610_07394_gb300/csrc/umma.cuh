@@ -136,6 +136,15 @@ __device__ __forceinline__ void bulk_store(float *gdst, uint32_t ssrc, uint32_t 
                  : "memory");
 }
 
+// shared -> global TMA tensor store of one box of a 3-D map (bulk group);
+// the box is read from shared memory in the map's swizzle
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t ssrc, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(ssrc)
+                 : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -143,6 +152,13 @@ __device__ __forceinline__ void bulk_commit() {
 // waits until this thread's committed bulk copies have read their sources
 __device__ __forceinline__ void bulk_wait_read() {
     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// waits until at most N of this thread's most recent bulk groups are still
+// reading their shared-memory sources
+template <int N>
+__device__ __forceinline__ void bulk_wait_read_le() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void bulk_wait_all() {
@@ -397,6 +413,29 @@ inline bool make_map_bf16_sw64(CUtensorMap *m, void *ptr, int64_t rows, int64_t 
     return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tile-packed EDM output as a 3-D FP32 tensor [tiles][128 rows][128
+// columns] (base 16-byte aligned), boxes of 32 columns x 32 rows of one tile
+// (4 KB, one 128-byte swizzle row per tile row), 128-byte swizzle.
+inline bool make_map_tiles_f32(CUtensorMap *m, float *out, int64_t tiles) {
+    EncodeTiled f = encode_fn();
+    if (!f) return false;
+    const cuuint64_t dims[3] = {128u, 128u, (cuuint64_t)tiles};
+    const cuuint64_t strides[2] = {128u * 4u, 128u * 128u * 4u};
+    const cuuint32_t box[3] = {32u, 32u, 1u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out, dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Shared-memory byte offset of float4 chunk c (0..7) of row r (0..31) inside a
+// 32 x 32 FP32 box in the 128-byte swizzle (box base 1024-byte aligned): the
+// chunk index is XORed with the row index mod 8, so the 32 lanes of a warp,
+// each writing chunk c of its own row, spread over all 32 banks.
+__host__ __device__ constexpr uint32_t box_chunk_off(int r, int c) {
+    return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
 }
 
 inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }

@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_abi_and_strerror(L):
-    assert sx.simplex_abi_version() == 4
+    assert sx.simplex_abi_version() == 5
     for st in range(7):
         assert L.simplex_strerror(st)
     assert L.simplex_last_cuda_error() == 0
@@ -132,6 +132,10 @@ def test_grid_and_workspace_sizes(L):
     assert sx.simplex_workspace_bytes("stress_fwd_bwd", 1000, 64, "lambda", "bf16x3") == \
         sx.simplex_workspace_bytes("stress_bwd", 1000, 64, "lambda", "bf16x3") > 0
     assert sx.simplex_workspace_bytes("atm_energy", 0, 3) == -1
+    # tile-packed EDM: nt(nt+1)/2 tiles of 128 x 128, nt = ceil(n / 128)
+    assert [sx.simplex_edm_tiles_len(n) for n in (1, 128, 129, 256, 65536)] == \
+        [16384, 16384, 3 * 16384, 3 * 16384, 512 * 513 // 2 * 16384]
+    assert sx.simplex_edm_tiles_len(0) == -1 and sx.simplex_edm_tiles_len((1 << 31) + 1) == -1
 
 
 def test_validation_before_gpu_work(L):
@@ -164,6 +168,11 @@ def test_validation_before_gpu_work(L):
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, null, 16, 0, 0, null, 0, null) == 1  # NULL grad
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, 12, 0, 0, null, 0, null) == 2    # loss not 8B
     assert L.simplex_stress_fwd_bwd(8, 4, 16, 16, 1.0, 16, 16, 0, 0, null, 0, null) == 6    # no workspace
+    assert L.simplex_edm_tiles(0, 3, 16, 16, 0, 0, null, 0, null) == 1           # n < 1
+    assert L.simplex_edm_tiles(4, 3, 16, 16, 4, 0, null, 0, null) == 1           # bad map
+    assert L.simplex_edm_tiles((1 << 31) + 1, 3, 16, 16, 0, 0, null, 0, null) == 3   # n > 2^31
+    assert L.simplex_edm_tiles(8, 64, 16, 16, 0, 1, null, 0, null) == 6          # no workspace
+    assert L.simplex_edm_tiles(8, 64, 16, 20, 0, 1, 256, 1 << 20, null) == 2     # TMA stores need 16 B
     assert L.simplex_map_blocks_host(2, 4, 0, null) == 1
     assert L.simplex_map3(10, 4, 3, 16, 16, null) == 1                           # no 3-simplex RB
     assert L.simplex_atm_energy(8, 3, 16, 1.0, 1e-4, 16, 3, 256, 1 << 20, null) == 1  # RB for m = 3

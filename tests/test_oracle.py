@@ -413,6 +413,35 @@ def test_edm_invariances(oracle):
     assert (D[i * (i + 1) // 2 + i] == 0).all()
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 300])
+def test_edm_tiles_layout(oracle, n):
+    """Tile-packed layout on points of a line (x_i = i, so D_ij = (i - j)^2
+    names the pair): walking the tile triangle row by row with nested loops,
+    each 128 x 128 block is the corresponding block of the full square matrix
+    (numpy broadcasting), the padding past n is 0, every float is accounted
+    for, and the lower entries of the tiles are exactly the packed rows."""
+    x = np.zeros((n, 2))
+    x[:, 0] = np.arange(n)
+    T = oracle.edm_tiles(x)
+    nt = -(-n // 128)
+    full = np.zeros((nt * 128, nt * 128))
+    idx = np.arange(n, dtype=np.float64)
+    full[:n, :n] = (idx[:, None] - idx[None, :]) ** 2
+    off, lower = 0, []
+    for I in range(nt):
+        for J in range(I + 1):
+            blk = T[off:off + 128 * 128].reshape(128, 128)
+            assert np.array_equal(blk, full[128 * I:128 * I + 128, 128 * J:128 * J + 128])
+            off += 128 * 128
+    assert off == len(T)
+    # gather the lower triangle back from the tiles, row by row
+    for i in range(n):
+        I = i // 128
+        row = [T[(I * (I + 1) // 2 + j // 128) * 16384 + (i % 128) * 128 + j % 128] for j in range(i + 1)]
+        lower.extend(row)
+    assert np.array_equal(np.array(lower), oracle.edm_packed(x))
+
+
 def test_edm_pairs_matches_packed(oracle):
     x = synth.normal(80, 5, seed=2)
     D = oracle.edm_packed(x)
