@@ -2,17 +2,23 @@
 """Benchmark of the simplex-domain hot path on GB300.
 
 Headline workload (one "step"): the Axilrod-Teller-Muto triple-dipole energy
-over all i < j < k of n = 1024 points uniform in a cube of side 10 (seed 1),
-nu = 1, eps = 1e-4: 178,433,024 triples on the lambda-mapped 3-simplex grid
-(two-branch recursive map plus the J = K plane), FP32 per triple, FP64
-reduction.  Metric: triples per second (whole job), with the same step timed
-for the bounding-box and linear (cube-root) maps, the dominant kernel timed
-live against the FP32 ALU roofline, an end-to-end number through the C ABI
-with host buffers, and the FP64 CPU oracle timed on the host cores.
+and its adjoint forces F = -dE/dx over all i < j < k of n = 16384 points
+uniform in a cube of side 20 (seed 6), nu = 1, eps = 1e-4: 732,873,539,584
+triples on the lambda-mapped 3-simplex grid (two-branch recursive map plus
+the J = K plane), one call of simplex_atm_forces (force tables over the
+2-simplex of blocks, the forces kernel, the FP64 reduction of the energy),
+FP32 per triple, FP64 force and energy sums.  Metric: triples per second
+(whole job), with the same step timed for the bounding-box and linear
+(cube-root) maps, the forces kernel timed live against the FP32 ALU
+roofline, an end-to-end number through the C ABI with host buffers, and the
+FP64 CPU oracle timed on all host cores (a bounded sample, extrapolated).
 
 ``--rows`` (default on at one GPU) also times every other kernel on the path
-at its own configuration (EDM n=1024 d=3, ATM energy+forces n=4096 and
-n=16384, EDM n=32768 d=256, stress loss forward/backward n=65536 d=64).
+at its own configuration (coverage m = 2, 3, 4; EDM n = 1024 d = 3,
+n = 32768 d = 256, n = 65536 d = 64 in both layouts; ATM energy n = 1024,
+energy and forces n = 4096; stress loss forward/backward n = 65536 d = 64;
+and non-powers of two: EDM n = 49152, ATM n = 3000 and n = 12000, coverage
+n = 12000), each row with its own CPU oracle baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -22,9 +28,12 @@ per rank, no data collective; "scaling": "weak").
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -39,15 +48,13 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "pairs/s and triplets/s, λ-map vs bounding-box on 1 GB300; % of HBM/FP32 roofline"
-WORKLOAD = "atm_n1024"
+WORKLOAD = "atm_n16384"
 NU, EPS = 1.0, 1e-4
-# Algorithmic FP32 flops per triple with the pair terms hoisted into tables
-# (edge vectors scaled by r^(3/2), and r^3): three 3-vector dot products
-# (3 x 5), the product of the three (2, the second as an FMA into one
-# accumulator) and r_ik^3 r_jk^3 into the other (1 FMA, 2): 20 flops (r_ij^3
-# and the combination r_ij^3 s0 - 3 s1 once per pair).  With unscaled unit
-# vectors the same energy takes 22 (R^3 and the bracket 1 + 3 cos cos cos
-# separately).
+# Algorithmic FP32 flops per triple of the energy kernel with the pair terms
+# hoisted into tables (edge vectors scaled by r^(3/2), and r^3): three
+# 3-vector dot products (3 x 5), the product of the three (2, the second as
+# an FMA into one accumulator) and r_ik^3 r_jk^3 into the other (1 FMA, 2):
+# 20 flops (r_ij^3 and the combination r_ij^3 s0 - 3 s1 once per pair).
 FLOPS_PER_TRIPLE = 20
 # The same count (an FMA is 2 flops) for a triple of the forces kernel, which
 # forms e and its three derivatives by the squared sides: the three unit-vector
@@ -56,26 +63,19 @@ FLOPS_PER_TRIPLE = 20
 # (1), S = Y - X - Z (2), the three derivatives (15) and their sums into the
 # (i,j), (i,k) and (j,k) accumulators (2.5): 53.5.
 FORCE_FLOPS_PER_TRIPLE = 53.5
-ROWS_NAMES = ("cover2_n16384", "cover3_n1024", "cover4_n256", "edm_n1024_d3", "edm_n32768_d256", "edm_n65536_d64", "atm_n4096", "atm_n16384",
-              "stress_n65536_d64", "edm_n16384_d64", "edm_n16384_d256", "stress_n16384_d64")
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) of one k_atm_energy_tab<lambda> launch on this
-# workload, from the ncu capture summarised in
-# profiles/k_atm_energy_lambda_n1024.md (set to None whenever the kernel
-# changes and the capture has not been repeated).
-ENERGY_KERNEL_DRAM_BYTES = 10.031360e6
 L2_FLUSH_BYTES = 512 << 20
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rows", choices=["auto", "on", "off"], default="auto")
-    ap.add_argument("--row", choices=sorted(ROWS_NAMES), default=None,
-                    help="time only this row (no headline line)")
+    ap.add_argument("--row", default=None, help="time only this row (no headline line)")
     return ap.parse_args()
 
 
@@ -87,6 +87,29 @@ def measured_peaks():
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "sm_max_mhz": 2070.0}, "fallback"
+
+
+def stated_traffic(summary: str):
+    """DRAM bytes (read + write) per launch of a kernel from an ncu summary
+    under profiles/: its line
+      <!-- bench: source=<file> sha256=<hash> traffic_bytes_per_launch=<B> -->
+    names the kernel's source file as captured; the figure is used only while
+    that file is unchanged (else None: the counters predate the kernel)."""
+    path = os.path.join(PROFILES, summary)
+    if not os.path.exists(path):
+        return None, f"{summary}: missing"
+    m = re.search(r"<!-- bench: source=(\S+) sha256=([0-9a-f]+) traffic_bytes_per_launch=([0-9.e+]+)"
+                  r"(?: scale=(\S+))? -->", open(path).read())
+    if not m:
+        return None, f"{summary}: no bench line"
+    src = os.path.join(ROOT, m.group(1))
+    cur = hashlib.sha256(open(src, "rb").read()).hexdigest() if os.path.exists(src) else ""
+    if cur != m.group(2):
+        return None, f"{summary}: {m.group(1)} changed since the capture"
+    note = f"ncu capture summarised in profiles/{summary}"
+    if m.group(4):
+        note += f" ({m.group(4).replace('_', ' ')})"
+    return float(m.group(3)), note
 
 
 class Clocks:
@@ -166,6 +189,11 @@ def triples(n):
     return n * (n - 1) * (n - 2) // 6
 
 
+def row_triples(n, i):
+    """Triples i < j < k < n with the given i."""
+    return (n - 1 - i) * (n - 2 - i) // 2
+
+
 def job_rate(ms_local: float, units_per_rank: int, world: int, dist=None, device=None):
     """Whole-job throughput of independent replicas: every rank processes
     `units_per_rank`; the job's step time is the slowest rank's (MAX
@@ -180,74 +208,115 @@ def job_rate(ms_local: float, units_per_rank: int, world: int, dist=None, device
     return world * units_per_rank / (ms / 1e3), ms
 
 
-# ------------------------------------------------------------------ oracle arm
+# ------------------------------------------------------------------ oracle on the host
 
-def oracle_energy_rate(x, seconds_min=10.0, i_hi=None):
-    """Times the FP64 oracle on this host: the whole sum (i_hi None) or the
-    triples with i < i_hi, repeated until `seconds_min` have passed."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_parallel(fn, tasks, workers):
+    """Runs fn over tasks on `workers` host threads (the oracle's ctypes calls
+    release the GIL); returns (results, wall seconds)."""
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        res = list(ex.map(fn, tasks))
+    return res, time.perf_counter() - t0
+
+
+def oracle_rate(work, tasks, units, workers, kind="oracle"):
+    """Units per second of the FP64 oracle over `tasks` on `workers` threads
+    (one task per thread at a time), and on one thread for the first task."""
+    _, wall = host_parallel(work, tasks, workers)
+    _, one = host_parallel(work, tasks[:1], 1)
+    return {"value": sum(units) / wall, "cores": workers, "kind": kind,
+            "single_core": units[0] / one, "seconds": wall + one}
+
+
+def cpu_atm(x, rows, forces: bool, workers):
+    """The oracle's energy (or energy and gradient) over whole i-rows of the
+    3-simplex: one row per task.  Extrapolates to the full sum by triples."""
     import oracle
     oracle.build()
     n = len(x)
-    if i_hi is None:
-        units = triples(n)
-        run = lambda: oracle.atm_energy(x, NU, EPS)  # noqa: E731
-    else:
-        units = sum((n - 1 - i) * (n - 2 - i) // 2 for i in range(i_hi))
-        run = lambda: oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)  # noqa: E731
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        val = run()
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds_min:
-            break
-    return units * reps / el, units, reps, el, val
+    xd = x.astype(np.float64)
+
+    def work(i):
+        if forces:
+            oracle.atm_energy_grad_slice(xd, i, i + 1, NU, EPS)
+        else:
+            oracle.atm_energy_slice(xd, i, i + 1, NU, EPS)
+
+    units = [row_triples(n, i) for i in rows]
+    r = oracle_rate(work, list(rows), units, workers)
+    what = "energy and gradient" if forces else "energy"
+    r.update({"unit": "triplets/s", "extrapolated": True,
+              "sample": f"FP64 C oracle, {what} of the triples with i in {len(rows)} rows "
+                        f"{rows[0]}..{rows[-1]} ({sum(units)} of {triples(n)} triples), one row per "
+                        f"host thread; rate extrapolated to the whole sum by triple count"})
+    return r
 
 
-def reference_arm(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    x = synth.make_points(WORKLOAD)
+def rows_with(n, target, count):
+    """`count` consecutive i-rows whose triple counts are near `target` each."""
+    i = max(0, min(n - 3, n - 1 - int(math.isqrt(2 * target))))
+    i = min(i, max(0, n - 3 - count))
+    return list(range(i, i + count))
+
+
+def cpu_edm(x, count, workers, seed=90):
+    """The oracle's squared distances of `count` seeded pairs, split over the
+    host threads; extrapolated to the whole triangle by pair count."""
     import oracle
     oracle.build()
     n = len(x)
-    i_hi = 40
-    units = sum((n - 1 - i) * (n - 2 - i) // 2 for i in range(i_hi))
-    for _ in range(args.warmup):
-        oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.atm_energy_slice(x, 0, i_hi, NU, EPS)
-        ts.append(time.perf_counter() - t0)
-    ms = 1e3 * sum(ts) / len(ts)
-    value = units / (ms / 1e3)
-    sample = (f"triples with i < {i_hi} of the n=1024 workload ({units} of {triples(n)}) per step, "
-              "FP64 oracle, 1 thread")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "triplets/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_block(),
-        "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    pr = synth.sample_pairs(count, n, seed)
+    chunks = np.array_split(pr, workers)
+    r = oracle_rate(lambda c: oracle.edm_pairs(x, c), chunks, [len(c) for c in chunks], workers)
+    r.update({"unit": "pairs/s", "extrapolated": True,
+              "sample": f"FP64 C oracle, squared distances of {count} seeded pairs, split over the "
+                        f"host threads; extrapolated to n(n+1)/2 pairs by count"})
+    return r
 
 
-def config_block():
-    w = synth.WORKLOADS[WORKLOAD]
-    return {"workload": f"ATM triple-dipole energy over i<j<k, n={w['n']} uniform in a cube of "
-                        f"side {w['side']:g}, seed {w['seed']}, nu=1, eps=1e-4 ({triples(w['n'])} triples)",
-            "map": "lambda (two-branch recursive 3-simplex map + J=K plane)",
-            "n": w["n"], "triples": triples(w["n"]),
-            "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write)"}
+def cpu_stress(x, y, rows, workers):
+    """The oracle's loss terms over whole rows (forward) and gradient rows
+    (backward), one row block per thread."""
+    import oracle
+    oracle.build()
+    n = len(x)
+    blocks = np.array_split(np.asarray(rows), workers)
+    fwd = oracle_rate(lambda b: oracle.stress_loss_rows(x, y, int(b[0]), int(b[-1]) + 1), blocks,
+                      [int(sum(int(i) for i in b)) for b in blocks], workers)
+    bwd = oracle_rate(lambda b: oracle.stress_grad_rows(x, y, b), blocks,
+                      [len(b) * (n - 1) for b in blocks], workers)
+    # a backward row touches n - 1 pairs from one side; each pair has two
+    # sides, so pairs/s of the whole backward is half the rows' pair rate
+    bwd["value"] /= 2
+    bwd["single_core"] /= 2
+    for r, what in ((fwd, "loss terms (D - delta)^2 of the pairs j < i"), (bwd, "gradient rows")):
+        r.update({"unit": "pairs/s", "extrapolated": True,
+                  "sample": f"FP64 C oracle, {what} of {len(rows)} rows {rows[0]}..{rows[-1]}, "
+                            f"split over the host threads; extrapolated by pair count"})
+    return {"fwd": fwd, "bwd": bwd}
 
 
-# ------------------------------------------------------------------ our arm
+def cpu_cover(m, n, rho):
+    """The oracle's coverage count (map table walk, one thread) of the same
+    problem, whole."""
+    import oracle
+    oracle.build()
+    fn = {2: oracle.cover2, 3: oracle.cover3, 4: oracle.cover4}[m]
+    t0 = time.perf_counter()
+    fn(n, rho, "lambda")
+    el = time.perf_counter() - t0
+    vol = math.comb(n + m - 1, m)
+    return {"value": vol / el, "unit": "elements/s", "cores": 1, "kind": "oracle", "extrapolated": False,
+            "sample": f"FP64 C oracle, the whole lambda coverage of n={n}, rho={rho} on one thread",
+            "seconds": el}
+# ------------------------------------------------------------------ rows
 
 def _median_ms(torch, fn, steps, warmup=1):
     return statistics.median(time_steps(torch, fn, steps, warmup))
@@ -300,6 +369,7 @@ def row_edm_n1024_d3(torch, sx, peaks):
         del g
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
     r["lambda_vs_rb"] = r["lambda"] / r["rb"]
+    r["cpu_baseline"] = cpu_edm(synth.make_points("edm_n1024_d3"), 4_000_000, host_cores())
     return r
 
 
@@ -368,6 +438,7 @@ def row_edm_n32768_d256(torch, sx, peaks):
     sx.simplex_edm_packed(x, o, "lambda", "bf16x3", sx.workspace("edm", x.shape[0], x.shape[1], "lambda", "bf16x3"))
     r["error_lambda"] = _edm_error(torch, o, xh, seed=21)
     r["fp32_simt_lambda"] = _edm_big(torch, sx, peaks, x, "fp32", ("lambda", "bbox"), out=o)["lambda"]
+    r["cpu_baseline"] = cpu_edm(xh, 2_000_000, host_cores())
     return r
 
 
@@ -383,6 +454,7 @@ def row_edm_n65536_d64(torch, sx, peaks):
     del o
     torch.cuda.empty_cache()
     r["tiles"] = _edm_tiles(torch, sx, peaks, x)
+    r["cpu_baseline"] = cpu_edm(xh, 4_000_000, host_cores())
     return r
 
 
@@ -428,44 +500,111 @@ def row_edm_n16384_d256(torch, sx, peaks):
     return _edm_big(torch, sx, peaks, x, "bf16x3")
 
 
-def row_atm_n4096(torch, sx, peaks):
-    """ATM n=4096 (differentiation config): energy, energy+forces."""
-    x = torch.from_numpy(synth.make_points("atm_n4096")).cuda()
-    n = 4096
-    r = {"unit": "triplets/s", "triples": triples(n)}
+def _atm_row(torch, sx, x, maps=("lambda", "bbox", "linear"), steps=3, warmup=1):
+    """ATM energy (pair tables + energy kernel + FP64 reduction) and energy
+    with forces (force tables + forces kernel) per map: whole-call rates,
+    L2 not flushed (the tables of a call are larger than L2 from n = 4096)."""
+    n = len(x)
+    r = {"unit": "triplets/s", "triples": triples(n), "n": n}
     e = torch.empty((), dtype=torch.float64, device="cuda")
-    for mp in ("lambda", "bbox", "linear"):
+    for mp in maps:
         ws = sx.workspace("atm_energy", n, 3, mp)
-        ms = _median_ms(torch, lambda: sx.simplex_atm_energy(x, NU, EPS, e, mp, ws), 3)
+        ms = _median_ms(torch, lambda: sx.simplex_atm_energy(x, NU, EPS, e, mp, ws), steps, warmup)
         r["energy_" + mp] = triples(n) / (ms / 1e3)
-    r["energy_lambda_vs_bbox"] = r["energy_lambda"] / r["energy_bbox"]
+        del ws
     f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-    for mp in ("lambda", "bbox"):
+    for mp in maps:
         ws = sx.workspace("atm_forces", n, 3, mp)
-        ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws), 3)
+        ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws), steps, warmup)
         r["energy_forces_" + mp] = triples(n) / (ms / 1e3)
-    r["energy_forces_lambda_vs_bbox"] = r["energy_forces_lambda"] / r["energy_forces_bbox"]
+        del ws
+        torch.cuda.empty_cache()
+    for k in ("energy", "energy_forces"):
+        r[k + "_lambda_vs_bbox"] = r[k + "_lambda"] / r[k + "_bbox"]
+        if "linear" in maps:
+            r[k + "_lambda_vs_linear"] = r[k + "_lambda"] / r[k + "_linear"]
     r["energy_fp32_frac"] = FLOPS_PER_TRIPLE * r["energy_lambda"] / 1e12 / _fp32_peak(torch)
     r["energy_forces_fp32_frac"] = FORCE_FLOPS_PER_TRIPLE * r["energy_forces_lambda"] / 1e12 / _fp32_peak(torch)
     return r
 
 
-def row_atm_n16384(torch, sx, peaks):
-    """ATM n=16384 (scale config): 7.33e11 triples."""
-    n = 16384
-    x = torch.from_numpy(synth.make_points("atm_n16384")).cuda()
-    r = {"unit": "triplets/s", "triples": triples(n)}
+def _atm_cpu(xh, target):
+    w = host_cores()
+    rows = rows_with(len(xh), target, w)
+    return {"energy": cpu_atm(xh, rows, False, w), "energy_forces": cpu_atm(xh, rows, True, w)}
+
+
+def row_atm_n4096(torch, sx, peaks):
+    """ATM n=4096 (differentiation config): energy, energy+forces."""
+    xh = synth.make_points("atm_n4096")
+    r = _atm_row(torch, sx, torch.from_numpy(xh).cuda())
+    r["cpu_baseline"] = _atm_cpu(xh, 8_000_000)
+    return r
+
+
+def row_atm_n3000(torch, sx, peaks):
+    """ATM n=3000 (a non-power of two: lambda pads the 94 blocks to 128 and
+    filters, Sec. III-A "approach n from above"), uniform in a cube of side
+    20, seed 7."""
+    xh = synth.uniform_cube(3000, 3, 20.0, seed=7)
+    r = _atm_row(torch, sx, torch.from_numpy(xh).cuda())
+    r["grid_blocks"] = {mp: sx.simplex_grid_blocks(3, -(-3000 // 32), mp) for mp in ("lambda", "bbox", "linear")}
+    r["cpu_baseline"] = _atm_cpu(xh, 4_000_000)
+    return r
+
+
+def row_atm_n12000(torch, sx, peaks):
+    """ATM n=12000 (375 blocks, padded to 512 by lambda), uniform in a cube
+    of side 20, seed 8: 2.88e11 triples."""
+    xh = synth.uniform_cube(12000, 3, 20.0, seed=8)
+    r = _atm_row(torch, sx, torch.from_numpy(xh).cuda(), steps=2)
+    r["grid_blocks"] = {mp: sx.simplex_grid_blocks(3, -(-12000 // 32), mp) for mp in ("lambda", "bbox", "linear")}
+    r["cpu_baseline"] = _atm_cpu(xh, 20_000_000)
+    return r
+
+
+def row_atm_n1024(torch, sx, peaks, steps=100):
+    """ATM energy alone, n=1024 (the 3-simplex plain config, 178,433,024
+    triples): the step is the pair tables, the energy kernel and the FP64
+    reduction, L2 flushed between steps; the energy kernel against the FP32
+    ALU roofline; the energy against the oracle's FP64 sum."""
+    xh = synth.make_points("atm_n1024")
+    x = torch.from_numpy(xh).cuda()
+    n = len(xh)
+    units = triples(n)
     e = torch.empty((), dtype=torch.float64, device="cuda")
-    ws = sx.workspace("atm_energy", n, 3, "lambda")
-    ms = _median_ms(torch, lambda: sx.simplex_atm_energy(x, NU, EPS, e, "lambda", ws), 1, 0)
-    r["energy_lambda"] = triples(n) / (ms / 1e3)
-    del ws
-    ws = sx.workspace("atm_forces", n, 3, "lambda")
-    f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
-    ms = _median_ms(torch, lambda: sx.simplex_atm_forces(x, NU, EPS, e, f, "lambda", ws), 1, 0)
-    r["energy_forces_lambda"] = triples(n) / (ms / 1e3)
-    r["energy_fp32_frac"] = FLOPS_PER_TRIPLE * r["energy_lambda"] / 1e12 / _fp32_peak(torch)
-    r["energy_forces_fp32_frac"] = FORCE_FLOPS_PER_TRIPLE * r["energy_forces_lambda"] / 1e12 / _fp32_peak(torch)
+    flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    flush = lambda: flush_buf.fill_(1)  # noqa: E731
+    r = {"unit": "triplets/s", "triples": units}
+    e_gpu = None
+    for mp in ("lambda", "bbox", "linear"):
+        ws = sx.workspace("atm_energy", n, 3, mp)
+        step = lambda: sx.simplex_atm_energy(x, NU, EPS, e, mp, ws)  # noqa: E731
+        ts = time_steps(torch, step, steps, 3, flush, label="energy_n1024_" + mp)
+        r[mp] = units / (sum(ts) / len(ts) / 1e3)
+        r[mp + "_ms"] = sum(ts) / len(ts)
+        if mp == "lambda":
+            sx.simplex_profile(True)
+            time_steps(torch, step, 20, 0, flush, label="energy_n1024_kernel")
+            k_ms, k, _ = sx.simplex_profile_read()
+            sx.simplex_profile(False)
+            k_ms /= max(k, 1)
+            r["kernel"] = "k_atm_energy_tab<lambda>"
+            r["kernel_ms"] = k_ms
+            r["kernel_tflops"] = FLOPS_PER_TRIPLE * units / (k_ms / 1e3) / 1e12
+            r["kernel_fp32_frac"] = r["kernel_tflops"] / _fp32_peak(torch)
+            e_gpu = float(e.item())
+    del flush_buf
+    r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
+    r["lambda_vs_linear"] = r["lambda"] / r["linear"]
+    import oracle
+    oracle.build()
+    r["cpu_baseline"] = cpu_atm(xh, list(range(0, n - 2)), False, host_cores())
+    r["cpu_baseline"]["extrapolated"] = False
+    r["cpu_baseline"]["sample"] = "FP64 C oracle, the whole n=1024 sum, one i-row per task on the host threads"
+    e_ref = oracle.atm_energy(xh, NU, EPS)
+    r["accuracy"] = {"energy": e_gpu, "energy_oracle": e_ref, "rel_err": abs(e_gpu - e_ref) / abs(e_ref),
+                     "tolerance": 1e-6}
     return r
 
 
@@ -495,6 +634,8 @@ def row_stress_n65536_d64(torch, sx, peaks):
     r["fwd_fp32_frac"] = r["fwd_tflops"] / fp32
     r["bwd_fp32_frac"] = r["bwd_tflops"] / fp32
     r.update(_stress_tensor(torch, sx, peaks, x, y, ("lambda", "bbox", "linear", "rb")))
+    w_ = host_cores()
+    r["cpu_baseline"] = cpu_stress(xn, yn, list(range(n - 4 * w_, n)), w_)
     return r
 
 
@@ -550,7 +691,7 @@ def row_stress_n16384_d64(torch, sx, peaks):
     return _stress_tensor(torch, sx, peaks, x, y, ("lambda",))
 
 
-def _cover_row(torch, sx, m, n, rho):
+def _cover_row(torch, sx, m, n, rho, cpu=True):
     """Coverage of the m-simplex with one thread per element: each map's grid
     launched as is, every thread decoding its block and counting its element
     (an atomic increment) or itself as idle.  The per-element work is one
@@ -571,6 +712,9 @@ def _cover_row(torch, sx, m, n, rho):
     r["lambda_vs_bbox"] = r["lambda"] / r["bbox"]
     if m == 2:
         r["lambda_vs_rb"] = r["lambda"] / r["rb"]
+        r["lambda_vs_linear"] = r["lambda"] / r["linear"]
+    if cpu:
+        r["cpu_baseline"] = cpu_cover(m, n, rho)
     return r
 
 
@@ -591,6 +735,29 @@ def row_cover4_n256(torch, sx, peaks):
     return _cover_row(torch, sx, 4, 256, 4)
 
 
+def row_cover2_n12000(torch, sx, peaks):
+    """Coverage of the 2-simplex at a non-power of two, n=12000, 16x16
+    threads per block (750 blocks: lambda pads to 1024)."""
+    r = _cover_row(torch, sx, 2, 12000, 16)
+    r["grid_blocks"] = {mp: sx.simplex_grid_blocks(2, 750, mp) for mp in ("lambda", "bbox", "linear", "rb")}
+    return r
+
+
+def row_edm_n49152_d64(torch, sx, peaks):
+    """EDM at a non-power of two, n=49152 (384 tiles of 128, 192 super-blocks
+    of 256: lambda pads them to 256), d=64, N(0,1) seed 9: both layouts,
+    every map."""
+    xh = synth.normal(49152, 64, seed=9)
+    x = torch.from_numpy(xh).cuda()
+    maps = ("lambda", "bbox", "linear", "rb")
+    r = _edm_big(torch, sx, peaks, x, "bf16x3", maps)
+    torch.cuda.empty_cache()
+    r["tiles"] = _edm_tiles(torch, sx, peaks, x, maps=maps)
+    r["grid_blocks_256"] = {mp: sx.simplex_grid_blocks(2, 192, mp) for mp in maps}
+    r["cpu_baseline"] = cpu_edm(xh, 4_000_000, host_cores())
+    return r
+
+
 ROWS = {
     "cover2_n16384": row_cover2_n16384,
     "cover3_n1024": row_cover3_n1024,
@@ -598,9 +765,14 @@ ROWS = {
     "edm_n1024_d3": row_edm_n1024_d3,
     "edm_n32768_d256": row_edm_n32768_d256,
     "edm_n65536_d64": row_edm_n65536_d64,
+    "atm_n1024": row_atm_n1024,
     "atm_n4096": row_atm_n4096,
-    "atm_n16384": row_atm_n16384,
     "stress_n65536_d64": row_stress_n65536_d64,
+    # non-powers of two (lambda pads to the next power and filters)
+    "cover2_n12000": row_cover2_n12000,
+    "edm_n49152_d64": row_edm_n49152_d64,
+    "atm_n3000": row_atm_n3000,
+    "atm_n12000": row_atm_n12000,
 }
 # profiling-only cases (not part of the default rows)
 PROFILE_ROWS = {"edm_n16384_d64": row_edm_n16384_d64, "edm_n16384_d256": row_edm_n16384_d256,
@@ -625,6 +797,64 @@ def row_only(args):
     peaks, _ = measured_peaks()
     fn = ROWS.get(args.row) or PROFILE_ROWS[args.row]
     print(json.dumps({"row": args.row, **fn(torch, sx, peaks)}), flush=True)
+
+
+# ------------------------------------------------------------------ the headline workload
+
+def config_block():
+    w = synth.WORKLOADS[WORKLOAD]
+    return {"workload": f"ATM triple-dipole energy and adjoint forces (E, F = -dE/dx) over i<j<k, "
+                        f"n={w['n']} uniform in a cube of side {w['side']:g}, seed {w['seed']}, nu=1, "
+                        f"eps=1e-4 ({triples(w['n'])} triples)",
+            "map": "lambda (two-branch recursive 3-simplex map + J=K plane)",
+            "n": w["n"], "triples": triples(w["n"]),
+            "l2": f"flushed before every timed step ({L2_FLUSH_BYTES >> 20} MB write); the call's "
+                  f"force tables (9.7 GB) exceed L2 as well"}
+
+
+def headline_cpu_rows(n, workers):
+    """The i-rows the oracle times for the headline (about 1e7 triples each,
+    one per host thread)."""
+    return rows_with(n, 10_000_000, workers)
+
+
+def reference_arm(args):
+    """The FP64 oracle on the host cores (all of them, one i-row of the
+    3-simplex per thread) on the headline's metric: each step the energy and
+    gradient of a bounded sample of the n=16384 triples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    x = synth.make_points(WORKLOAD)
+    import oracle
+    oracle.build()
+    n = len(x)
+    xd = x.astype(np.float64)
+    workers = host_cores()
+    rows = headline_cpu_rows(n, workers)
+    units = sum(row_triples(n, i) for i in rows)
+
+    def work(i):
+        oracle.atm_energy_grad_slice(xd, i, i + 1, NU, EPS)
+
+    for _ in range(args.warmup):
+        host_parallel(work, rows, workers)
+    ts = [host_parallel(work, rows, workers)[1] for _ in range(args.steps)]
+    ms = 1e3 * sum(ts) / len(ts)
+    value = units / (ms / 1e3)
+    sample = (f"energy and gradient of the triples with i in rows {rows[0]}..{rows[-1]} of the n={n} "
+              f"workload ({units} of {triples(n)} triples) per step, FP64 C oracle, one row per host "
+              f"thread ({workers} threads); rate extrapolated to the whole sum by triple count")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "triplets/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(),
+        "cpu_baseline": {"value": value, "unit": "triplets/s", "cores": workers, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def our_arm(args):
@@ -652,13 +882,14 @@ def our_arm(args):
     xh = synth.make_points(WORKLOAD)
     x = torch.from_numpy(xh).cuda()
     e = torch.empty((), dtype=torch.float64, device="cuda")
+    f = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     units = triples(n)
     flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     flush = lambda: flush_buf.fill_(1)  # noqa: E731
-    ws = {mp: sx.workspace("atm_energy", n, 3, mp) for mp in ("lambda", "bbox", "linear")}
+    ws = sx.workspace("atm_forces", n, 3, "lambda")
 
-    def step(mp="lambda"):
-        sx.simplex_atm_energy(x, NU, EPS, e, mp, ws[mp])
+    def step(mp="lambda", wsp=None):
+        sx.simplex_atm_forces(x, NU, EPS, e, f, mp, ws if wsp is None else wsp)
 
     clocks = Clocks(local)
     clocks.start()
@@ -670,14 +901,14 @@ def our_arm(args):
     torch.cuda.synchronize()
     # the timed steps run without the library's event pairs (profile(1) then
     # (0) clears the counters; the launch counter keeps counting), and a
-    # second pass of the same steps with the event pairs on times the main
+    # second pass of a few steps with the event pairs on times the forces
     # kernel for the roofline
     sx.simplex_profile(True)
     sx.simplex_profile(False)
-    times = time_steps(torch, step, args.steps, 0, flush, label="energy_lambda")
+    times = time_steps(torch, step, args.steps, 0, flush, label="energy_forces_lambda")
     _, _, launches = sx.simplex_profile_read()
     sx.simplex_profile(True)
-    time_steps(torch, step, min(args.steps, 100), 0, flush, label="energy_lambda_kernel")
+    time_steps(torch, step, min(args.steps, 3), 0, flush, label="energy_forces_kernel")
     main_ms, main_k, _ = sx.simplex_profile_read()
     sx.simplex_profile(False)
     torch.cuda.synchronize()
@@ -685,37 +916,54 @@ def our_arm(args):
         dist.barrier()
     value, ms_step = job_rate(sum(times) / len(times), units, world, dist, "cuda")
     k_ms = main_ms / max(main_k, 1)
-    achieved = FLOPS_PER_TRIPLE * units / (k_ms / 1e3) / 1e12
+    achieved = FORCE_FLOPS_PER_TRIPLE * units / (k_ms / 1e3) / 1e12
+    e_step = float(e.item())
+    f_step = f.cpu().numpy()
 
     # the same step on the other maps (same kernel body, same tile)
     maps = {"lambda": units / (ms_step / 1e3)}
+    other = min(args.steps, 2)
     for mp in ("bbox", "linear"):
-        tt = time_steps(torch, lambda: step(mp), args.steps, 3, flush, label="energy_" + mp)
+        wsm = sx.workspace("atm_forces", n, 3, mp)
+        tt = time_steps(torch, lambda: step(mp, wsm), other, 1, flush, label="energy_forces_" + mp)
         maps[mp] = units / (sum(tt) / len(tt) / 1e3)
+        maps[mp + "_energy_rel_diff"] = abs(float(e.item()) - e_step) / abs(e_step)
+        del wsm
+        torch.cuda.empty_cache()
     maps["lambda_vs_bbox"] = maps["lambda"] / maps["bbox"]
     maps["lambda_vs_linear"] = maps["lambda"] / maps["linear"]
-    maps["grid_blocks"] = {mp: sx.simplex_grid_blocks(3, -(-n // sx.simplex_block_rho("atm_energy")), mp)
+    maps["grid_blocks"] = {mp: sx.simplex_grid_blocks(3, -(-n // sx.simplex_block_rho("atm_forces")), mp)
                            for mp in ("lambda", "bbox", "linear")}
+    maps["steps_each"] = other
 
-    # end to end through the C ABI with host buffers: H2D of x, the call, D2H of E
+    # end to end through the public API with host buffers: the C ABI called
+    # through the package's ctypes binding, with the H2D copy of x and the
+    # D2H copies of E and F (pinned host memory) inside every timed step
     xp = torch.from_numpy(xh).pin_memory()
     ep = torch.empty((), dtype=torch.float64).pin_memory()
+    fp = torch.empty((n, 3), dtype=torch.float64).pin_memory()
 
     def e2e_step():
         x.copy_(xp, non_blocking=True)
         step()
         ep.copy_(e, non_blocking=True)
+        fp.copy_(f, non_blocking=True)
 
-    te = time_steps(torch, e2e_step, args.steps, 3, flush, label="energy_e2e")
-    e2e_value, e2e_ms = job_rate(sum(te) / len(te), units, world, dist, "cuda")
+    te = time_steps(torch, e2e_step, min(args.steps, 5), 1, flush, label="energy_forces_e2e")
+    e2e_value, _ = job_rate(sum(te) / len(te), units, world, dist, "cuda")
     e2e = {"value": e2e_value, "unit": "triplets/s",
            "h2d_bytes_per_step": int(xp.numel() * xp.element_size()),
-           "d2h_bytes_per_step": int(ep.numel() * ep.element_size())}
+           "d2h_bytes_per_step": int(ep.numel() * ep.element_size() + fp.numel() * fp.element_size()),
+           "path": "simplex_atm_forces through the package's ctypes binding; torch copies from and to "
+                   "pinned host buffers on the same stream", "steps": min(args.steps, 5)}
+    del ws
+    torch.cuda.empty_cache()
 
     do_rows = args.rows == "on" or (args.rows == "auto" and world == 1)
     rows = rows_measure(torch, sx, peaks) if (do_rows and rank == 0) else None
     clk = clocks.stop()
 
+    traffic, traffic_note = stated_traffic("k_atm_forces_n16384.md")
     line = {
         "metric": METRIC, "value": value, "unit": "triplets/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -723,25 +971,32 @@ def our_arm(args):
         "data": "synthetic", "config": config_block(),
         "maps": maps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": ENERGY_KERNEL_DRAM_BYTES,
-                     "algorithmic_bytes": 12 * n + 8 * 6656,
-                     "kernel": "k_atm_energy_tab<lambda>", "kernel_ms": k_ms,
-                     "flops_per_triple": FLOPS_PER_TRIPLE,
+                     "frac": achieved / fp32_peak, "traffic": traffic, "traffic_source": traffic_note,
+                     "algorithmic_bytes": 12 * n + 24 * n + 8,
+                     "kernel": "k_atm_forces<lambda>", "kernel_ms": k_ms,
+                     "flops_per_triple": FORCE_FLOPS_PER_TRIPLE,
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:g} MHz "
-                                   f"(unit counts and max clock; {peak_src} peaks file has no FP32 figure)"},
+                                   f"(unit counts and max clock; the {peak_src} peaks file has no FP32 "
+                                   f"figure)"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
     }
     if rank == 0 and world == 1:
-        rate, u, reps, el, e_ref = oracle_energy_rate(xh)
-        line["cpu_baseline"] = {"value": rate, "unit": "triplets/s", "cores": 1, "kind": "oracle",
-                                "sample": f"the whole n=1024 sum ({u} triples) x{reps}, {el:.1f} s, "
-                                          "FP64 C oracle, 1 thread"}
-        # the timed step's energy against the oracle's sum (parity of the measured run)
-        e_gpu = float(e.item())
-        line["accuracy"] = {"energy": e_gpu, "energy_oracle": e_ref,
-                            "rel_err": abs(e_gpu - e_ref) / abs(e_ref), "tolerance": 1e-6}
+        workers = host_cores()
+        line["cpu_baseline"] = cpu_atm(xh, headline_cpu_rows(n, workers), True, workers)
+        # the step's forces on seeded atoms against the oracle's analytic
+        # gradient (parity of the measured run; the energy is compared
+        # across maps above, the oracle's O(n^3) sum being out of reach)
+        import oracle
+        oracle.build()
+        atoms = synth.sample_indices(8, n, seed=6 + 10 ** 6)
+        g_ref, _ = host_parallel(lambda a: oracle.atm_grad_atoms(xh, [int(a)], NU, EPS)[0], list(atoms), workers)
+        g_ref = np.array(g_ref)
+        err = np.linalg.norm(f_step[atoms] + g_ref, axis=1) / np.linalg.norm(g_ref, axis=1)
+        line["accuracy"] = {"forces_max_rel_err": float(err.max()), "atoms": len(atoms),
+                            "reference": "FP64 oracle gradient rows", "tolerance": 1e-4,
+                            "energy": e_step}
     if rows is not None:
         line["rows"] = rows
     if rank == 0:

@@ -246,12 +246,16 @@ int simplex_atm_energy(int64_t n, int64_t d, const float *x, float nu, float eps
 
 /*
  * ATM forces F = -dE/dx (n x 3 FP64, written) and, if `energy` is not NULL,
- * the energy, on the same block grid: every triple adds dE/d(r^2) of its
- * three sides to per-pair coefficients, which are turned into forces once
- * per block; forces accumulate in FP64.  Workspace: simplex_workspace_bytes(
- * SIMPLEX_OP_ATM_FORCES, ...) bytes, 256-byte aligned: the pair terms of
- * every block pair (72 KB each, computed once per call, up to 16 GB; beyond
- * that the tiles build their own) and one FP64 partial per grid block.
+ * the energy, over the tiles of the same block grid: every triple adds
+ * dE/d(r^2) of its three sides to per-pair coefficients, which are turned
+ * into forces once per tile; forces accumulate in FP64.  A persistent kernel
+ * (as many blocks as are resident at once) takes the map's grid blocks in
+ * launch order from a counter in the workspace.  Workspace:
+ * simplex_workspace_bytes(SIMPLEX_OP_ATM_FORCES, ...) bytes, 256-byte
+ * aligned: the pair terms of every block pair (72 KB each, computed once per
+ * call, up to 16 GB; beyond that the tiles build their own), the 16-byte
+ * tile counter (zeroed by the call) and FP64 partials, one per grid block at
+ * most.  Calls that share a workspace must not overlap.
  */
 int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu, float eps,
                        double *energy, double *forces, int map, void *workspace,

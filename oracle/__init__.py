@@ -29,11 +29,16 @@ Parity status of each function (what pins it, see ``tests/test_oracle.py``):
   pinned by closed-form triangles (equilateral, collinear, right angle), a
   pure-Python brute force using angles, invariances, Euler's theorem for a
   homogeneous function and FD of the energy.
+* ``atm_energy_grad_slice``: pinned by FD of its own energy (a sum of terms
+  whose gradient it returns) and by slices that partition the total energy
+  and gradient.
 * ``atm_abs_energy`` (sum of |e|): pinned by the closed-form triangles in
   absolute value, a pure-Python brute force of sum |e| on a cloud with terms
   of both signs, and equality with E on a regular tetrahedron.
 * ``stress_loss`` / ``stress_grad_rows``: pinned by the two-point closed form,
   the zero at y = x, translation invariance and FD.
+* ``stress_loss_rows``: pinned by the moment-matrix form of the loss (rows
+  partition it) and the two-point closed form on its one row.
 """
 from __future__ import annotations
 
@@ -84,6 +89,8 @@ def lib():
             "oracle_cover4": (_i64, [_i64, _i64, ctypes.c_int, _i32p]),
             "oracle_edm_packed": (None, [_i64, _i64, _dp, _dp]),
             "oracle_edm_tiles": (None, [_i64, _i64, _dp, _dp]),
+            "oracle_atm_energy_grad_slice": (_d, [_i64, _dp, _d, _d, _i64, _i64, _dp]),
+            "oracle_stress_loss_rows": (_d, [_i64, _i64, _dp, _dp, _i64, _i64]),
             "oracle_edm_pairs": (None, [_i64, _dp, _i64p, _i64, _dp]),
             "oracle_atm_energy": (_d, [_i64, _dp, _d, _d]),
             "oracle_atm_energy_slice": (_d, [_i64, _dp, _d, _d, _i64, _i64]),
@@ -246,6 +253,17 @@ def atm_grad(x: np.ndarray, nu: float = 1.0, eps: float = 1e-4) -> np.ndarray:
     return g
 
 
+def atm_energy_grad_slice(x: np.ndarray, i_lo: int, i_hi: int, nu: float = 1.0,
+                          eps: float = 1e-4, grad: np.ndarray | None = None):
+    """(energy, gradient) of the triples with i in [i_lo, i_hi); the gradient
+    is added into `grad` when one is given (n x 3 FP64)."""
+    x = _f64(x)
+    g = np.zeros_like(x) if grad is None else grad
+    e = lib().oracle_atm_energy_grad_slice(len(x), _p(x, ctypes.c_double), nu, eps, i_lo, i_hi,
+                                           _p(g, ctypes.c_double))
+    return e, g
+
+
 def atm_grad_atoms(x: np.ndarray, atoms, nu: float = 1.0, eps: float = 1e-4) -> np.ndarray:
     x = _f64(x)
     a = np.ascontiguousarray(atoms, dtype=np.int64)
@@ -256,6 +274,13 @@ def atm_grad_atoms(x: np.ndarray, atoms, nu: float = 1.0, eps: float = 1e-4) -> 
 
 
 # ---------------------------------------------------------------- stress
+
+def stress_loss_rows(x: np.ndarray, y: np.ndarray, i_lo: int, i_hi: int) -> float:
+    """Loss terms of the rows i in [i_lo, i_hi) (pairs j < i)."""
+    x, y = _f64(x), _f64(y)
+    n, d = x.shape
+    return lib().oracle_stress_loss_rows(n, d, _p(x, ctypes.c_double), _p(y, ctypes.c_double), i_lo, i_hi)
+
 
 def stress_loss(x: np.ndarray, y: np.ndarray) -> float:
     x, y = _f64(x), _f64(y)

@@ -676,6 +676,31 @@ void oracle_atm_grad(int64_t n, const double *x, double nu, double eps, double *
             }
 }
 
+/* Energy of the triples i < j < k with i in [i_lo, i_hi), and their
+ * contribution to the gradient added into grad (n x 3): a slice of the outer
+ * loop of the total energy and gradient, used to time a bounded sample of the
+ * energy-and-forces workload (slices partition the sum). */
+double oracle_atm_energy_grad_slice(int64_t n, const double *x, double nu, double eps,
+                                    int64_t i_lo, int64_t i_hi, double *grad)
+{
+    double e = 0.0;
+    for (int64_t i = i_lo; i < i_hi && i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            for (int64_t k = j + 1; k < n; ++k) {
+                const double *xi = x + 3 * i, *xj = x + 3 * j, *xk = x + 3 * k;
+                double gA, gB, gC;
+                e += atm_term(xi, xj, xk, nu, eps);
+                atm_sides_grad(xi, xj, xk, nu, eps, &gA, &gB, &gC);
+                for (int t = 0; t < 3; ++t) {
+                    double ij = xi[t] - xj[t], jk = xj[t] - xk[t], ki = xk[t] - xi[t];
+                    grad[3 * i + t] += 2.0 * gA * ij - 2.0 * gC * ki;
+                    grad[3 * j + t] += -2.0 * gA * ij + 2.0 * gB * jk;
+                    grad[3 * k + t] += -2.0 * gB * jk + 2.0 * gC * ki;
+                }
+            }
+    return e;
+}
+
 /* Gradient rows of the listed atoms only, O(n^2) each. */
 void oracle_atm_grad_atoms(int64_t n, const double *x, double nu, double eps,
                            const int64_t *atoms, int64_t count, double *out)
@@ -710,6 +735,20 @@ double oracle_stress_loss(int64_t n, int64_t d, const double *x, const double *y
 {
     double L = 0.0;
     for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < i; ++j) {
+            double r = sqdist(x + i * d, x + j * d, d) - sqdist(y + i * d, y + j * d, d);
+            L += r * r;
+        }
+    return L;
+}
+
+/* The loss terms of rows i in [i_lo, i_hi): sum over j < i of (D_ij -
+ * delta_ij)^2 (slices partition L; used to time a bounded sample). */
+double oracle_stress_loss_rows(int64_t n, int64_t d, const double *x, const double *y,
+                               int64_t i_lo, int64_t i_hi)
+{
+    double L = 0.0;
+    for (int64_t i = i_lo; i < i_hi && i < n; ++i)
         for (int64_t j = 0; j < i; ++j) {
             double r = sqdist(x + i * d, x + j * d, d) - sqdist(y + i * d, y + j * d, d);
             L += r * r;

@@ -465,55 +465,71 @@ __global__ void __launch_bounds__(256, 3) k_atm_energy_tab(const float4 *__restr
 
 // ---------------------------------------------------------------- forces
 
-// Force tables, laid out like the energy tables for packed FP32x2 arithmetic
-// over the thread's two i-slots p (lanes x, y):
-//   fc[k][0][ti] = (u_ik0.x, u_ik1.x, u_ik0.y, u_ik1.y)
-//   fc[k][1][ti] = (u_ik0.z, u_ik1.z, r_ik0,   r_ik1)
-//   fc[k][2][ti] = (r_ik0^3, r_ik1^3, r_ik0^2, r_ik1^2)
-//   fb[k][q][0..2][tj] = the same three vectors of pair (j = tj + 16q, k),
-//   each value duplicated into both lanes (one broadcast load feeds both).
-struct AtmForceSmem {
-    float4 xs[3][R_];
-    float4 fc[R_][3][16];
-    float4 fb[R_][2][3][16];
-    float wjk[R_][R_ + 1];   // [k][j]: sum over i of de/db
-    float wik[R_][R_ + 1];   // [k][i]: sum over j of de/dc
-    float wij[R_][R_ + 1];   // [i][j]: sum over k of de/da
-    uint64_t bar;            // the tile's force tables landed (table-fed kernel)
-};
-
-// (u, r, r^3, r^2) of a pair: r = 1/sqrt(s), r^3 = 1/(s sqrt(s)), all zero
-// outside the simplex.
+// Pair terms of the forces, from the edge vector e = x_b - x_a of a pair and
+// its softened square s = |e|^2 + eps: the scaled edge w = e / s (= r u with
+// r = s^-1/2, u the unit vector), s, r^3 = s^-3/2 and q = 1/s = r^2; all zero
+// outside the simplex.  With scaled edges the vertex dot products of a
+// triangle (sides a = ij, b = jk, c = ik) carry the r factors the
+// derivatives need:
+//   P_i = w_ij . w_ik = cos_i r_a r_c,   P_j = w_ij . w_jk = -cos_j r_a r_b,
+//   P_k = w_ik . w_jk = cos_k r_b r_c,
+// so X = cos_j cos_k r_a r_c = -P_j P_k s_b, Y = cos_i cos_k r_a r_b =
+// P_i P_k s_c, Z = cos_i cos_j r_b r_c = -P_i P_j s_a and the cosine product
+// Cp = -P_i P_j P_k s_a s_b s_c.
 struct PairTerms {
-    float ux, uy, uz, r, r3, r2;
+    float wx, wy, wz, s, r3, q;
 };
 
 __device__ __forceinline__ PairTerms pair_terms(float4 from, float4 to, bool valid, float eps) {
     PairTerms t;
-    if (!valid) { t.ux = t.uy = t.uz = t.r = t.r3 = t.r2 = 0.0f; return t; }
+    if (!valid) { t.wx = t.wy = t.wz = t.s = t.r3 = t.q = 0.0f; return t; }
     const float4 e = edge(from, to);
     const float s = fmaf(e.x, e.x, fmaf(e.y, e.y, fmaf(e.z, e.z, eps)));
-    const float q = sqrtf(s);
-    t.r = 1.0f / q;
-    t.r3 = 1.0f / (s * q);
-    t.r2 = t.r * t.r;
-    t.ux = e.x * t.r; t.uy = e.y * t.r; t.uz = e.z * t.r;
+    const float sq = sqrtf(s);
+    t.s = s;
+    t.q = 1.0f / s;
+    t.r3 = 1.0f / (s * sq);
+    t.wx = e.x * t.q; t.wy = e.y * t.q; t.wz = e.z * t.q;
     return t;
 }
 
+// Force tables, laid out for packed FP32x2 arithmetic over the thread's two
+// i-slots p (lanes x, y: i = ti and ti + 16):
+//   fc[k][0][ti] = (w_ik0.x, w_ik1.x, w_ik0.y, w_ik1.y)
+//   fc[k][1][ti] = (w_ik0.z, w_ik1.z, s_ik0,   s_ik1)
+//   fc[k][2][ti] = (r_ik0^3, r_ik1^3, q_ik0,   q_ik1)
+//   fb[k][h][0..2][tj] = the same three vectors of pair (j = tj + 16 h, k),
+//   each value duplicated into both lanes (one broadcast load feeds both).
+// A persistent block walks many tiles: the side-coefficient matrices and the
+// point tiles are double-buffered (tile t uses buffer t & 1) so that the next
+// tile's tables, points and pair constants load while this tile's forces
+// are assembled.
+struct AtmForceSmem {
+    float4 fc[R_][3][16];
+    float4 fb[R_][2][3][16];
+    float4 xs[2][3][R_];
+    float wjk[2][R_][R_ + 1];   // [k][j]: sum over i of de/db
+    float wik[2][R_][R_ + 1];   // [k][i]: sum over j of de/dc
+    float wij[2][R_][R_ + 1];   // [i][j]: sum over k of de/da
+    uint64_t bar;               // the tile's force tables landed (table-fed kernel)
+    int tq[2][4];               // tiles t and t + 1: (I, J, K, valid), slot t & 1
+    long long walk_w;           // the grid block being split into tiles
+    int walk_sub;               // its next tile
+};
+
 __device__ __forceinline__ void build_force_tables(int64_t n, int I, int J, int K, float eps,
-                                                   AtmForceSmem &S) {
+                                                   const float4 (*xs)[R_], AtmForceSmem &S) {
     for (int e = threadIdx.x; e < R_ * R_; e += 256) {
         const int k = e >> 5, o = e & 31, half = o >> 4, t = o & 15;
         const int64_t gi = (int64_t)I * R_ + o, gj = (int64_t)J * R_ + o, gk = (int64_t)K * R_ + k;
-        const PairTerms c = pair_terms(S.xs[0][o], S.xs[2][k], gi < gk && gk < n, eps);
-        put_pair(S.fc[k][0][t], S.fc[k][1][t], half, make_float4(c.ux, c.uy, c.uz, c.r));
+        const PairTerms c = pair_terms(xs[0][o], xs[2][k], gi < gk && gk < n, eps);
+        put_pair(S.fc[k][0][t], S.fc[k][1][t], half, make_float4(c.wx, c.wy, c.wz, c.s));
         float *f2 = reinterpret_cast<float *>(&S.fc[k][2][t]);
-        f2[half] = c.r3; f2[2 + half] = c.r2;
-        const PairTerms b = pair_terms(S.xs[1][o], S.xs[2][k], gj < gk && gk < n, eps);
-        S.fb[k][half][0][t] = make_float4(b.ux, b.ux, b.uy, b.uy);
-        S.fb[k][half][1][t] = make_float4(b.uz, b.uz, b.r, b.r);
-        S.fb[k][half][2][t] = make_float4(b.r3, b.r3, b.r2, b.r2);
+        f2[half] = c.r3; f2[2 + half] = c.q;
+        const PairTerms b = pair_terms(xs[1][o], xs[2][k], gj < gk && gk < n, eps);
+        S.fb[k][half][0][t] = make_float4(b.wx, b.wx, b.wy, b.wy);
+        S.fb[k][half][1][t] = make_float4(b.wz, b.wz, b.s, b.s);
+        S.fb[k][half][2][t] = make_float4(b.r3, b.r3, b.q, b.q);
     }
 }
 
@@ -522,51 +538,45 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Two triples (i0, j, k), (i1, j, k) in the two lanes.  Energy term into acc
-// and the derivatives of e (without nu) with respect to the squared sides
-// a = |e_ij|^2, b = |e_jk|^2, c = |e_ik|^2.  From e = R^3 (1 + 3 D R^2) with
-// D = d_i d_j d_k (vertex dot products, 2 d_i = a + c - b, 2 d_j = a + b - c,
-// 2 d_k = b + c - a) and R^2 = 1/P:
-//   de/da = R^3 (3 R^2 dD/da - 1.5 (1 + 5 D R^2) r_a^2),
-//   dD/da = (d_j d_k + d_i d_k - d_i d_j)/2, and likewise for b, c.
-// In cosines (Cp = cos_i cos_j cos_k = D R^2, d_j d_k R^2 = cos_j cos_k r_a r_c,
-// d_i d_k R^2 = cos_i cos_k r_a r_b, d_i d_j R^2 = cos_i cos_j r_b r_c):
-//   de/da = 1.5 R^3 (X + Y - Z - H r_a^2),  de/db = 1.5 R^3 (Y + Z - X - H r_b^2),
-//   de/dc = 1.5 R^3 (X + Z - Y - H r_c^2),
-// with X = cos_j cos_k r_a r_c, Y = cos_i cos_k r_a r_b, Z = cos_i cos_j r_b r_c,
-// H = 1 + 5 Cp, and R^3 the product of the pairs' r^3.  Here cos_j enters
-// negated (cjn = u_ij . u_jk = -cos_j).  36 packed operations.
+// The pair (i, j) of a thread's i-slots (both lanes) as the triple loop uses
+// it: the scaled edge w_ij, s_a, q_a = 1/s_a and g_a = 1.5 r_a^3.
 struct PairPack {
-    float2 ux, uy, uz;     // u_ij of the two i-slots
-    float2 ra, ra2, ra3;
+    float2 wx, wy, wz;
+    float2 sa, qa, ga;
 };
 
-__device__ __forceinline__ void triple_grad2(const PairPack &c, float4 C0, float4 C1, float4 C2,
-                                             float4 B0, float4 B1, float4 B2, float2 &acc,
-                                             float2 &ea, float2 &eb, float2 &ec) {
-    const float2 cx = f2(C0.x, C0.y), cy = f2(C0.z, C0.w), cz = f2(C1.x, C1.y), rc = f2(C1.z, C1.w);
-    const float2 rc3 = f2(C2.x, C2.y), rc2 = f2(C2.z, C2.w);
-    const float2 bx = f2(B0.x, B0.y), by = f2(B0.z, B0.w), bz = f2(B1.x, B1.y), rb = f2(B1.z, B1.w);
-    const float2 rb3 = f2(B2.x, B2.y), rb2 = f2(B2.z, B2.w);
-    const float2 ci = fma2(c.ux, cx, fma2(c.uy, cy, mul2(c.uz, cz)));
-    const float2 cjn = fma2(c.ux, bx, fma2(c.uy, by, mul2(c.uz, bz)));
-    const float2 ck = fma2(cx, bx, fma2(cy, by, mul2(cz, bz)));
-    const float2 p1 = mul2(cjn, ck);            // -cos_j cos_k
-    const float2 p2 = mul2(ci, cjn);            // -cos_i cos_j
-    const float2 cik = mul2(ci, ck);            //  cos_i cos_k
-    const float2 cpn = mul2(ci, p1);            // -Cp
-    const float2 xn = mul2(p1, mul2(c.ra, rc)); // -X
-    const float2 zn = mul2(p2, mul2(rb, rc));   // -Z
-    const float2 y = mul2(cik, mul2(c.ra, rb)); //  Y
-    const float2 R3 = mul2(mul2(c.ra3, rc3), rb3);
-    acc = fma2(R3, fma2(f2(-3.0f, -3.0f), cpn, f2(1.0f, 1.0f)), acc);
-    const float2 H = fma2(f2(-5.0f, -5.0f), cpn, f2(1.0f, 1.0f));
-    const float2 h = mul2(f2(1.5f, 1.5f), R3);
-    const float2 S = add2(y, f2(-(xn.x + zn.x), -(xn.y + zn.y)));
-    const float2 nH = f2(-H.x, -H.y);
-    ea = mul2(h, fma2(nH, c.ra2, fma2(f2(2.0f, 2.0f), zn, S)));
-    eb = mul2(h, fma2(nH, rb2, fma2(f2(2.0f, 2.0f), xn, S)));
-    ec = mul2(h, fma2(nH, rc2, fma2(f2(-2.0f, -2.0f), y, S)));
+// Two triples (i0, j, k), (i1, j, k) in the two lanes.  With e = R^3 (1 + 3 Cp)
+// (R^3 = r_a^3 r_b^3 r_c^3) and its derivatives by the squared sides
+//   de/da = 1.5 R^3 (X + Y - Z - H q_a),  de/db = 1.5 R^3 (Y + Z - X - H q_b),
+//   de/dc = 1.5 R^3 (X + Z - Y - H q_c),  H = 1 + 5 Cp
+// (from e = P^-3/2 + 3 D P^-5/2, P = s_a s_b s_c, D the product of the three
+// vertex dot products), written with g = 1.5 R^3 and S = X + Y + Z as
+//   e = g (2/3 + 2 Cp),  de/da = g (S - 2 Z - H q_a), ...
+// The energy goes to acc, de/da to wa (summed over k in registers), de/dc to
+// ecs (summed over the thread's two j) and de/db, summed over the two
+// i-lanes, is returned.  32 packed operations and one scalar add.
+__device__ __forceinline__ float triple_grad2(const PairPack &c, float4 C0, float4 C1, float4 C2,
+                                              float4 B0, float4 B1, float4 B2, float2 &acc,
+                                              float2 &wa, float2 &ecs) {
+    const float2 cx = f2(C0.x, C0.y), cy = f2(C0.z, C0.w), cz = f2(C1.x, C1.y), sc = f2(C1.z, C1.w);
+    const float2 rc3 = f2(C2.x, C2.y), qc = f2(C2.z, C2.w);
+    const float2 bx = f2(B0.x, B0.y), by = f2(B0.z, B0.w), bz = f2(B1.x, B1.y), sb = f2(B1.z, B1.w);
+    const float2 rb3 = f2(B2.x, B2.y), qb = f2(B2.z, B2.w);
+    const float2 pi = fma2(c.wx, cx, fma2(c.wy, cy, mul2(c.wz, cz)));
+    const float2 pj = fma2(c.wx, bx, fma2(c.wy, by, mul2(c.wz, bz)));
+    const float2 pk = fma2(cx, bx, fma2(cy, by, mul2(cz, bz)));
+    const float2 xn = mul2(mul2(pj, pk), sb);               // -X
+    const float2 y = mul2(mul2(pi, pk), sc);                //  Y
+    const float2 zn = mul2(mul2(pi, pj), c.sa);             // -Z
+    const float2 cpn = mul2(mul2(zn, pk), mul2(sb, sc));    // -Cp
+    const float2 g = mul2(c.ga, mul2(rb3, rc3));            // 1.5 R^3
+    acc = fma2(g, fma2(f2(-2.0f, -2.0f), cpn, f2(2.0f / 3.0f, 2.0f / 3.0f)), acc);
+    const float2 nh = fma2(f2(5.0f, 5.0f), cpn, f2(-1.0f, -1.0f));   // -H
+    const float2 sg = fma2(add2(xn, zn), f2(-1.0f, -1.0f), y);        //  S
+    wa = fma2(g, fma2(nh, c.qa, fma2(f2(2.0f, 2.0f), zn, sg)), wa);
+    ecs = fma2(g, fma2(nh, qc, fma2(f2(-2.0f, -2.0f), y, sg)), ecs);
+    const float2 eb = mul2(g, fma2(nh, qb, fma2(f2(2.0f, 2.0f), xn, sg)));
+    return eb.x + eb.y;
 }
 
 // Sum over the 16 lanes of a half-warp (xor 8, 4, 2, 1) of 16 values per
@@ -593,7 +603,7 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
 // AtmForceSmem's fc and fb so that a tile (I, J, K) copies the tables of
 // (I, K) and (J, K) into shared memory as they are:
 //   fc form [b][3][16]: pairs (a = t, b) and (a = t + 16, b) in the two
-//       lanes of (u.x, u.y), (u.z, r), (r^3, r^2);
+//       lanes of (w.x, w.y), (w.z, s), (r^3, q);
 //   fb form [b][2][3][16]: pair (a = t + 16 h, b), each value in both lanes;
 // from pair_terms, zero unless a < b < n.  72 KB per block pair.
 constexpr int kFTabFc = R_ * 3 * 16;               // float4 of the fc form (24 KB)
@@ -626,102 +636,156 @@ __global__ void __launch_bounds__(256) k_atm_forcetab(int64_t n, const float *__
             const int64_t gb = (int64_t)B2 * R_ + b, ga = (int64_t)B1 * R_ + a;
             const PairTerms c0 = pair_terms(xs[0][a], xs[1][b], ga < gb && gb < n, eps);
             const PairTerms c1 = pair_terms(xs[0][a + 16], xs[1][b], ga + 16 < gb && gb < n, eps);
-            fc[(3 * b + 0) * 16 + a] = make_float4(c0.ux, c1.ux, c0.uy, c1.uy);
-            fc[(3 * b + 1) * 16 + a] = make_float4(c0.uz, c1.uz, c0.r, c1.r);
-            fc[(3 * b + 2) * 16 + a] = make_float4(c0.r3, c1.r3, c0.r2, c1.r2);
-            fb[((2 * b + 0) * 3 + 0) * 16 + a] = make_float4(c0.ux, c0.ux, c0.uy, c0.uy);
-            fb[((2 * b + 0) * 3 + 1) * 16 + a] = make_float4(c0.uz, c0.uz, c0.r, c0.r);
-            fb[((2 * b + 0) * 3 + 2) * 16 + a] = make_float4(c0.r3, c0.r3, c0.r2, c0.r2);
-            fb[((2 * b + 1) * 3 + 0) * 16 + a] = make_float4(c1.ux, c1.ux, c1.uy, c1.uy);
-            fb[((2 * b + 1) * 3 + 1) * 16 + a] = make_float4(c1.uz, c1.uz, c1.r, c1.r);
-            fb[((2 * b + 1) * 3 + 2) * 16 + a] = make_float4(c1.r3, c1.r3, c1.r2, c1.r2);
+            fc[(3 * b + 0) * 16 + a] = make_float4(c0.wx, c1.wx, c0.wy, c1.wy);
+            fc[(3 * b + 1) * 16 + a] = make_float4(c0.wz, c1.wz, c0.s, c1.s);
+            fc[(3 * b + 2) * 16 + a] = make_float4(c0.r3, c1.r3, c0.q, c1.q);
+            fb[((2 * b + 0) * 3 + 0) * 16 + a] = make_float4(c0.wx, c0.wx, c0.wy, c0.wy);
+            fb[((2 * b + 0) * 3 + 1) * 16 + a] = make_float4(c0.wz, c0.wz, c0.s, c0.s);
+            fb[((2 * b + 0) * 3 + 2) * 16 + a] = make_float4(c0.r3, c0.r3, c0.q, c0.q);
+            fb[((2 * b + 1) * 3 + 0) * 16 + a] = make_float4(c1.wx, c1.wx, c1.wy, c1.wy);
+            fb[((2 * b + 1) * 3 + 1) * 16 + a] = make_float4(c1.wz, c1.wz, c1.s, c1.s);
+            fb[((2 * b + 1) * 3 + 2) * 16 + a] = make_float4(c1.r3, c1.r3, c1.q, c1.q);
         }
     }
 }
 
-// TAB: the tile's (i, k) and (j, k) tables arrive by two bulk copies from
-// the force tables of k_atm_forcetab (tab) instead of being built per tile.
+// The tiles of a persistent block, handed out dynamically: one thread takes
+// the next grid block from a counter shared by all blocks of the launch
+// (atomicAdd) and splits it into its tiles (up to two; blocks outside the
+// simplex give none).  Grid blocks go out in the order the one-block-per-tile
+// launches use (x fastest, then y, then z with the layers reversed), so the
+// work is balanced to the last tile whatever each block's share of idle grid
+// blocks.  The walk state lives in shared memory.
+template <int MAP>
+__device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p, int nb,
+                          AtmForceSmem &S, int slot) {
+    const int64_t gxy = (int64_t)gx * gy, total = gxy * gz;
+    long long w = S.walk_w;
+    int sub = S.walk_sub;
+    int *out = S.tq[slot];
+    for (;;) {
+        if (w >= 0 && w < total) {
+            const int64_t z = w / gxy, rem = w - z * gxy;
+            const int64_t y = rem / gx;
+            const List3 L = decode3<MAP>((uint32_t)(rem - y * gx), (uint32_t)y, (uint32_t)(gz - 1 - z), p, nb);
+            if (sub < L.cnt) {
+                int I, J, K;
+                block_of(L, sub, I, J, K);
+                out[0] = I; out[1] = J; out[2] = K; out[3] = 1;
+                S.walk_w = w;
+                S.walk_sub = sub + 1;
+                return;
+            }
+        }
+        w = (long long)atomicAdd(ctr, 1ull);
+        sub = 0;
+        if (w >= total) {
+            out[3] = 0;
+            S.walk_w = w;
+            S.walk_sub = 0;
+            return;
+        }
+    }
+}
+
+// The pair constants of the thread's pairs (i = ti, ti + 16; j = tj + 16 q)
+// from the fc form of the (I, J) force table (both i-slots in the two lanes).
+__device__ __forceinline__ void load_pair_consts(const float4 *__restrict__ tab, int I, int J, int ti,
+                                                 int tj, PairPack (&pc)[2]) {
+    const float4 *tij = tab + pair_slot(I, J) * kFTabPair + ti;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float4 *e = tij + 3 * (tj + 16 * q) * 16;
+        const float4 C0 = __ldg(e), C1 = __ldg(e + 16), C2 = __ldg(e + 32);
+        pc[q].wx = f2(C0.x, C0.y); pc[q].wy = f2(C0.z, C0.w); pc[q].wz = f2(C1.x, C1.y);
+        pc[q].sa = f2(C1.z, C1.w); pc[q].ga = f2(1.5f * C2.x, 1.5f * C2.y); pc[q].qa = f2(C2.z, C2.w);
+    }
+}
+
+// Persistent energy-and-forces kernel: each block walks tiles (32^3 triples)
+// of the map's grid with stride gridDim.x.  Per tile: wait for its (i, k) and
+// (j, k) tables (TAB: two bulk copies of the force tables of
+// k_atm_forcetab issued during the previous tile; else built here from the
+// points), the packed triple loop (per thread 2 x 2 pairs (i, j), 32 k)
+// forming the energy and the side coefficients, the (j, k) sides reduced by
+// a half-warp reduce-scatter and the (i, k) sides by one xor-16 exchange and
+// shared atomics; then, while the next tile's tables, points and pair
+// constants load, the forces of the tile's 96 atoms, grad_p = 2 sum_q w_pq
+// (x_p - x_q), added once per tile and atom by FP64 atomics.  The
+// coefficient matrices and point tiles are double-buffered, so a tile costs
+// two block barriers.  One FP64 energy partial per block.
 template <int MAP, bool TAB>
 __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *__restrict__ x,
-                                                       float nu, float eps, int nb, int p,
-                                                       const float4 *__restrict__ tab,
+                                                       float nu, float eps, int nb, int gx, int gy,
+                                                       int gz, int p, const float4 *__restrict__ tab,
+                                                       unsigned long long *__restrict__ ctr,
                                                        double *__restrict__ partials,
                                                        double *__restrict__ forces) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AtmForceSmem &S = *reinterpret_cast<AtmForceSmem *>(smem_raw);
     __shared__ float red[16];
-    const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, gridDim.z - 1 - blockIdx.z, p, nb);
-    if (L.cnt == 0) {   // a block outside the simplex exits at once
-        if (partials && threadIdx.x == 0)
-            partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
-        return;
-    }
     const int tid = threadIdx.x, ti = tid & 15, tj = tid >> 4, lane = tid & 31;
     const uint32_t bar = umma::smem_u32(&S.bar);
-    if (TAB) {
-        if (tid == 0) {
-            umma::mbar_init(bar, 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
+    if (TAB && tid == 0) {
+        umma::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    bool bad = false;   // a wait of this thread ran out (the block's energy is then NaN)
+    if (tid == 0) {
+        S.walk_w = -1;
+        S.walk_sub = 0;
+        grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, 0);
+        grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, 1);
+    }
+    bool bad = false;   // a bounded wait ran out (block-uniform after each tile)
     float hi = 0.f, lo = 0.f;
+    PairPack pc[2];
+    __syncthreads();
+    int I = S.tq[0][0], J = S.tq[0][1], K = S.tq[0][2];
+    bool have = S.tq[0][3] != 0;
+    // the first tile's tables, points and pair constants
+    auto issue_tables = [&](int Ii, int Ji, int Ki) {
+        umma::mbar_expect_tx(bar, (uint32_t)(kFTabPair * 16));
+        umma::bulk_load(umma::smem_u32(&S.fc[0][0][0]), tab + pair_slot(Ii, Ki) * kFTabPair, kFTabFc * 16, bar);
+        umma::bulk_load(umma::smem_u32(&S.fb[0][0][0][0]), tab + pair_slot(Ji, Ki) * kFTabPair + kFTabFc,
+                        kFTabFb * 16, bar);
+    };
+    if (have) {
+        if (TAB && tid == 0) issue_tables(I, J, K);
+        load_tiles(x, n, I, J, K, S.xs[0]);
+        for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0][0])[e] = 0.0f;
+        if (TAB) load_pair_consts(tab, I, J, ti, tj, pc);
+    }
+    uint32_t t = 0;
 #pragma unroll 1
-    for (int t = 0; t < L.cnt; ++t) {
-        int I, J, K;
-        block_of(L, t, I, J, K);
-        if (t) __syncthreads();
-        if (TAB && tid == 0 && !bad) {
-            umma::mbar_expect_tx(bar, (uint32_t)(kFTabPair * 16));
-            umma::bulk_load(umma::smem_u32(&S.fc[0][0][0]), tab + pair_slot(I, K) * kFTabPair,
-                            kFTabFc * 16, bar);
-            umma::bulk_load(umma::smem_u32(&S.fb[0][0][0][0]), tab + pair_slot(J, K) * kFTabPair + kFTabFc,
-                            kFTabFb * 16, bar);
-        }
-        load_tiles(x, n, I, J, K, S.xs);
-        for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0])[e] = 0.0f;
-        __syncthreads();
-        if (!TAB) build_force_tables(n, I, J, K, eps, S);
-        PairPack pc[2];
-        if (TAB) {
-            // the pairs (i = ti, ti + 16; j = tj + 16 q) from the fc form of the
-            // (I, J) force table: both i-slots in the two lanes, as used here
-            const float4 *tij = tab + pair_slot(I, J) * kFTabPair + ti;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float4 *e = tij + 3 * (tj + 16 * q) * 16;
-                const float4 C0 = __ldg(e), C1 = __ldg(e + 16), C2 = __ldg(e + 32);
-                pc[q].ux = f2(C0.x, C0.y); pc[q].uy = f2(C0.z, C0.w); pc[q].uz = f2(C1.x, C1.y);
-                pc[q].ra = f2(C1.z, C1.w); pc[q].ra3 = f2(C2.x, C2.y); pc[q].ra2 = f2(C2.z, C2.w);
-            }
-        } else {
+    while (have) {
+        const int b = (int)(t & 1);
+        __syncthreads();   // this tile's points and zeroed (i, k) sums; the last assembly done
+        if (!TAB) {
+            build_force_tables(n, I, J, K, eps, S.xs[b], S);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int64_t gj = (int64_t)J * R_ + tj + 16 * q;
-                const PairTerms a0 = pair_terms(S.xs[0][ti], S.xs[1][tj + 16 * q],
+                const PairTerms a0 = pair_terms(S.xs[b][0][ti], S.xs[b][1][tj + 16 * q],
                                                 (int64_t)I * R_ + ti < gj && gj < n, eps);
-                const PairTerms a1 = pair_terms(S.xs[0][ti + 16], S.xs[1][tj + 16 * q],
+                const PairTerms a1 = pair_terms(S.xs[b][0][ti + 16], S.xs[b][1][tj + 16 * q],
                                                 (int64_t)I * R_ + ti + 16 < gj && gj < n, eps);
-                pc[q].ux = f2(a0.ux, a1.ux); pc[q].uy = f2(a0.uy, a1.uy); pc[q].uz = f2(a0.uz, a1.uz);
-                pc[q].ra = f2(a0.r, a1.r); pc[q].ra2 = f2(a0.r2, a1.r2); pc[q].ra3 = f2(a0.r3, a1.r3);
+                pc[q].wx = f2(a0.wx, a1.wx); pc[q].wy = f2(a0.wy, a1.wy); pc[q].wz = f2(a0.wz, a1.wz);
+                pc[q].sa = f2(a0.s, a1.s); pc[q].qa = f2(a0.q, a1.q); pc[q].ga = f2(1.5f * a0.r3, 1.5f * a1.r3);
             }
-        }
-        // bounded wait for the tables; a timeout flags the error, drains
-        // (bounded) and lets the block finish with a NaN energy
-        if (TAB && !bad) {
+            __syncthreads();
+        } else if (!bad) {
+            // bounded wait for the tables; a timeout flags the error and drains (bounded)
             const long long t0 = clock64();
-            while (!umma::mbar_try_wait(bar, (uint32_t)t & 1)) {
+            while (!umma::mbar_try_wait(bar, t & 1)) {
                 if (clock64() - t0 > umma::kWaitCycles) {
                     atomicExch(&g_atm_error, 1);
-                    umma::mbar_drain(bar, (uint32_t)t & 1);
+                    umma::mbar_drain(bar, t & 1);
                     bad = true;
                     break;
                 }
             }
         }
-        __syncthreads();
-        float2 acc = f2(0.f, 0.f);
+        float2 acc[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
         float2 wa[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
 #pragma unroll 1
         for (int k0 = 0; k0 < R_; k0 += 8) {
@@ -734,11 +798,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const float4 B0 = S.fb[k][q][0][tj], B1 = S.fb[k][q][1][tj], B2 = S.fb[k][q][2][tj];
-                    float2 ea, eb, ec;
-                    triple_grad2(pc[q], C0, C1, C2, B0, B1, B2, acc, ea, eb, ec);
-                    wa[q] = add2(wa[q], ea);
-                    vb[8 * q + kk] = eb.x + eb.y;          // sum over the two i of this thread
-                    ecs = add2(ecs, ec);                   // sum over the two j of this thread
+                    vb[8 * q + kk] = triple_grad2(pc[q], C0, C1, C2, B0, B1, B2, acc[q], wa[q], ecs);
                 }
                 vc[kk] = ecs.x;
                 vc[8 + kk] = ecs.y;
@@ -746,7 +806,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
             // (j, k) sides: sum over the 16 i of this half-warp; lane ti ends
             // with j = tj + 16 (ti >> 3), k = k0 + (ti & 7)
             const float sb = reduce_scatter16(vb, lane);
-            S.wjk[k0 + (ti & 7)][tj + 16 * (ti >> 3)] = sb;
+            S.wjk[b][k0 + (ti & 7)][tj + 16 * (ti >> 3)] = sb;
             // (i, k) sides: sum over the two tj of this warp (lanes l, l ^ 16),
             // then over the warps by shared atomics
             const bool up = (lane & 16) != 0;
@@ -758,59 +818,91 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
             }
             const int ip = ti + 16 * (up ? 1 : 0);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) atomicAdd(&S.wik[k0 + m][ip], vc[m]);
+            for (int m = 0; m < 8; ++m) atomicAdd(&S.wik[b][k0 + m][ip], vc[m]);
         }
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            S.wij[ti][tj + 16 * q] = wa[q].x;
-            S.wij[ti + 16][tj + 16 * q] = wa[q].y;
+            S.wij[b][ti][tj + 16 * q] = wa[q].x;
+            S.wij[b][ti + 16][tj + 16 * q] = wa[q].y;
         }
-        add_ff(hi, lo, acc.x, 0.f);
-        add_ff(hi, lo, acc.y, 0.f);
-        __syncthreads();
-        // Pair coefficients -> gradient: grad_p += 2 sum_q w_pq (x_p - x_q).
+        add_ff(hi, lo, acc[0].x + acc[1].x, 0.f);
+        add_ff(hi, lo, acc[0].y + acc[1].y, 0.f);
+        // the tile's sums are complete and its tables no longer read
+        bad = __syncthreads_or(bad) != 0;
+        if (bad) break;
+        // the next tile (taken during the previous tile); a loader thread
+        // takes the one after it into the slot this tile's entry held
+        const int *nx = S.tq[(t + 1) & 1];
+        const int In = nx[0], Jn = nx[1], Kn = nx[2];
+        const bool hn = nx[3] != 0;
+        if (hn && tid == 6 * R_) grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, (int)(t & 1));
+        if (hn) {
+            // the next tile's tables (into the free table buffer), points and
+            // zeroed (i, k) sums (into the other buffers), pair constants
+            if (TAB && tid == 0) issue_tables(In, Jn, Kn);
+            if (TAB) load_pair_consts(tab, In, Jn, ti, tj, pc);
+            if (tid >= 6 * R_) {
+                const int e0 = tid - 6 * R_;
+                for (int e = e0; e < 3 * R_; e += 256 - 6 * R_) {
+                    const int which = e / R_, o = e % R_;
+                    const int blk = which == 0 ? In : which == 1 ? Jn : Kn;
+                    const int64_t g = (int64_t)blk * R_ + o;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (g < n) v = make_float4(__ldg(x + 3 * g), __ldg(x + 3 * g + 1), __ldg(x + 3 * g + 2), 0.f);
+                    S.xs[b ^ 1][which][o] = v;
+                }
+                for (int e = e0; e < R_ * (R_ + 1); e += 256 - 6 * R_) (&S.wik[b ^ 1][0][0])[e] = 0.0f;
+            }
+        }
+        // Pair coefficients -> forces of the tile's 96 atoms: atom p (thread
+        // pair 2p, 2p + 1, one per partner block) sums w_pq (x_p - x_q).
         if (tid < 6 * R_) {
             const int atom = tid >> 1, half = tid & 1;
-            float gx = 0.f, gy = 0.f, gz = 0.f;
             const int which = atom / R_, o = atom % R_;
-            const float4 xp = S.xs[which][o];
-            for (int q = 0; q < R_; ++q) {
-                float w;
-                float4 xq;
-                if (which == 0) {
-                    if (half == 0) { w = S.wij[o][q]; xq = S.xs[1][q]; }
-                    else { w = S.wik[q][o]; xq = S.xs[2][q]; }
-                } else if (which == 1) {
-                    if (half == 0) { w = S.wij[q][o]; xq = S.xs[0][q]; }
-                    else { w = S.wjk[q][o]; xq = S.xs[2][q]; }
-                } else {
-                    if (half == 0) { w = S.wjk[o][q]; xq = S.xs[1][q]; }
-                    else { w = S.wik[o][q]; xq = S.xs[0][q]; }
-                }
-                gx = fmaf(w, xp.x - xq.x, gx);
-                gy = fmaf(w, xp.y - xq.y, gy);
-                gz = fmaf(w, xp.z - xq.z, gz);
+            const float *wrow;
+            int stride;
+            const float4 *xq;
+            if (which == 0) {
+                if (half == 0) { wrow = &S.wij[b][o][0]; stride = 1; xq = S.xs[b][1]; }
+                else { wrow = &S.wik[b][0][o]; stride = R_ + 1; xq = S.xs[b][2]; }
+            } else if (which == 1) {
+                if (half == 0) { wrow = &S.wij[b][0][o]; stride = R_ + 1; xq = S.xs[b][0]; }
+                else { wrow = &S.wjk[b][0][o]; stride = R_ + 1; xq = S.xs[b][2]; }
+            } else {
+                if (half == 0) { wrow = &S.wjk[b][o][0]; stride = 1; xq = S.xs[b][1]; }
+                else { wrow = &S.wik[b][o][0]; stride = 1; xq = S.xs[b][0]; }
             }
-            gx += __shfl_xor_sync(0xffffffffu, gx, 1);
-            gy += __shfl_xor_sync(0xffffffffu, gy, 1);
-            gz += __shfl_xor_sync(0xffffffffu, gz, 1);
+            const float4 xp = S.xs[b][which][o];
+            float gx_ = 0.f, gy_ = 0.f, gz_ = 0.f;
+#pragma unroll 8
+            for (int q = 0; q < R_; ++q) {
+                const float w = wrow[q * stride];
+                const float4 v = xq[q];
+                gx_ = fmaf(w, xp.x - v.x, gx_);
+                gy_ = fmaf(w, xp.y - v.y, gy_);
+                gz_ = fmaf(w, xp.z - v.z, gz_);
+            }
+            gx_ += __shfl_xor_sync(0xffffffffu, gx_, 1);
+            gy_ += __shfl_xor_sync(0xffffffffu, gy_, 1);
+            gz_ += __shfl_xor_sync(0xffffffffu, gz_, 1);
             const int blk = which == 0 ? I : which == 1 ? J : K;
             const int64_t g = (int64_t)blk * R_ + o;
             if (half == 0 && g < n) {
                 const double f = -2.0 * (double)nu;
-                atomicAdd(forces + 3 * g, f * gx);
-                atomicAdd(forces + 3 * g + 1, f * gy);
-                atomicAdd(forces + 3 * g + 2, f * gz);
+                atomicAdd(forces + 3 * g, f * gx_);
+                atomicAdd(forces + 3 * g + 1, f * gy_);
+                atomicAdd(forces + 3 * g + 2, f * gz_);
             }
         }
+        I = In; J = Jn; K = Kn;
+        have = hn;
+        ++t;
     }
     if (partials) {
         const bool any_bad = __syncthreads_or(bad) != 0;
         const double s = block_sum_ff<256>(hi, lo, red);
-        if (tid == 0) {
-            const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
-            partials[bid] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)nu * s;
-        }
+        if (tid == 0)
+            partials[blockIdx.x] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)nu * s;
     }
 }
 
@@ -848,6 +940,22 @@ static int smem_optin() {
     return SIMPLEX_OK;
 }
 
+// Blocks of a persistent kernel: as many as are resident on the device at
+// once (occupancy of `kern` with 256 threads and `smem` bytes), at most
+// `work` (the grid blocks to walk).
+template <typename Kern>
+static int persistent_blocks(Kern kern, int smem, int64_t work, int &ctas) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (occ < 1) return SIMPLEX_EUNSUPPORTED;
+    const int64_t c = (int64_t)occ * sms;
+    ctas = (int)(c < work ? c : work);
+    return SIMPLEX_OK;
+}
+
 static int atm_check(int64_t n, int64_t d, const float *x, int map, void *ws, int64_t ws_bytes,
                      Grid &g, int64_t &nb, int64_t extra = 0) {
     if (n < 1 || d != 3 || !x || map < MAP_LAMBDA || map > MAP_LINEAR) return d != 3 && d > 0 ? SIMPLEX_EUNSUPPORTED : SIMPLEX_EINVAL;
@@ -875,10 +983,15 @@ static int64_t force_table_bytes(int64_t nb) {
     return t <= kFTabMaxBytes ? t : 0;
 }
 
+// The forces' workspace: [force tables][the tile counter, 16 bytes][FP64
+// partials (one per block of the persistent grid; room for one per grid
+// block)][reduction slots].
+constexpr int64_t kCounterBytes = 16;
+
 int64_t atm_forces_workspace_bytes(int64_t n, int map) {
     const int64_t nb = (n + R_ - 1) / R_;
     const Grid g = grid3(nb, map);
-    return force_table_bytes(nb) + 8 * (g.gx * g.gy * g.gz + kReduceSlots);
+    return force_table_bytes(nb) + kCounterBytes + 8 * (g.gx * g.gy * g.gz + kReduceSlots);
 }
 
 int64_t atm_energy_workspace_bytes(int64_t n, int map) {
@@ -954,15 +1067,16 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
     Grid g;
     int64_t nb = (n + R_ - 1) / R_;
     const int64_t ftab = n >= 1 ? force_table_bytes(nb) : 0;
-    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb, ftab);
+    int st = atm_check(n, d, x, map, workspace, ws_bytes, g, nb, ftab + kCounterBytes);
     if (st) return st;
     if (!aligned(forces, 8) || (energy && !aligned(energy, 8))) return SIMPLEX_EALIGN;
     cudaStream_t s = (cudaStream_t)stream;
-    // workspace: [force tables][one FP64 partial per grid block][reduction slots]
     const float4 *tab = (const float4 *)workspace;
-    double *partials = energy ? (double *)((char *)workspace + ftab) : nullptr;
+    unsigned long long *ctr = (unsigned long long *)((char *)workspace + ftab);
+    double *partials = energy ? (double *)((char *)workspace + ftab + kCounterBytes) : nullptr;
     const int64_t blocks = g.gx * g.gy * g.gz;
     if ((st = cuda_status(cudaMemsetAsync(forces, 0, sizeof(double) * 3 * (size_t)n, s)))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s)))) return st;
     const int smem = (int)sizeof(AtmForceSmem);
     if ((st = smem_optin())) return st;
     if (ftab) {
@@ -975,20 +1089,33 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
         note_launches(1);
         if ((st = launch_status())) return st;
     }
+    // persistent: as many blocks as are resident at once, each walking the grid
+    int ctas = 0;
+    if (ftab) {
+        if (map == MAP_LAMBDA) st = persistent_blocks(k_atm_forces<MAP_LAMBDA, true>, smem, blocks, ctas);
+        else if (map == MAP_BBOX) st = persistent_blocks(k_atm_forces<MAP_BBOX, true>, smem, blocks, ctas);
+        else st = persistent_blocks(k_atm_forces<MAP_LINEAR, true>, smem, blocks, ctas);
+    } else {
+        if (map == MAP_LAMBDA) st = persistent_blocks(k_atm_forces<MAP_LAMBDA, false>, smem, blocks, ctas);
+        else if (map == MAP_BBOX) st = persistent_blocks(k_atm_forces<MAP_BBOX, false>, smem, blocks, ctas);
+        else st = persistent_blocks(k_atm_forces<MAP_LINEAR, false>, smem, blocks, ctas);
+    }
+    if (st) return st;
+    const int gx = (int)g.gx, gy = (int)g.gy, gz = (int)g.gz;
     prof_begin(s);
     if (ftab) {
-        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, true><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, tab, partials, forces);
-        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, true><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, tab, partials, forces);
-        else k_atm_forces<MAP_LINEAR, true><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, tab, partials, forces);
+        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, tab, ctr, partials, forces);
+        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, tab, ctr, partials, forces);
+        else k_atm_forces<MAP_LINEAR, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, tab, ctr, partials, forces);
     } else {
-        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, false><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, nullptr, partials, forces);
-        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, false><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, nullptr, partials, forces);
-        else k_atm_forces<MAP_LINEAR, false><<<dim_of(g), 256, smem, s>>>(n, x, nu, eps, (int)nb, g.p, nullptr, partials, forces);
+        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, nullptr, ctr, partials, forces);
+        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, nullptr, ctr, partials, forces);
+        else k_atm_forces<MAP_LINEAR, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, nullptr, ctr, partials, forces);
     }
     prof_end(s);
     note_launches(1);
     if ((st = launch_status())) return st;
-    if (energy) return reduce_partials(partials, blocks, partials + blocks, energy, s);
+    if (energy) return reduce_partials(partials, ctas, partials + blocks, energy, s);
     return SIMPLEX_OK;
 }
 

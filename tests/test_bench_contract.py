@@ -36,22 +36,48 @@ def test_reference_arm_line():
 
 
 def test_headline_workload_matches_recipe():
+    """The headline is the largest single-GPU configuration: ATM energy and
+    forces at n = 16384, uniform in a cube of side 20, seed 6."""
     import bench
     import synth
     w = synth.WORKLOADS[bench.WORKLOAD]
     cfg = bench.config_block()
-    assert cfg["n"] == w["n"] == 1024 and w["side"] == 10.0 and w["seed"] == 1
-    assert cfg["triples"] == bench.triples(w["n"]) == 1024 * 1023 * 1022 // 6
+    assert cfg["n"] == w["n"] == 16384 and w["side"] == 20.0 and w["seed"] == 6
+    assert cfg["triples"] == bench.triples(w["n"]) == 16384 * 16383 * 16382 // 6
     x = synth.make_points(bench.WORKLOAD)
-    assert x.shape == (1024, 3) and x.dtype.name == "float32"
-    assert float(x.min()) >= 0.0 and float(x.max()) < 10.0
+    assert x.shape == (16384, 3) and x.dtype.name == "float32"
+    assert float(x.min()) >= 0.0 and float(x.max()) < 20.0
+    rows = bench.headline_cpu_rows(16384, 4)
+    assert len(rows) == 4 and all(5e6 < bench.row_triples(16384, i) < 2e7 for i in rows)
 
 
 @pytest.mark.parametrize("name", ["cover2_n16384", "cover3_n1024", "cover4_n256", "edm_n65536_d64",
-                                  "atm_n4096", "stress_n65536_d64"])
+                                  "atm_n1024", "atm_n4096", "stress_n65536_d64", "cover2_n12000",
+                                  "edm_n49152_d64", "atm_n3000", "atm_n12000"])
 def test_rows_are_registered(name):
     import bench
-    assert name in bench.ROWS and name in bench.ROWS_NAMES
+    assert name in bench.ROWS
+
+
+def test_stated_traffic(tmp_path, monkeypatch):
+    """roofline.traffic comes from a committed ncu summary only while the
+    kernel's source file is the one captured."""
+    import hashlib
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "prof"
+    prof.mkdir()
+    (prof / "k.md").write_text(f"# k\n<!-- bench: source=k.cu sha256={digest} traffic_bytes_per_launch=1.5e9 "
+                               f"scale=captured_at_n=4096 -->\n")
+    monkeypatch.setattr(bench, "PROFILES", str(prof))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    value, note = bench.stated_traffic("k.md")
+    assert value == 1.5e9 and "captured at n=4096" in note
+    src.write_text("kernel v2\n")
+    assert bench.stated_traffic("k.md")[0] is None
+    assert bench.stated_traffic("missing.md")[0] is None
 
 
 def test_edm_error_report(monkeypatch):

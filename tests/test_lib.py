@@ -120,8 +120,9 @@ def test_grid_and_workspace_sizes(L):
     # FP64 partial per grid block and 1024 reduction slots
     assert sx.simplex_workspace_bytes("atm_energy", 1024, 3, "lambda") == nb * (nb + 1) // 2 * 16384 + 8 * (
         sx.simplex_grid_blocks(3, nb, "lambda") + 1024)
-    # forces: their own pair tables (72 KB per block pair), then the partials
-    assert sx.simplex_workspace_bytes("atm_forces", 1024, 3, "lambda") == nb * (nb + 1) // 2 * 73728 + 8 * (
+    # forces: their own pair tables (72 KB per block pair), the 16-byte tile
+    # counter of the persistent kernel, then the partials
+    assert sx.simplex_workspace_bytes("atm_forces", 1024, 3, "lambda") == nb * (nb + 1) // 2 * 73728 + 16 + 8 * (
         sx.simplex_grid_blocks(3, nb, "lambda") + 1024)
     assert sx.simplex_workspace_bytes("map2", 10, 1) == 0
     # loss and gradient in one pass: FP32 tiles need one FP64 partial per grid

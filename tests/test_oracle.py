@@ -664,3 +664,38 @@ def test_stress_moment_identity(oracle):
     Lh, gh = stress_moments(x, y)
     assert Lh == pytest.approx(L, rel=1e-12)
     assert np.allclose(gh, grad, rtol=1e-12, atol=1e-12 * np.abs(grad).max())
+
+
+def test_atm_energy_grad_slice(oracle):
+    """The slice [i_lo, i_hi) of the outer loop: its gradient is the FD
+    gradient of its own energy (a different function of x than the total),
+    and slices partition the total energy and gradient."""
+    x = synth.uniform_cube(14, 3, 2.5, seed=16).astype(np.float64)
+    e, g = oracle.atm_energy_grad_slice(x, 3, 9)
+    h = 1e-5
+    for a in (0, 3, 8, 13):
+        for t in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[a, t] += h
+            xm[a, t] -= h
+            fd = (oracle.atm_energy_grad_slice(xp, 3, 9)[0] - oracle.atm_energy_grad_slice(xm, 3, 9)[0]) / (2 * h)
+            assert fd == pytest.approx(g[a, t], rel=1e-6, abs=1e-9 * np.abs(g).max())
+    e0, g0 = oracle.atm_energy_grad_slice(x, 0, 3)
+    e2, g2 = oracle.atm_energy_grad_slice(x, 9, 14)
+    assert e0 + e + e2 == pytest.approx(oracle.atm_energy(x), rel=1e-12)
+    assert np.allclose(g0 + g + g2, oracle.atm_grad(x), rtol=1e-11, atol=1e-13 * np.abs(g).max())
+
+
+def test_stress_loss_rows(oracle):
+    """Row slices of the loss: the two-point closed form on the one row that
+    holds a pair, and slices that add up to the moment-matrix form of L
+    (O(n d^2), no pairwise loop)."""
+    from helpers import stress_moments
+    x = np.array([[0.0, 1.0], [2.0, -1.0]])
+    y = np.array([[0.5, 0.0], [1.0, 1.0]])
+    assert oracle.stress_loss_rows(x, y, 0, 1) == 0.0
+    assert oracle.stress_loss_rows(x, y, 1, 2) == (8.0 - 1.25) ** 2
+    a = synth.normal(90, 5, seed=17).astype(np.float64)
+    b = synth.perturbed(a, 0.2, seed=18).astype(np.float64)
+    parts = oracle.stress_loss_rows(a, b, 0, 31) + oracle.stress_loss_rows(a, b, 31, 90)
+    assert parts == pytest.approx(stress_moments(a, b)[0], rel=1e-11)
