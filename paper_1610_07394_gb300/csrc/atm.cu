@@ -503,13 +503,16 @@ __device__ __forceinline__ PairTerms pair_terms(float4 from, float4 to, bool val
 // A persistent block walks many tiles: the side-coefficient matrices and the
 // point tiles are double-buffered (tile t uses buffer t & 1) so that the next
 // tile's tables, points and pair constants load while this tile's forces
-// are assembled.
+// are assembled; the (i, k) sums, which the triple loop adds atomically into
+// a zeroed matrix, are triple-buffered (buffer t mod 3), so that the matrix
+// of tile t + 2 is zeroed during tile t and one block barrier per tile
+// orders everything.
 struct AtmForceSmem {
     float4 fc[R_][3][16];
     float4 fb[R_][2][3][16];
     float4 xs[2][3][R_];
     float wjk[2][R_][R_ + 1];   // [k][j]: sum over i of de/db
-    float wik[2][R_][R_ + 1];   // [k][i]: sum over j of de/dc
+    float wik[3][R_][R_ + 1];   // [k][i]: sum over j of de/dc
     float wij[2][R_][R_ + 1];   // [i][j]: sum over k of de/da
     uint64_t bar;               // the tile's force tables landed (table-fed kernel)
     int tq[2][4];               // tiles t and t + 1: (I, J, K, valid), slot t & 1
@@ -652,22 +655,53 @@ __global__ void __launch_bounds__(256) k_atm_forcetab(int64_t n, const float *__
 // The tiles of a persistent block, handed out dynamically: one thread takes
 // the next grid block from a counter shared by all blocks of the launch
 // (atomicAdd) and splits it into its tiles (up to two; blocks outside the
-// simplex give none).  Grid blocks go out in the order the one-block-per-tile
-// launches use (x fastest, then y, then z with the layers reversed), so the
-// work is balanced to the last tile whatever each block's share of idle grid
-// blocks.  The walk state lives in shared memory.
+// simplex give none), so the work is balanced to the last tile whatever each
+// block's share of idle grid blocks.  The walk state lives in shared memory.
+//
+// Order of the hand-out.  A tile (I, J, K) reads the tables of (I, K) and
+// (J, K).  In the map's grid order (x fastest, then y, then z) one of the two
+// changes with every block, and half of the lambda cube (its reflected case,
+// (J, K) = (h + x, h + y)) meets a table again only one whole z-layer later,
+// far beyond the L2.  So where the grid's x and y extents are multiples of 8
+// the counter walks 8 x 8 patches of the (x, y) plane, and within a patch all
+// z-layers (from the top: the J = K plane's layers of two tiles per block go
+// first) before the next patch; within a layer the 64 blocks of the patch.
+// Every (I, K) and (J, K) table is then used about eight times within a
+// patch's span of tiles.  Which grid blocks exist, and the data blocks they
+// map to, are the map's; only the order in which the persistent blocks take
+// them changes.
+__device__ __forceinline__ void handout_block(int64_t c, int gx, int gy, int gz, uint32_t &x, uint32_t &y,
+                                              uint32_t &z) {
+    if ((gx & 7) == 0 && (gy & 7) == 0) {
+        const int64_t per_patch = 64 * (int64_t)gz;
+        const int64_t patch = c / per_patch, r = c - patch * per_patch;
+        const int64_t layer = r >> 6, o = r & 63;
+        const int64_t pgx = gx >> 3, py = patch / pgx, px = patch - py * pgx;
+        x = (uint32_t)(8 * px + (o & 7));
+        y = (uint32_t)(8 * py + (o >> 3));
+        z = (uint32_t)(gz - 1 - layer);
+    } else {
+        const int64_t gxy = (int64_t)gx * gy;
+        const int64_t zz = c / gxy, rem = c - zz * gxy;
+        const int64_t yy = rem / gx;
+        x = (uint32_t)(rem - yy * gx);
+        y = (uint32_t)yy;
+        z = (uint32_t)(gz - 1 - zz);
+    }
+}
+
 template <int MAP>
 __device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p, int nb,
                           AtmForceSmem &S, int slot) {
-    const int64_t gxy = (int64_t)gx * gy, total = gxy * gz;
+    const int64_t total = (int64_t)gx * gy * gz;
     long long w = S.walk_w;
     int sub = S.walk_sub;
     int *out = S.tq[slot];
     for (;;) {
         if (w >= 0 && w < total) {
-            const int64_t z = w / gxy, rem = w - z * gxy;
-            const int64_t y = rem / gx;
-            const List3 L = decode3<MAP>((uint32_t)(rem - y * gx), (uint32_t)y, (uint32_t)(gz - 1 - z), p, nb);
+            uint32_t bx, by, bz;
+            handout_block(w, gx, gy, gz, bx, by, bz);
+            const List3 L = decode3<MAP>(bx, by, bz, p, nb);
             if (sub < L.cnt) {
                 int I, J, K;
                 block_of(L, sub, I, J, K);
@@ -752,15 +786,19 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
     if (have) {
         if (TAB && tid == 0) issue_tables(I, J, K);
         load_tiles(x, n, I, J, K, S.xs[0]);
-        for (int e = tid; e < R_ * (R_ + 1); e += 256) (&S.wik[0][0][0])[e] = 0.0f;
+        for (int e = tid; e < 2 * R_ * (R_ + 1); e += 256) (&S.wik[0][0][0])[e] = 0.0f;
         if (TAB) load_pair_consts(tab, I, J, ti, tj, pc);
     }
+    __syncthreads();   // the first tile's points and the first two zeroed (i, k) matrices
     uint32_t t = 0;
+    int b3 = 0;        // t mod 3
 #pragma unroll 1
     while (have) {
         const int b = (int)(t & 1);
-        __syncthreads();   // this tile's points and zeroed (i, k) sums; the last assembly done
         if (!TAB) {
+            // the points of this tile (loaded during the last tile) are
+            // visible and the last tile's loop is done with the tables
+            __syncthreads();
             build_force_tables(n, I, J, K, eps, S.xs[b], S);
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -818,7 +856,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
             }
             const int ip = ti + 16 * (up ? 1 : 0);
 #pragma unroll
-            for (int m = 0; m < 8; ++m) atomicAdd(&S.wik[b][k0 + m][ip], vc[m]);
+            for (int m = 0; m < 8; ++m) atomicAdd(&S.wik[b3][k0 + m][ip], vc[m]);
         }
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -837,8 +875,8 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         const bool hn = nx[3] != 0;
         if (hn && tid == 6 * R_) grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, (int)(t & 1));
         if (hn) {
-            // the next tile's tables (into the free table buffer), points and
-            // zeroed (i, k) sums (into the other buffers), pair constants
+            // the next tile's tables (into the free table buffer), points
+            // (into the other buffer) and pair constants
             if (TAB && tid == 0) issue_tables(In, Jn, Kn);
             if (TAB) load_pair_consts(tab, In, Jn, ti, tj, pc);
             if (tid >= 6 * R_) {
@@ -851,8 +889,13 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
                     if (g < n) v = make_float4(__ldg(x + 3 * g), __ldg(x + 3 * g + 1), __ldg(x + 3 * g + 2), 0.f);
                     S.xs[b ^ 1][which][o] = v;
                 }
-                for (int e = e0; e < R_ * (R_ + 1); e += 256 - 6 * R_) (&S.wik[b ^ 1][0][0])[e] = 0.0f;
             }
+        }
+        // the (i, k) matrix of tile t + 2 (last read by the assembly of tile
+        // t - 1, which every warp finished before this tile's barrier)
+        if (tid >= 6 * R_) {
+            const int z3 = b3 == 0 ? 2 : b3 - 1;
+            for (int e = tid - 6 * R_; e < R_ * (R_ + 1); e += 256 - 6 * R_) (&S.wik[z3][0][0])[e] = 0.0f;
         }
         // Pair coefficients -> forces of the tile's 96 atoms: atom p (thread
         // pair 2p, 2p + 1, one per partner block) sums w_pq (x_p - x_q).
@@ -864,13 +907,13 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
             const float4 *xq;
             if (which == 0) {
                 if (half == 0) { wrow = &S.wij[b][o][0]; stride = 1; xq = S.xs[b][1]; }
-                else { wrow = &S.wik[b][0][o]; stride = R_ + 1; xq = S.xs[b][2]; }
+                else { wrow = &S.wik[b3][0][o]; stride = R_ + 1; xq = S.xs[b][2]; }
             } else if (which == 1) {
                 if (half == 0) { wrow = &S.wij[b][0][o]; stride = R_ + 1; xq = S.xs[b][0]; }
                 else { wrow = &S.wjk[b][0][o]; stride = R_ + 1; xq = S.xs[b][2]; }
             } else {
                 if (half == 0) { wrow = &S.wjk[b][o][0]; stride = 1; xq = S.xs[b][1]; }
-                else { wrow = &S.wik[b][o][0]; stride = 1; xq = S.xs[b][0]; }
+                else { wrow = &S.wik[b3][o][0]; stride = 1; xq = S.xs[b][0]; }
             }
             const float4 xp = S.xs[b][which][o];
             float gx_ = 0.f, gy_ = 0.f, gz_ = 0.f;
@@ -888,15 +931,16 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
             const int blk = which == 0 ? I : which == 1 ? J : K;
             const int64_t g = (int64_t)blk * R_ + o;
             if (half == 0 && g < n) {
-                const double f = -2.0 * (double)nu;
-                atomicAdd(forces + 3 * g, f * gx_);
-                atomicAdd(forces + 3 * g + 1, f * gy_);
-                atomicAdd(forces + 3 * g + 2, f * gz_);
+                const float f = -2.0f * nu;   // F = -dE/dx, the tile's part in FP32, summed in FP64
+                atomicAdd(forces + 3 * g, (double)(f * gx_));
+                atomicAdd(forces + 3 * g + 1, (double)(f * gy_));
+                atomicAdd(forces + 3 * g + 2, (double)(f * gz_));
             }
         }
         I = In; J = Jn; K = Kn;
         have = hn;
         ++t;
+        b3 = b3 == 2 ? 0 : b3 + 1;
     }
     if (partials) {
         const bool any_bad = __syncthreads_or(bad) != 0;
