@@ -273,58 +273,13 @@ __global__ void __launch_bounds__(256) k_atm_pairtab(int64_t n, const float *__r
 __device__ int g_atm_error;   // set when a bounded wait of the energy kernel runs out
 
 // A tile's two tables: ik = table of (I, K) (a = i, b = k), jk = table of
-// (J, K) (a = j, b = k).  A warp's 16 distinct ti read 256 contiguous bytes
-// of ik (two wavefronts, no bank conflict); its two tj read two addresses of
-// jk (one broadcast wavefront).
+// (J, K) (a = j, b = k).  A warp of k_atm_energy_tab reads 8 distinct i of ik
+// (128 contiguous bytes) and 4 distinct j of jk per load: no bank conflict.
 struct AtmEnergyTabSmem {
     float4 ik[R_ / 2][2][R_];
     float4 jk[R_ / 2][2][R_];
     uint64_t bar;
 };
-
-// Steps h in [h0, h1) of the packed triple loop of k_atm_energy_tab (two
-// consecutive k per step) for the thread's pairs (i, j) = (ti + 16p, tj + 16q):
-// (0,0) and (1,0) always, (0,1) and (1,1) when Q1.  Pairs in the order
-// (0,0) (0,1) (1,1) (1,0): three of the four loaded (i, k) / (j, k) values
-// are live at a time.  The bounds are uniform over a warp.
-template <bool Q1>
-__device__ __forceinline__ void energy_tab_steps(const AtmEnergyTabSmem &S, int ti, int tj, int h0,
-                                                 int h1, const float2 (&vij)[2][2][3],
-                                                 float2 (&s0)[2][2], float2 (&s1)[2][2]) {
-#pragma unroll 2
-    for (int h = h0; h < h1; ++h) {
-        const float4 C00 = S.ik[h][0][ti], C01 = S.ik[h][1][ti];
-        const float4 B00 = S.jk[h][0][tj], B01 = S.jk[h][1][tj];
-        triple_energy2s(vij[0][0], C00, C01, B00, B01, s0[0][0], s1[0][0]);
-        if (Q1) {
-            const float4 B10 = S.jk[h][0][tj + 16], B11 = S.jk[h][1][tj + 16];
-            triple_energy2s(vij[0][1], C00, C01, B10, B11, s0[0][1], s1[0][1]);
-            const float4 C10 = S.ik[h][0][ti + 16], C11 = S.ik[h][1][ti + 16];
-            triple_energy2s(vij[1][1], C10, C11, B10, B11, s0[1][1], s1[1][1]);
-            triple_energy2s(vij[1][0], C10, C11, B00, B01, s0[1][0], s1[1][0]);
-        } else {
-            const float4 C10 = S.ik[h][0][ti + 16], C11 = S.ik[h][1][ti + 16];
-            triple_energy2s(vij[1][0], C10, C11, B00, B01, s0[1][0], s1[1][0]);
-        }
-    }
-}
-
-// The same loop for a tile with I = J, whose pairs i < j are the thread's
-// two pairs a and b (any i, j of the tile each): steps [ha, h1) for pair a,
-// [hb, h1) for pair b (ha >= hb), each step loading that pair's own values.
-__device__ __forceinline__ void energy_tab_steps2(const AtmEnergyTabSmem &S, int hb, int ha, int h1,
-                                                  int ia, int ja, const float2 (&va)[3], float2 &s0a,
-                                                  float2 &s1a, int ib, int jb, const float2 (&vb)[3],
-                                                  float2 &s0b, float2 &s1b) {
-#pragma unroll 2
-    for (int h = hb; h < ha; ++h)
-        triple_energy2s(vb, S.ik[h][0][ib], S.ik[h][1][ib], S.jk[h][0][jb], S.jk[h][1][jb], s0b, s1b);
-#pragma unroll 2
-    for (int h = ha; h < h1; ++h) {
-        triple_energy2s(vb, S.ik[h][0][ib], S.ik[h][1][ib], S.jk[h][0][jb], S.jk[h][1][jb], s0b, s1b);
-        triple_energy2s(va, S.ik[h][0][ia], S.ik[h][1][ia], S.jk[h][0][ja], S.jk[h][1][ja], s0a, s1a);
-    }
-}
 
 // v_ij of the pair (i, j) of a tile in both lanes, from the (I, J) table
 // (entry a = i, lane j & 1 of the step holding b = j).
@@ -359,30 +314,37 @@ __device__ __forceinline__ void wait_tables(uint32_t bar, uint32_t parity, bool 
     }
 }
 
-// The energy kernel fed by the pair tables: per tile, one thread starts two
-// bulk copies (2 x 16 KB) into shared memory, every thread reads its pair
-// constants (v_ij, r_ij^3) from the (I, J) table meanwhile, then a packed
-// triple loop over the scaled vectors (triple_energy2s) whose two lanes are
-// two consecutive k: the (i, k) and (j, k) values are loaded as packed
-// pairs, the pair constants of (i, j) are the same in both lanes, and each
-// thread's 2 x 2 pairs (i, j) reuse every load twice.
-// Three blocks per SM (80 registers, no spills): four at 64 registers
-// spilled around the k loop and ran 1% slower, the FMA pipe being the first
-// stall either way.
+// The energy kernel fed by the pair tables, register-blocked.  Per tile, one
+// thread starts two bulk copies (2 x 16 KB) of the (I, K) and (J, K) tables
+// into shared memory and every thread reads its pair constants (v_ij, r_ij^3)
+// from the (I, J) table meanwhile; then a packed triple loop over the scaled
+// vectors (triple_energy2s) whose two lanes are two consecutive k.  128
+// threads per tile, thread (ti, tj) = (t mod 8, t / 8) owns the 4 x 2 pairs
+// (i, j) = (ti + 8 p, tj + 16 q), and per step (two consecutive k) loads
+// the four (i, k) and the two (j, k) table entries: 12 shared loads of
+// 128 bits for 16 triples, where 2 x 2 pairs per thread take 8 for 8.  A
+// 128-bit shared load costs four wavefronts however many lanes share an
+// address, so that ratio sets the shared-memory time per triple, which in
+// the 2 x 2 layout exceeded the FP32 pipe's (32 wavefronts against 96 FMA
+// cycles per scheduler and step, four schedulers sharing the one
+// shared-memory pipe).  Tiles on a diagonal plane run the same loop (their
+// tables are zero outside i < j < k; skipping their empty steps, as the 2 x 2
+// layout did, changed nothing here).  Four blocks per SM (120 registers): at
+// n = 1024 the kernel takes 0.0944 ms against 0.0979 ms with 2 x 2 pairs per
+// thread and 256 threads, at n = 4096 2.22e12 triples/s against 2.12e12.
 template <int MAP>
-__global__ void __launch_bounds__(256, 3) k_atm_energy_tab(const float4 *__restrict__ tab, float nu,
-                                                           int nb, int p,
-                                                           double *__restrict__ partials) {
+__global__ void __launch_bounds__(128, 4) k_atm_energy_tab(const float4 *__restrict__ tab, float nu, int nb,
+                                                           int p, double *__restrict__ partials) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AtmEnergyTabSmem &S = *reinterpret_cast<AtmEnergyTabSmem *>(smem_raw);
-    __shared__ float red[16];
+    __shared__ float red[8];
     const List3 L = decode3<MAP>(blockIdx.x, blockIdx.y, gridDim.z - 1 - blockIdx.z, p, nb);
+    const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
     if (L.cnt == 0) {   // a block outside the simplex exits at once
-        if (threadIdx.x == 0)
-            partials[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = 0.0;
+        if (threadIdx.x == 0) partials[bid] = 0.0;
         return;
     }
-    const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+    const int ti = threadIdx.x & 7, tj = threadIdx.x >> 3;
     const uint32_t bar = umma::smem_u32(&S.bar);
     if (threadIdx.x == 0) {
         umma::mbar_init(bar, 1);
@@ -390,7 +352,7 @@ __global__ void __launch_bounds__(256, 3) k_atm_energy_tab(const float4 *__restr
     }
     __syncthreads();
     float hi = 0.f, lo = 0.f;
-    bool bad = false;   // a wait of this thread ran out (the block's result is then NaN)
+    bool bad = false;
 #pragma unroll 1
     for (int t = 0; t < L.cnt; ++t) {
         int I, J, K;
@@ -404,63 +366,39 @@ __global__ void __launch_bounds__(256, 3) k_atm_energy_tab(const float4 *__restr
                             kTabPair * 16, bar);
         }
         const float4 *tij = tab + pair_slot(I, J) * kTabPair;
-        // Tiles on a diagonal plane skip what lies outside i < j < k (the
-        // tables are zero there, so the sums are unchanged).  J = K: the pairs
-        // j in {2w, 2w + 1} of warp w meet a k > j only from step w on, the
-        // pairs j + 16 from step w + 8.  I = J: of the 32 x 32 pairs only
-        // i < j count, so each thread takes two of them, (ti, tj + 16) and
-        // (ti, tj) when ti < tj, else (tj + 16, ti + 16) (ti = tj: a zero
-        // pair), instead of four.
-        const int w = tj >> 1;
-        const bool jk_diag = J == K;
-        if (I != J) {
-            // pair constants of (i, j) = (ti + 16p, tj + 16q): v_ij in both
-            // lanes (r_ij^3 is read again after the loop, to spare registers)
-            float2 vij[2][2][3];
+        float2 vij[4][2][3];
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
+        for (int pp = 0; pp < 4; ++pp)
 #pragma unroll
-                for (int pp = 0; pp < 2; ++pp) pair_const(tij, ti + 16 * pp, tj + 16 * q, vij[pp][q]);
-            wait_tables(bar, (uint32_t)t & 1, bad);
-            float2 s0[2][2], s1[2][2];
+            for (int q = 0; q < 2; ++q) pair_const(tij, ti + 8 * pp, tj + 16 * q, vij[pp][q]);
+        wait_tables(bar, (uint32_t)t & 1, bad);
+        float2 s0[4][2], s1[4][2];
 #pragma unroll
-            for (int pp = 0; pp < 2; ++pp)
+        for (int pp = 0; pp < 4; ++pp)
 #pragma unroll
-                for (int q = 0; q < 2; ++q) s0[pp][q] = s1[pp][q] = make_float2(0.f, 0.f);
-            if (!jk_diag) {
-                energy_tab_steps<true>(S, ti, tj, 0, R_ / 2, vij, s0, s1);
-            } else {
-                energy_tab_steps<false>(S, ti, tj, w, w + R_ / 4, vij, s0, s1);
-                energy_tab_steps<true>(S, ti, tj, w + R_ / 4, R_ / 2, vij, s0, s1);
+            for (int q = 0; q < 2; ++q) s0[pp][q] = s1[pp][q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int h = 0; h < R_ / 2; ++h) {
+            const float4 B00 = S.jk[h][0][tj], B01 = S.jk[h][1][tj];
+            const float4 B10 = S.jk[h][0][tj + 16], B11 = S.jk[h][1][tj + 16];
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const float4 C0 = S.ik[h][0][ti + 8 * pp], C1 = S.ik[h][1][ti + 8 * pp];
+                triple_energy2s(vij[pp][0], C0, C1, B00, B01, s0[pp][0], s1[pp][0]);
+                triple_energy2s(vij[pp][1], C0, C1, B10, B11, s0[pp][1], s1[pp][1]);
             }
-#pragma unroll
-            for (int pp = 0; pp < 2; ++pp)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float ra3 = pair_r3(tij, ti + 16 * pp, tj + 16 * q);
-                    add_ff(hi, lo, fmaf(ra3, s0[pp][q].x + s0[pp][q].y, -3.0f * (s1[pp][q].x + s1[pp][q].y)),
-                           0.f);
-                }
-        } else {
-            const int ia = ti, ja = tj + 16;
-            const int ib = ti <= tj ? ti : tj + 16, jb = ti <= tj ? tj : ti + 16;
-            float2 va[3], vb[3];
-            pair_const(tij, ia, ja, va);
-            pair_const(tij, ib, jb, vb);
-            wait_tables(bar, (uint32_t)t & 1, bad);
-            float2 s0a = make_float2(0.f, 0.f), s1a = s0a, s0b = s0a, s1b = s0a;
-            if (!jk_diag) energy_tab_steps2(S, 0, 0, R_ / 2, ia, ja, va, s0a, s1a, ib, jb, vb, s0b, s1b);
-            else energy_tab_steps2(S, w, w + R_ / 4, R_ / 2, ia, ja, va, s0a, s1a, ib, jb, vb, s0b, s1b);
-            add_ff(hi, lo, fmaf(pair_r3(tij, ia, ja), s0a.x + s0a.y, -3.0f * (s1a.x + s1a.y)), 0.f);
-            add_ff(hi, lo, fmaf(pair_r3(tij, ib, jb), s0b.x + s0b.y, -3.0f * (s1b.x + s1b.y)), 0.f);
         }
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float ra3 = pair_r3(tij, ti + 8 * pp, tj + 16 * q);
+                add_ff(hi, lo, fmaf(ra3, s0[pp][q].x + s0[pp][q].y, -3.0f * (s1[pp][q].x + s1[pp][q].y)), 0.f);
+            }
     }
     const bool any_bad = __syncthreads_or(bad) != 0;
-    const double s = block_sum_ff<256>(hi, lo, red);
-    if (threadIdx.x == 0) {
-        const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
-        partials[bid] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)nu * s;
-    }
+    const double s = block_sum_ff<128>(hi, lo, red);
+    if (threadIdx.x == 0) partials[bid] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)nu * s;
 }
 
 // ---------------------------------------------------------------- forces
@@ -1090,9 +1028,9 @@ extern "C" int simplex_atm_energy(int64_t n, int64_t d, const float *x, float nu
     }
     prof_begin(s);
     if (tab_bytes) {
-        if (map == MAP_LAMBDA) k_atm_energy_tab<MAP_LAMBDA><<<dim_of(g), 256, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
-        else if (map == MAP_BBOX) k_atm_energy_tab<MAP_BBOX><<<dim_of(g), 256, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
-        else k_atm_energy_tab<MAP_LINEAR><<<dim_of(g), 256, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
+        if (map == MAP_LAMBDA) k_atm_energy_tab<MAP_LAMBDA><<<dim_of(g), 128, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
+        else if (map == MAP_BBOX) k_atm_energy_tab<MAP_BBOX><<<dim_of(g), 128, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
+        else k_atm_energy_tab<MAP_LINEAR><<<dim_of(g), 128, kEnergyTabSmem, s>>>(tab, nu, (int)nb, g.p, partials);
     } else {
         if (map == MAP_LAMBDA) k_atm_energy<MAP_LAMBDA><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
         else if (map == MAP_BBOX) k_atm_energy<MAP_BBOX><<<dim_of(g), 256, kEnergySmem, s>>>(n, x, nu, eps, (int)nb, g.p, partials);
