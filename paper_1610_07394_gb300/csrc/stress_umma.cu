@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
                       const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
                       int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
-                      double *__restrict__ partials) {
+                      double *__restrict__ partials, int qshift) {
     using Walk = ChunkWalk<MAP>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -308,8 +308,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!(ok = ring_acquire<NS>(ctl, s_stages, it, STAGE_BYTES, dst, bar, fail))) break;
                     tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
                     tma_load_2d(dst + TILE_BYTES, &mPl, c * KC, Y * TM, bar);
-                    tma_load_2d(dst + 2 * TILE_BYTES, &mQh, c * KC, X * TN, bar);
-                    tma_load_2d(dst + 3 * TILE_BYTES, &mQl, c * KC, X * TN, bar);
+                    const int qx = (c * KC + qshift) % (2 * d);   // Q chunk c (qshift: Q read from P)
+                    tma_load_2d(dst + 2 * TILE_BYTES, &mQh, qx, X * TN, bar);
+                    tma_load_2d(dst + 3 * TILE_BYTES, &mQl, qx, X * TN, bar);
                 }
                 if (ok && have) {
                     // GEMM2 operands of the previous tile: X^T of its columns, then of its rows
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_stress_umma_fwd(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
                     const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                     const float *__restrict__ a, int64_t n, int d, int nb, int nb2, int gx,
-                    int64_t total, double *__restrict__ partials) {
+                    int64_t total, double *__restrict__ partials, int qshift) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -643,8 +644,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tma_load_2d(dst, &mPh, c * KC, Y * TM, bar);
                     tma_load_2d(dst + A_BYTES, &mPl, c * KC, Y * TM, bar);
                     // this CTA's column block, rows 128 r .. 128 r + 127 of both CTAs' B
-                    tma_load_2d_mc(dst + 2 * A_BYTES + rank * TILE_BYTES, &mQh, c * KC, Xr * TN, bar, 3);
-                    tma_load_2d_mc(dst + 2 * A_BYTES + B_BYTES + rank * TILE_BYTES, &mQl, c * KC, Xr * TN,
+                    const int qx = (c * KC + qshift) % (2 * d);   // Q chunk c (qshift: Q read from P)
+                    tma_load_2d_mc(dst + 2 * A_BYTES + rank * TILE_BYTES, &mQh, qx, Xr * TN, bar, 3);
+                    tma_load_2d_mc(dst + 2 * A_BYTES + B_BYTES + rank * TILE_BYTES, &mQl, qx, Xr * TN,
                                    bar, 3);
                     ++it;
                 }
@@ -772,8 +774,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace f256
 
-// P = [S | Delta], Q = [Delta | S] (BF16 hi, lo; rows of 2d), a = S . Delta in
-// FP32, and for the backward pass X^T hi, lo (rows t < d: coordinates; row d:
+// P = [S | Delta], Q = [Delta | S] (BF16 hi, lo; rows of 2d; Q only when
+// Qh is given), a = S . Delta in FP32, and for the backward pass X^T hi, lo (rows t < d: coordinates; row d:
 // ones; rows d+1 .. NG-1: zeros; row pitch `pitch`).  32 points per block.
 __global__ void __launch_bounds__(256) k_stress_prep(const float *__restrict__ x,
                                                      const float *__restrict__ y, int64_t n, int d,
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(256) k_stress_prep(const float *__restrict__ x
             const __nv_bfloat16 dl = __float2bfloat16_rn(D - __bfloat162float(dh));
             const int64_t o = i * 2 * d + t;
             Ph[o] = sh; Pl[o] = sl; Ph[o + d] = dh; Pl[o + d] = dl;
-            Qh[o] = dh; Ql[o] = dl; Qh[o + d] = sh; Ql[o + d] = sl;
+            if (Qh) { Qh[o] = dh; Ql[o] = dl; Qh[o + d] = sh; Ql[o + d] = sl; }
             acc = fmaf(S, D, acc);
             xs[p][t] = xv;
         }
@@ -875,25 +877,26 @@ static int smem_optin() {
 
 static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
                               const float *a, int64_t n, int d, int nb, int gx, int64_t total, int chunk,
-                              float scale4, float *grad, double *partials) {
+                              float scale4, float *grad, double *partials, int qshift) {
     if (map == MAP_LAMBDA)
         k_stress_umma_bwd<MAP_LAMBDA><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
     else if (map == MAP_BBOX)
         k_stress_umma_bwd<MAP_BBOX><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
     else if (map == MAP_RB)
         k_stress_umma_bwd<MAP_RB><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
     else
         k_stress_umma_bwd<MAP_LINEAR><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
     return cudaGetLastError();
 }
 
 // The forward runs as two-CTA clusters in 128 x 256 steps.
 static cudaError_t launch_fwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *a,
-                              int64_t n, int d, int nb, int nb2, int gx, int64_t total, double *partials) {
+                              int64_t n, int d, int nb, int nb2, int gx, int64_t total, double *partials,
+                              int qshift) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kThreads);
@@ -908,15 +911,15 @@ static cudaError_t launch_fwd(int map, unsigned ctas, cudaStream_t s, const CUte
     cfg.numAttrs = 1;
     if (map == MAP_LAMBDA)
         return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_LAMBDA>, m[0], m[1], m[2], m[3], a, n, d, nb,
-                                  nb2, gx, total, partials);
+                                  nb2, gx, total, partials, qshift);
     if (map == MAP_BBOX)
         return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_BBOX>, m[0], m[1], m[2], m[3], a, n, d, nb,
-                                  nb2, gx, total, partials);
+                                  nb2, gx, total, partials, qshift);
     if (map == MAP_RB)
         return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_RB>, m[0], m[1], m[2], m[3], a, n, d, nb,
-                                  nb2, gx, total, partials);
+                                  nb2, gx, total, partials, qshift);
     return cudaLaunchKernelEx(&cfg, f256::k_stress_umma_fwd<MAP_LINEAR>, m[0], m[1], m[2], m[3], a, n, d, nb,
-                              nb2, gx, total, partials);
+                              nb2, gx, total, partials, qshift);
 }
 
 // Two-CTA clusters of the forward kernel that fit on the device at once (one
@@ -980,12 +983,23 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     float *a = reinterpret_cast<float *>(w + L.a);
     double *partials = reinterpret_cast<double *>(w + L.part);
     const int NG = (int)d + 16;
+    // Q = [Delta | S] is P = [S | Delta] with its two halves swapped: where d
+    // is a multiple of the K chunk, Q's chunk c is P's chunk at column
+    // (64 c + d) mod 2d, so the kernels read Q's tiles from P's memory (one
+    // operand copy fewer to write and to keep in L2); otherwise Q is written.
+    const bool qview = d % KC == 0;
+    const int qshift = qview ? (int)d : 0;
     CUtensorMap m[6];
     if (!make_map_bf16(&m[0], bf(L.Ph), n, 2 * d, 2 * d, TM) ||
-        !make_map_bf16(&m[1], bf(L.Pl), n, 2 * d, 2 * d, TM) ||
-        !make_map_bf16(&m[2], bf(L.Qh), n, 2 * d, 2 * d, TM) ||
-        !make_map_bf16(&m[3], bf(L.Ql), n, 2 * d, 2 * d, TM))
+        !make_map_bf16(&m[1], bf(L.Pl), n, 2 * d, 2 * d, TM))
         return SIMPLEX_ECUDA;
+    if (qview) {
+        m[2] = m[0];
+        m[3] = m[1];
+    } else if (!make_map_bf16(&m[2], bf(L.Qh), n, 2 * d, 2 * d, TM) ||
+               !make_map_bf16(&m[3], bf(L.Ql), n, 2 * d, 2 * d, TM)) {
+        return SIMPLEX_ECUDA;
+    }
     if (bwd) {
         if (!make_map_bf16(&m[4], bf(L.Th), NG, n, L.pitch, NG) ||
             !make_map_bf16(&m[5], bf(L.Tl), NG, n, L.pitch, NG))
@@ -997,7 +1011,7 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     int st = smem_optin();
     if (st) return st;
     k_stress_prep<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(
-        x, y, n, (int)d, NG, L.pitch, bf(L.Ph), bf(L.Pl), bf(L.Qh), bf(L.Ql),
+        x, y, n, (int)d, NG, L.pitch, bf(L.Ph), bf(L.Pl), qview ? nullptr : bf(L.Qh), qview ? nullptr : bf(L.Ql),
         bwd ? bf(L.Th) : nullptr, bwd ? bf(L.Tl) : nullptr, a);
     note_launches(1);
     if ((st = launch_status())) return st;
@@ -1017,7 +1031,7 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
         if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
         prof_begin(s);
         le = launch_bwd(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
-                        (float)(4.0 * gscale), grad, loss ? partials : nullptr);
+                        (float)(4.0 * gscale), grad, loss ? partials : nullptr, qshift);
     } else {
         // two-CTA clusters over the map's grid of 256 x 256 super-blocks
         const int64_t nb2 = (nb + 1) / 2;
@@ -1030,7 +1044,7 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
         ctas = 2 * clusters;
         prof_begin(s);
         le = launch_fwd(map, (unsigned)ctas, s, m, a, n, (int)d, (int)nb, (int)nb2, (int)g2.gx, total2,
-                        partials);
+                        partials, qshift);
     }
     prof_end(s);
     note_launches(1);
