@@ -455,7 +455,8 @@ struct AtmForceSmem {
     uint64_t bar;               // the tile's force tables landed (table-fed kernel)
     int tq[2][4];               // tiles t and t + 1: (I, J, K, valid), slot t & 1
     long long walk_w;           // the grid block being split into tiles
-    int walk_sub;               // its next tile
+    long long walk_end;         // end of the run of grid blocks the block has claimed
+    int walk_sub;               // the next tile of walk_w
 };
 
 __device__ __forceinline__ void build_force_tables(int64_t n, int I, int J, int K, float eps,
@@ -590,11 +591,16 @@ __global__ void __launch_bounds__(256) k_atm_forcetab(int64_t n, const float *__
     }
 }
 
-// The tiles of a persistent block, handed out dynamically: one thread takes
-// the next grid block from a counter shared by all blocks of the launch
-// (atomicAdd) and splits it into its tiles (up to two; blocks outside the
-// simplex give none), so the work is balanced to the last tile whatever each
-// block's share of idle grid blocks.  The walk state lives in shared memory.
+// The tiles of a persistent block, handed out dynamically: one thread claims
+// the next run of `claim` grid blocks from a counter shared by all blocks of
+// the launch (atomicAdd) and splits them into their tiles (up to two per
+// grid block; blocks outside the simplex give none), so the work is balanced
+// whatever each block's share of idle grid blocks.  A run of up to 8 grid
+// blocks per atomic keeps the claims off the loader's path where the map's
+// grid is mostly idle (lambda at a non-power of two pads nb up to p; at
+// n = 12000 25.3 M grid blocks hold 8.9 M tiles), and the host keeps at
+// least 64 claims per persistent block.  The walk state lives in shared
+// memory.
 //
 // Order of the hand-out.  A tile (I, J, K) reads the tables of (I, K) and
 // (J, K).  In the map's grid order (x fastest, then y, then z) one of the two
@@ -629,14 +635,14 @@ __device__ __forceinline__ void handout_block(int64_t c, int gx, int gy, int gz,
 }
 
 template <int MAP>
-__device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p, int nb,
+__device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p, int nb, int claim,
                           AtmForceSmem &S, int slot) {
     const int64_t total = (int64_t)gx * gy * gz;
-    long long w = S.walk_w;
+    long long w = S.walk_w, end = S.walk_end;
     int sub = S.walk_sub;
     int *out = S.tq[slot];
     for (;;) {
-        if (w >= 0 && w < total) {
+        if (w < end) {
             uint32_t bx, by, bz;
             handout_block(w, gx, gy, gz, bx, by, bz);
             const List3 L = decode3<MAP>(bx, by, bz, p, nb);
@@ -645,15 +651,22 @@ __device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p
                 block_of(L, sub, I, J, K);
                 out[0] = I; out[1] = J; out[2] = K; out[3] = 1;
                 S.walk_w = w;
+                S.walk_end = end;
                 S.walk_sub = sub + 1;
                 return;
             }
+            ++w;
+            sub = 0;
+            continue;
         }
-        w = (long long)atomicAdd(ctr, 1ull);
+        // the next run of `claim` hand-out positions
+        w = (long long)atomicAdd(ctr, 1ull) * claim;
+        end = w + claim < total ? w + claim : total;
         sub = 0;
         if (w >= total) {
             out[3] = 0;
             S.walk_w = w;
+            S.walk_end = w;
             S.walk_sub = 0;
             return;
         }
@@ -689,7 +702,7 @@ __device__ __forceinline__ void load_pair_consts(const float4 *__restrict__ tab,
 template <int MAP, bool TAB>
 __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *__restrict__ x,
                                                        float nu, float eps, int nb, int gx, int gy,
-                                                       int gz, int p, const float4 *__restrict__ tab,
+                                                       int gz, int p, int claim, const float4 *__restrict__ tab,
                                                        unsigned long long *__restrict__ ctr,
                                                        double *__restrict__ partials,
                                                        double *__restrict__ forces) {
@@ -703,10 +716,11 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid == 0) {
-        S.walk_w = -1;
+        S.walk_w = 0;
+        S.walk_end = 0;
         S.walk_sub = 0;
-        grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, 0);
-        grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, 1);
+        grab_tile<MAP>(ctr, gx, gy, gz, p, nb, claim, S, 0);
+        grab_tile<MAP>(ctr, gx, gy, gz, p, nb, claim, S, 1);
     }
     bool bad = false;   // a bounded wait ran out (block-uniform after each tile)
     float hi = 0.f, lo = 0.f;
@@ -811,7 +825,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         const int *nx = S.tq[(t + 1) & 1];
         const int In = nx[0], Jn = nx[1], Kn = nx[2];
         const bool hn = nx[3] != 0;
-        if (hn && tid == 6 * R_) grab_tile<MAP>(ctr, gx, gy, gz, p, nb, S, (int)(t & 1));
+        if (hn && tid == 6 * R_) grab_tile<MAP>(ctr, gx, gy, gz, p, nb, claim, S, (int)(t & 1));
         if (hn) {
             // the next tile's tables (into the free table buffer), points
             // (into the other buffer) and pair constants
@@ -1084,15 +1098,18 @@ extern "C" int simplex_atm_forces(int64_t n, int64_t d, const float *x, float nu
     }
     if (st) return st;
     const int gx = (int)g.gx, gy = (int)g.gy, gz = (int)g.gz;
+    // grid blocks per claim: up to 8, at least 64 claims per persistent block
+    int64_t claim64 = blocks / ((int64_t)ctas * 64);
+    const int claim = (int)(claim64 < 1 ? 1 : (claim64 > 8 ? 8 : claim64));
     prof_begin(s);
     if (ftab) {
-        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, tab, ctr, partials, forces);
-        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, tab, ctr, partials, forces);
-        else k_atm_forces<MAP_LINEAR, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, tab, ctr, partials, forces);
+        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, claim, tab, ctr, partials, forces);
+        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, claim, tab, ctr, partials, forces);
+        else k_atm_forces<MAP_LINEAR, true><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, claim, tab, ctr, partials, forces);
     } else {
-        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, nullptr, ctr, partials, forces);
-        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, nullptr, ctr, partials, forces);
-        else k_atm_forces<MAP_LINEAR, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, nullptr, ctr, partials, forces);
+        if (map == MAP_LAMBDA) k_atm_forces<MAP_LAMBDA, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, claim, nullptr, ctr, partials, forces);
+        else if (map == MAP_BBOX) k_atm_forces<MAP_BBOX, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, claim, nullptr, ctr, partials, forces);
+        else k_atm_forces<MAP_LINEAR, false><<<ctas, 256, smem, s>>>(n, x, nu, eps, (int)nb, gx, gy, gz, g.p, claim, nullptr, ctr, partials, forces);
     }
     prof_end(s);
     note_launches(1);

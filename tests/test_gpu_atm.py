@@ -126,3 +126,23 @@ def test_scale_config_n16384(gpu, oracle):
     assert err_fd.max() <= F_TOL
     e_bb = energy(gpu, x, "bbox")
     assert e_bb == pytest.approx(E.item(), rel=1e-6)
+
+
+def test_forces_per_tile_tables(gpu, oracle):
+    """Past 16 GB of force tables (n >= 21,825: 683 blocks of 32) the forces
+    kernel builds each tile's tables from the points instead of copying
+    them: n = 21,856, forces of 4 seeded atoms against the oracle's analytic
+    gradient, and the energy equal across the lambda and linear maps."""
+    n = 21856
+    nb = -(-n // 32)
+    assert nb * (nb + 1) // 2 * 73728 > 16 << 30
+    assert gpu.simplex_workspace_bytes("atm_forces", n, 3, "lambda") < 4 << 30   # no tables
+    x = synth.uniform_cube(n, 3, 20.0, seed=21)
+    F, E = gpu.atm_forces(to_gpu(x), 1.0, 1e-4, "lambda")
+    atoms = synth.sample_indices(4, n, seed=22)
+    G = grad_atoms_threads(oracle, x, atoms)
+    err = atom_err(F.cpu().numpy()[atoms], G)
+    print(f"n={n} per-tile force tables: max rel err {err.max():.3e} (4 atoms)")
+    assert err.max() <= F_TOL
+    _, E_lin = gpu.atm_forces(to_gpu(x), 1.0, 1e-4, "linear", with_energy=True)
+    assert E_lin.item() == pytest.approx(E.item(), rel=1e-9)
