@@ -438,6 +438,12 @@ def row_edm_n32768_d256(torch, sx, peaks):
     sx.simplex_edm_packed(x, o, "lambda", "bf16x3", sx.workspace("edm", x.shape[0], x.shape[1], "lambda", "bf16x3"))
     r["error_lambda"] = _edm_error(torch, o, xh, seed=21)
     r["fp32_simt_lambda"] = _edm_big(torch, sx, peaks, x, "fp32", ("lambda", "bbox"), out=o)["lambda"]
+    del o
+    torch.cuda.empty_cache()
+    t = _edm_tiles(torch, sx, peaks, x)
+    t["tensor_tflops_lambda"] = 6.0 * x.shape[1] * t["pairs"] / (t["lambda_ms"] / 1e3) / 1e12
+    t["tensor_frac_lambda"] = t["tensor_tflops_lambda"] / peaks["bf16_tflops"]
+    r["tiles"] = t
     r["cpu_baseline"] = cpu_edm(xh, 2_000_000, host_cores())
     return r
 
