@@ -32,6 +32,13 @@ Parity status of each function (what pins it, see ``tests/test_oracle.py``):
 * ``atm_energy_grad_slice``: pinned by FD of its own energy (a sum of terms
   whose gradient it returns) and by slices that partition the total energy
   and gradient.
+* ``atm_grad_abs`` (per atom, the sum of the magnitudes of its gradient's
+  per-side parts): pinned by the equilateral triangle, where the two parts
+  at each atom have equal length at 60 degrees so the sum is 2/sqrt(3) times
+  the gradient's norm whatever the derivative's value, by a collinear
+  triple with an end atom (parallel parts: equal to the norm, or the norm
+  of the difference when the parts oppose), and by sum >= |gradient| on a
+  cloud.
 * ``atm_abs_energy`` (sum of |e|): pinned by the closed-form triangles in
   absolute value, a pure-Python brute force of sum |e| on a cloud with terms
   of both signs, and equality with E on a regular tetrahedron.
@@ -98,6 +105,7 @@ def lib():
             "oracle_atm_atom_energy": (_d, [_i64, _dp, _i64, _d, _d]),
             "oracle_atm_grad": (None, [_i64, _dp, _d, _d, _dp]),
             "oracle_atm_grad_atoms": (None, [_i64, _dp, _d, _d, _i64p, _i64, _dp]),
+            "oracle_atm_grad_abs": (None, [_i64, _dp, _d, _d, _dp]),
             "oracle_stress_loss": (_d, [_i64, _i64, _dp, _dp]),
             "oracle_stress_grad_rows": (None, [_i64, _i64, _dp, _dp, _i64p, _i64, _dp]),
         }
@@ -251,6 +259,16 @@ def atm_grad(x: np.ndarray, nu: float = 1.0, eps: float = 1e-4) -> np.ndarray:
     g = np.empty_like(x)
     lib().oracle_atm_grad(len(x), _p(x, ctypes.c_double), nu, eps, _p(g, ctypes.c_double))
     return g
+
+
+def atm_grad_abs(x: np.ndarray, nu: float = 1.0, eps: float = 1e-4) -> np.ndarray:
+    """Per atom, the sum of the magnitudes of the per-side parts of its
+    gradient (2 |de/ds| |x_a - x_b| over its triples): the scale of the
+    rounding error of an FP32 evaluation of that gradient."""
+    x = _f64(x)
+    out = np.empty(len(x))
+    lib().oracle_atm_grad_abs(len(x), _p(x, ctypes.c_double), nu, eps, _p(out, ctypes.c_double))
+    return out
 
 
 def atm_energy_grad_slice(x: np.ndarray, i_lo: int, i_hi: int, nu: float = 1.0,

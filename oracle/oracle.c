@@ -676,6 +676,32 @@ void oracle_atm_grad(int64_t n, const double *x, double nu, double eps, double *
             }
 }
 
+/* Conditioning of the gradient: for every atom, the sum over the triples
+ * that hold it of the magnitudes of the two parts its gradient gets from
+ * the triple's two sides at that atom, 2 |de/ds| |x_a - x_b| each (the
+ * gradient itself sums the same parts as vectors).  An FP32 evaluation
+ * that rounds each side derivative independently errs in an atom's gradient
+ * by a small multiple of the FP32 unit roundoff times this sum, however
+ * much the parts cancel (a pair of atoms much closer than the rest makes
+ * the parts at a third atom large and nearly opposite). */
+void oracle_atm_grad_abs(int64_t n, const double *x, double nu, double eps, double *out)
+{
+    memset(out, 0, sizeof(double) * n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j)
+            for (int64_t k = j + 1; k < n; ++k) {
+                const double *xi = x + 3 * i, *xj = x + 3 * j, *xk = x + 3 * k;
+                double gA, gB, gC;
+                atm_sides_grad(xi, xj, xk, nu, eps, &gA, &gB, &gC);
+                const double a = 2.0 * fabs(gA) * sqrt(sqdist(xi, xj, 3));
+                const double b = 2.0 * fabs(gB) * sqrt(sqdist(xj, xk, 3));
+                const double c = 2.0 * fabs(gC) * sqrt(sqdist(xk, xi, 3));
+                out[i] += a + c;
+                out[j] += a + b;
+                out[k] += b + c;
+            }
+}
+
 /* Energy of the triples i < j < k with i in [i_lo, i_hi), and their
  * contribution to the gradient added into grad (n x 3): a slice of the outer
  * loop of the total energy and gradient, used to time a bounded sample of the

@@ -13,6 +13,11 @@ from helpers import fd_grad_atoms, grad_atoms_threads, rel_err, to_gpu
 pytestmark = pytest.mark.gpu
 E_TOL = 1e-6
 F_TOL = 1e-4
+# An FP32 side derivative takes about 16 roundings (the table's r^3 and
+# edge terms, their products, the cosine terms), and each atom's force sums
+# 32 partners per tile and 32 values of k per coefficient in FP32: about
+# 16 + 2 sqrt(32) ~ 27 unit roundoffs of kappa for independent roundings.
+KAPPA_C = 32
 
 
 def energy(gpu, x, mp="lambda", nu=1.0, eps=1e-4):
@@ -45,6 +50,45 @@ def test_parameters_nu_eps(gpu, oracle):
     x = synth.uniform_cube(70, 3, 2.0, seed=7)
     for nu, eps in ((0.5, 0.0), (2.0, 1e-2)):
         assert energy(gpu, x, "lambda", nu, eps) == pytest.approx(oracle.atm_energy(x, nu, eps), rel=E_TOL)
+
+
+def near_coincident(n, side, seed, sep, pairs=10):
+    """A uniform cloud in which atoms n/2 .. n/2 + pairs - 1 sit at distances
+    sep .. 1.9 sep from atoms 0 .. pairs - 1 (seeded directions)."""
+    x = synth.uniform_cube(n, 3, side, seed).astype(np.float64)
+    d = synth.normal(pairs, 3, seed + 1).astype(np.float64)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    h = n // 2
+    x[h:h + pairs] = x[:pairs] + sep * d * (1 + np.arange(pairs)[:, None] / pairs)
+    return x.astype(np.float32)
+
+
+U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("mp", ["lambda", "bbox"])
+@pytest.mark.parametrize("side,sep,eps", [(6.0, 1e-3, 1e-4), (6.0, 1e-3, 1e-8), (20.0, 3e-3, 1e-4),
+                                          (20.0, 1e-2, 1e-4), (6.0, 3e-3, 1e-6)])
+def test_near_coincident_pairs(gpu, oracle, mp, side, sep, eps):
+    """Pairs 1e-3 .. 1e-2 apart in clouds of several units, the triples
+    that dominate E.  Energy against the oracle within 1e-6.  Forces: the
+    parts 2 (de/ds)(x_k - x_q) that a third atom k gets from a close pair
+    (i, j) are large and nearly opposite, so an FP32 evaluation of the side
+    derivatives errs at k by a few FP32 roundings of their magnitudes, not
+    of the small net force: every atom's error is checked against
+    C U32 kappa_k, kappa_k the oracle's sum of those magnitudes."""
+    x = near_coincident(200, side, 40, sep)
+    F, E = gpu.atm_forces(to_gpu(x), 1.0, eps, mp)
+    G = oracle.atm_grad(x, 1.0, eps)
+    kappa = oracle.atm_grad_abs(x, 1.0, eps)
+    err = np.linalg.norm(F.cpu().numpy() + G, axis=1)
+    e_ref = oracle.atm_energy(x, 1.0, eps)
+    print(f"near-coincident {mp} side {side} sep {sep} eps {eps}: force rel max "
+          f"{(err / np.linalg.norm(G, axis=1)).max():.2e}, err / (u kappa) max {(err / (U32 * kappa)).max():.2f}, "
+          f"energy rel {abs(E.item() / e_ref - 1):.2e}")
+    assert (err <= KAPPA_C * U32 * kappa).all()
+    assert E.item() == pytest.approx(e_ref, rel=E_TOL)
+    assert energy(gpu, x, mp, 1.0, eps) == pytest.approx(e_ref, rel=E_TOL)
 
 
 def test_closed_form_triangles(gpu):

@@ -496,6 +496,40 @@ def test_atm_bruteforce_law_of_cosines(oracle):
     assert oracle.atm_energy(x, 1.0, 0.0) == pytest.approx(tot, rel=1e-11)
 
 
+def test_atm_grad_abs(oracle):
+    """The per-atom sum of the magnitudes of the gradient's per-side parts.
+    Equilateral triangle: at each atom two parts of equal length at 60
+    degrees, so the sum is 2/sqrt(3) times the gradient's norm, whatever the
+    side derivative is.  Right isosceles triangle: at the right-angle vertex
+    two equal parts at 90 degrees, ratio sqrt(2).  Additive over the four
+    triples of four atoms; at least the gradient's norm on a cloud;
+    homogeneous of degree -10 without softening (the gradient of a degree -9
+    energy)."""
+    L = 1.3
+    tri = np.array([[0, 0, 0], [L, 0, 0], [L / 2, L * np.sqrt(3) / 2, 0]])
+    for eps in (0.0, 1e-4):
+        k = oracle.atm_grad_abs(tri, 1.0, eps)
+        g = np.linalg.norm(oracle.atm_grad(tri, 1.0, eps), axis=1)
+        assert np.allclose(k / g, 2 / np.sqrt(3), rtol=1e-12)
+    ri = np.array([[0.4, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.4, 0.0]])   # right angle at atom 1
+    k = oracle.atm_grad_abs(ri, 1.0, 1e-4)
+    g = np.linalg.norm(oracle.atm_grad(ri, 1.0, 1e-4), axis=1)
+    assert k[1] / g[1] == pytest.approx(np.sqrt(2), rel=1e-12)
+    four = synth.uniform_cube(4, 3, 2.0, seed=91).astype(np.float64)
+    total = np.zeros(4)
+    for drop in range(4):
+        keep = [a for a in range(4) if a != drop]
+        total[keep] += oracle.atm_grad_abs(four[keep], 1.0, 1e-4)
+    assert np.allclose(oracle.atm_grad_abs(four, 1.0, 1e-4), total, rtol=1e-12)
+    cloud = synth.uniform_cube(40, 3, 3.0, seed=92)
+    k = oracle.atm_grad_abs(cloud, 1.0, 1e-4)
+    g = np.linalg.norm(oracle.atm_grad(cloud, 1.0, 1e-4), axis=1)
+    assert (k >= g * (1 - 1e-12)).all() and (k > 1.5 * g).any()
+    c = cloud.astype(np.float64)
+    assert np.allclose(oracle.atm_grad_abs(2.0 * c, 1.0, 0.0), 2.0 ** -10 * oracle.atm_grad_abs(c, 1.0, 0.0),
+                       rtol=1e-10)
+
+
 def test_atm_abs_energy(oracle):
     """Sum of |e| over the triples: on one triangle it is |E| of the closed
     forms (equilateral e > 0, collinear e < 0); on a cloud it matches a
