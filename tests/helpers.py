@@ -56,6 +56,18 @@ def _pool_map(fn, items):
         return list(ex.map(fn, items))
 
 
+def grad_all_threads(oracle, x, nu=1.0, eps=1e-4, slices=256):
+    """(energy, gradient) of the oracle over all atoms, as slices of its
+    outer loop i with about equal work (the triples of row i number about
+    (n - i)^2 / 2) run on host threads; the slices partition both sums."""
+    n = len(x)
+    w = np.cumsum((n - np.arange(n, dtype=np.float64)) ** 2)
+    w /= w[-1]
+    cuts = sorted(set([0, n] + [min(n, int(np.searchsorted(w, (s + 1) / slices)) + 1) for s in range(slices - 1)]))
+    res = _pool_map(lambda k: oracle.atm_energy_grad_slice(x, cuts[k], cuts[k + 1], nu, eps), range(len(cuts) - 1))
+    return sum(r[0] for r in res), sum(r[1] for r in res)
+
+
 def fd_grad_atoms(oracle, x, atoms, h=1e-4, nu=1.0, eps=1e-4):
     """FP64 central differences (x_a +- h e_t) of the oracle's partial energy
     E_a (the triples holding atom a, O(n^2)), which has the same gradient in

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import synth
-from helpers import fd_grad_atoms, grad_atoms_threads, rel_err, to_gpu
+from helpers import fd_grad_atoms, grad_all_threads, grad_atoms_threads, rel_err, to_gpu
 
 pytestmark = pytest.mark.gpu
 E_TOL = 1e-6
@@ -132,6 +132,21 @@ def test_differentiation_config_n4096(gpu, oracle):
     # the three maps give the same energy (no oracle run of 1.1e10 triples)
     e = [energy(gpu, x, mp) for mp in ("lambda", "bbox", "linear")]
     assert e[1] == pytest.approx(e[0], rel=1e-9) and e[2] == pytest.approx(e[0], rel=1e-9)
+
+
+def test_differentiation_config_all_atoms(gpu, oracle):
+    """n = 4096 (U[0,20)^3, seed 3): every atom's force against the oracle's
+    FP64 gradient (its outer loop split into slices on the host cores), and
+    the energy of the same call."""
+    w = synth.WORKLOADS["atm_n4096"]
+    x = synth.make_points("atm_n4096")
+    F, E = gpu.atm_forces(to_gpu(x), 1.0, 1e-4, "lambda")
+    e_ref, G = grad_all_threads(oracle, x)
+    err = atom_err(F.cpu().numpy(), G)
+    print(f"n={w['n']} all atoms: force max {err.max():.2e}, median {np.median(err):.2e}; "
+          f"energy {abs(E.item() / e_ref - 1):.2e}")
+    assert err.max() <= F_TOL
+    assert E.item() == pytest.approx(e_ref, rel=E_TOL)
 
 
 def test_properties_full_size(gpu):
