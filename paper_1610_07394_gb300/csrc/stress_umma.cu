@@ -25,8 +25,9 @@
 // row / column sums of C in column d of the accumulator, zero rows up to
 // d + 16).  The C tile serves as the K-major A operand of the row side and,
 // read M-major through its descriptor, as C^T for the column side.  Each
-// CTA walks interleaved chunks of 32 consecutive grid blocks of the map's
-// grid, along which the row block Y stays fixed for runs of tiles (with the
+// CTA walks chunks of 32 consecutive grid blocks of the map's grid (dealt
+// by tile count, so that the CTAs finish together), along which the row
+// block Y stays fixed for runs of tiles (with the
 // lambda map for 2^floor(log2 wy) consecutive grid blocks of row wy), so G_Y
 // accumulates in TMEM over a run and is flushed once per run; G_X (two
 // buffers where TMEM has room) is flushed per tile.  Flushes are FP32 vector
@@ -88,76 +89,158 @@ static_assert(sizeof(Ctl) <= kCtlBytes, "control block");
 static_assert(offsetof(Ctl, acol) % 16 == 0, "float4 reads of a_j");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per block");
 
-// The tiles a CTA handles: the map's grid (gx x gy, x fastest) cut into C
-// chunks of `chunk` consecutive grid blocks (up to kChunk, smaller when the
-// grid would give a CTA fewer than four chunks); CTA b takes the chunks pi(c) for
-// c = b, b + gridDim.x, ..., with pi a fixed pseudo-random permutation of
-// [0, C) (chunk_perm), so that no CTA keeps drawing the same position within
-// the map's rows; each grid block maps to zero, one or two tiles.  Along a grid row the row
-// block Y stays fixed for runs of tiles (with the lambda map for
-// 2^floor(log2 wy) consecutive grid blocks of row wy), so within a chunk
-// G_Y accumulates over runs of up to `chunk` tiles, while interleaving the
-// scattered chunks spreads the map's uneven parts (the diagonal-pair row of
-// lambda, the empty upper half of the bounding box) evenly over the CTAs.
+// The tiles a CTA handles.  The map's grid (gx x gy, x fastest) lists the
+// T = nb(nb+1)/2 tiles of the 2-simplex of blocks in its order (zero, one
+// or two per grid block); that sequence is cut into N = q gridDim.x chunks
+// of equal size (chunk c holds tiles floor(c T / N) .. floor((c+1) T / N) - 1,
+// so sizes differ by one tile at most, about kChunk each), and in round k
+// CTA b takes chunk k gridDim.x + (b + k) mod gridDim.x (the rotation mixes
+// the chunk sizes each CTA gets): every CTA gets the same number of tiles,
+// whatever the map's idle grid blocks or two-tile rows (the lambda map's
+// diagonal-pair row, the bounding box's empty upper half).  A prologue scans
+// the tiles of the grid blocks and finds each chunk's first grid block.
+// Along a grid row the row block Y stays fixed for runs of tiles (with the
+// lambda map for 2^floor(log2 wy) consecutive grid blocks of row wy), so
+// within a chunk G_Y accumulates over runs of up to kChunk tiles.
 constexpr int kChunk = 32;
+constexpr int kScanBlock = 1024;   // grid blocks per block of the scan
 
-// A permutation of [0, C): a three-round Feistel network on 2h bits
-// (2^(2h) >= C), applied again while the value is >= C (cycle walking, at
-// most a few rounds since 2^(2h) < 4C).
-__device__ __forceinline__ uint32_t feistel(uint32_t v, int h) {
-    const uint32_t mask = (1u << h) - 1u;
-    uint32_t L = v >> h, R = v & mask;
-#pragma unroll
-    for (uint32_t r = 0; r < 3; ++r) {
-        const uint32_t f = ((R + r * 0x632BE5ABu) * 0x9E3779B1u) >> 11;
-        const uint32_t t = L ^ (f & mask);
-        L = R;
-        R = t;
-    }
-    return (L << h) | R;
+template <int MAP>
+__device__ __forceinline__ List2 decode_grid2(int64_t w, int wx, int wy, int nb) {
+    return MAP == MAP_LINEAR ? decode2_linear(w, nb) : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb);
 }
 
-__device__ __forceinline__ int64_t chunk_perm(int64_t c, int64_t C) {
-    int h = 1;
-    while ((int64_t(1) << (2 * h)) < C) ++h;
-    uint32_t v = feistel((uint32_t)c, h);
-    while ((int64_t)v >= C) v = feistel(v, h);
-    return v;
+// Tiles of each grid block: their exclusive prefix within each scan block
+// (loc) and each scan block's total (bsum).
+template <int MAP>
+__global__ void __launch_bounds__(kScanBlock) k_tile_scan(int64_t total, int gx, int nb, int *__restrict__ loc,
+                                                          int64_t *__restrict__ bsum) {
+    __shared__ int wsum[kScanBlock / 32];
+    const int64_t w = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int c = 0;
+    if (w < total) {
+        const int wy = (int)(w / gx), wx = (int)(w - (int64_t)wy * gx);
+        c = decode_grid2<MAP>(w, wx, wy, nb).cnt;
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int v = c;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[wp] = v;
+    __syncthreads();
+    if (wp == 0) {
+        int t = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        wsum[lane] = t;   // inclusive over warps
+    }
+    __syncthreads();
+    const int before = wp ? wsum[wp - 1] : 0;
+    if (w < total) loc[w] = before + v - c;
+    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = wsum[31];
+}
+
+// Exclusive prefix of the scan blocks' totals, in place (one block).
+__global__ void __launch_bounds__(1024) k_bsum_scan(int64_t nblk, int64_t *__restrict__ bsum) {
+    __shared__ int64_t part[32];
+    int64_t carry = 0;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nblk; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t c = i < nblk ? bsum[i] : 0;
+        int64_t v = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane == 31) part[wp] = v;
+        __syncthreads();
+        if (wp == 0) {
+            int64_t t = part[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            part[lane] = t;
+        }
+        __syncthreads();
+        const int64_t before = carry + (wp ? part[wp - 1] : 0);
+        if (i < nblk) bsum[i] = before + v - c;
+        carry += part[31];
+        __syncthreads();
+    }
+}
+
+// First tile of each chunk: 2 w + s for grid block w and its tile s.  The
+// tile r = floor(c T / N) lies in the last grid block whose prefix is <= r
+// (a block after it with no tile has the same prefix, so that block holds
+// tiles): a binary search over the scan blocks, then within one.
+__global__ void __launch_bounds__(256) k_chunk_starts(int64_t total, int64_t nblk, int64_t T, int64_t N,
+                                                      const int *__restrict__ loc,
+                                                      const int64_t *__restrict__ boff, int64_t *__restrict__ start) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int64_t r = c * T / N;
+    int64_t lo = 0, hi = nblk - 1;   // last scan block with boff <= r
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (boff[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    const int64_t b = lo, rr = r - boff[b];
+    int64_t a = b * kScanBlock, z = (b + 1) * kScanBlock < total ? (b + 1) * kScanBlock - 1 : total - 1;
+    while (a < z) {
+        const int64_t mid = (a + z + 1) >> 1;
+        if (loc[mid] <= rr) a = mid; else z = mid - 1;
+    }
+    start[c] = 2 * a + (rr - loc[a]);
 }
 
 template <int MAP>
 struct ChunkWalk {
-    int64_t c, w, end, total, nchunks;
-    int wx, wy, gx, nb, chunk;
-    int pend, px, py;
-    __device__ ChunkWalk(int gx_, int64_t total_, int nb_, int chunk_)
-        : c(blockIdx.x), total(total_), nchunks((total_ + chunk_ - 1) / chunk_), gx(gx_), nb(nb_),
-          chunk(chunk_), pend(0), px(0), py(0) {
+    const int64_t *start;
+    int64_t k, c, w, T, N;
+    int left, sub, wx, wy, gx, nb;
+    __device__ ChunkWalk(int gx_, int nb_, int64_t T_, int64_t N_, const int64_t *start_)
+        : start(start_), k(0), T(T_), N(N_), left(0), gx(gx_), nb(nb_) {
         open();
     }
     __device__ void open() {
-        w = c < nchunks ? chunk_perm(c, nchunks) * chunk : total;
-        end = w + chunk < total ? w + chunk : total;
+        c = k * gridDim.x + (blockIdx.x + k) % gridDim.x;
+        if (c >= N) { left = 0; return; }
+        const int64_t s0 = start[c];
+        w = s0 >> 1;
+        sub = (int)(s0 & 1);
+        left = (int)((c + 1) * T / N - c * T / N);
         wy = (int)(w / gx);
         wx = (int)(w - (int64_t)wy * gx);
     }
     __device__ bool next(int &X, int &Y) {
-        if (pend) { pend = 0; X = px; Y = py; return true; }
         for (;;) {
-            if (w >= end) {
-                c += gridDim.x;
-                if (c >= nchunks) return false;
+            if (left == 0) {
+                ++k;
+                if (k * gridDim.x >= N) return false;
                 open();
                 continue;
             }
-            const List2 L = MAP == MAP_LINEAR ? decode2_linear(w, nb)
-                                              : decode2<MAP>((uint32_t)wx, (uint32_t)wy, nb);
+            const List2 L = decode_grid2<MAP>(w, wx, wy, nb);
+            if (sub < L.cnt) {
+                X = sub ? L.x[1] : L.x[0];
+                Y = sub ? L.y[1] : L.y[0];
+                ++sub;
+                --left;
+                return true;
+            }
             ++w;
+            sub = 0;
             if (++wx == gx) { wx = 0; ++wy; }
-            if (L.cnt == 0) continue;
-            X = L.x[0]; Y = L.y[0];
-            if (L.cnt > 1) { pend = 1; px = L.x[1]; py = L.y[1]; }
-            return true;
         }
     }
 };
@@ -249,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                       const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
                       const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
-                      int gx, int64_t total, int chunk, float scale4, float *__restrict__ grad,
-                      double *__restrict__ partials, int qshift) {
+                      int gx, int64_t T, int64_t nchunks, const int64_t *__restrict__ start,
+                      float scale4, float *__restrict__ grad, double *__restrict__ partials, int qshift) {
     using Walk = ChunkWalk<MAP>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -299,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
-            Walk walk(gx, total, nb, chunk);
+            Walk walk(gx, nb, T, nchunks, start);
             uint32_t it = 0, dst, bar;
             int X, Y, pX = 0, pY = 0;
             bool ok = true, have = false;
@@ -338,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
-            Walk walk(gx, total, nb, chunk);
+            Walk walk(gx, nb, T, nchunks, start);
             uint32_t it = 0, t = 0, src;
             int X, Y, prevY = -1, prev2Y = -1;
             bool ok = true;
@@ -438,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ngx = gx_buffers(NG);
         unsigned char *rowh = cbuf + half * TILE_BYTES + (r >> 3) * 1024 + (r & 7) * 128;
         unsigned char *rowl = rowh + 2 * TILE_BYTES;
-        Walk walk(gx, total, nb, chunk);
+        Walk walk(gx, nb, T, nchunks, start);
         uint32_t t = 0;
         int X, Y, pX = 0, pY = 0;
         bool have = walk.next(X, Y);
@@ -824,8 +907,15 @@ __global__ void __launch_bounds__(256) k_stress_prep(const float *__restrict__ x
 }
 
 struct Layout {
-    int64_t Ph, Pl, Qh, Ql, Th, Tl, a, part, edm, total, pitch;
+    int64_t Ph, Pl, Qh, Ql, Th, Tl, a, part, edm, deal, total, pitch;
 };
+
+// The backward's chunks of the tile sequence: q per CTA, about kChunk
+// tiles each and at least four per CTA.
+static int64_t chunks_of(int64_t T, int64_t ctas) {
+    int64_t q = (T + ctas * kChunk - 1) / (ctas * kChunk);
+    return ctas * (q < 4 ? 4 : q);
+}
 
 static Layout layout_of(int64_t n, int64_t d, bool bwd) {
     Layout L;
@@ -837,7 +927,23 @@ static Layout layout_of(int64_t n, int64_t d, bool bwd) {
     L.a = L.Tl + xt;
     L.part = L.a + align_up(n * 4, 1024);
     L.edm = L.part + align_up(8 * (kMaxCtas + kReduceSlots), 1024);
-    L.total = L.edm + ((!bwd && d % 64 == 0) ? edm_umma_workspace_bytes(n, d) : 0);
+    L.deal = L.edm + ((!bwd && d % 64 == 0) ? edm_umma_workspace_bytes(n, d) : 0);
+    // backward: the tile scan of the grid blocks (int each), the scan
+    // blocks' offsets and the chunk starts (int64 each), for the largest
+    // grid of any map and the most CTAs
+    int64_t deal_bytes = 0;
+    if (bwd) {
+        const int64_t nb = (n + TM - 1) / TM;
+        int64_t most = 0;
+        for (int mp = MAP_LAMBDA; mp <= MAP_RB; ++mp) {
+            const Grid g = grid2(nb, mp);
+            if (g.gx * g.gy > most) most = g.gx * g.gy;
+        }
+        const int64_t nblk = (most + kScanBlock - 1) / kScanBlock;
+        deal_bytes = align_up(4 * most, 1024) + align_up(8 * nblk, 1024) +
+                     align_up(8 * chunks_of(nb * (nb + 1) / 2, kMaxCtas), 1024);
+    }
+    L.total = L.deal + deal_bytes;
     return L;
 }
 
@@ -876,20 +982,42 @@ static int smem_optin() {
 }
 
 static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
-                              const float *a, int64_t n, int d, int nb, int gx, int64_t total, int chunk,
-                              float scale4, float *grad, double *partials, int qshift) {
+                              const float *a, int64_t n, int d, int nb, int gx, int64_t T, int64_t nchunks,
+                              const int64_t *start, float scale4, float *grad, double *partials, int qshift) {
     if (map == MAP_LAMBDA)
         k_stress_umma_bwd<MAP_LAMBDA><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            partials, qshift);
     else if (map == MAP_BBOX)
         k_stress_umma_bwd<MAP_BBOX><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            partials, qshift);
     else if (map == MAP_RB)
         k_stress_umma_bwd<MAP_RB><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            partials, qshift);
     else
         k_stress_umma_bwd<MAP_LINEAR><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, total, chunk, scale4, grad, partials, qshift);
+            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            partials, qshift);
+    return cudaGetLastError();
+}
+
+// The backward's prologue: the tile scan of the map's grid and the first
+// tile of every chunk, into the workspace.
+static cudaError_t chunk_starts(int map, int64_t total, int gx, int nb, int64_t T, int64_t nchunks, int *loc,
+                                int64_t *boff, int64_t *start, cudaStream_t s) {
+    const int64_t nblk = (total + kScanBlock - 1) / kScanBlock;
+    const unsigned b = (unsigned)nblk;
+    if (map == MAP_LAMBDA) k_tile_scan<MAP_LAMBDA><<<b, kScanBlock, 0, s>>>(total, gx, nb, loc, boff);
+    else if (map == MAP_BBOX) k_tile_scan<MAP_BBOX><<<b, kScanBlock, 0, s>>>(total, gx, nb, loc, boff);
+    else if (map == MAP_RB) k_tile_scan<MAP_RB><<<b, kScanBlock, 0, s>>>(total, gx, nb, loc, boff);
+    else k_tile_scan<MAP_LINEAR><<<b, kScanBlock, 0, s>>>(total, gx, nb, loc, boff);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bsum_scan<<<1, 1024, 0, s>>>(nblk, boff);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_chunk_starts<<<(unsigned)((nchunks + 255) / 256), 256, 0, s>>>(total, nblk, T, nchunks, loc, boff, start);
     return cudaGetLastError();
 }
 
@@ -1021,16 +1149,20 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     int64_t ctas;
     cudaError_t le;
     if (bwd) {
-        const int64_t total = g.gx * g.gy;
-        // chunks of up to kChunk grid blocks, at least four per CTA where the grid allows
-        int64_t chunk = total / (4 * (int64_t)sms);
-        chunk = chunk < 1 ? 1 : (chunk > kChunk ? kChunk : chunk);
-        const int64_t chunks = (total + chunk - 1) / chunk;
-        ctas = chunks < sms ? chunks : sms;
+        const int64_t total = g.gx * g.gy, T = nb * (nb + 1) / 2;
+        ctas = T < sms ? T : sms;
         if (ctas > kMaxCtas) ctas = kMaxCtas;
+        const int64_t nchunks = chunks_of(T, ctas);
+        const int64_t nblk = (total + kScanBlock - 1) / kScanBlock;
+        int *loc = reinterpret_cast<int *>(w + L.deal);
+        int64_t *boff = reinterpret_cast<int64_t *>(w + L.deal + align_up(4 * total, 1024));
+        int64_t *start = reinterpret_cast<int64_t *>(reinterpret_cast<unsigned char *>(boff) + align_up(8 * nblk, 1024));
+        if ((st = cuda_status(chunk_starts(map, total, (int)g.gx, (int)nb, T, nchunks, loc, boff, start, s))))
+            return st;
+        note_launches(3);
         if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
         prof_begin(s);
-        le = launch_bwd(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, total, (int)chunk,
+        le = launch_bwd(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, T, nchunks, start,
                         (float)(4.0 * gscale), grad, loss ? partials : nullptr, qshift);
     } else {
         // two-CTA clusters over the map's grid of 256 x 256 super-blocks
