@@ -323,11 +323,13 @@ __device__ __forceinline__ void wait_tables(uint32_t bar, uint32_t parity, bool 
 // (i, j) = (ti + 8 p, tj + 16 q), and per step (two consecutive k) loads
 // the four (i, k) and the two (j, k) table entries: 12 shared loads of
 // 128 bits for 16 triples, where 2 x 2 pairs per thread take 8 for 8.  A
-// 128-bit shared load costs four wavefronts however many lanes share an
-// address, so that ratio sets the shared-memory time per triple, which in
-// the 2 x 2 layout exceeded the FP32 pipe's (32 wavefronts against 96 FMA
-// cycles per scheduler and step, four schedulers sharing the one
-// shared-memory pipe).  Tiles on a diagonal plane run the same loop (their
+// 128-bit shared load takes two wavefronts when a warp's lanes read at most
+// a few distinct 16-byte words and four when they read eight or more, so
+// per step a warp of this layout spends 8 x 4 on its (i, k) loads (eight
+// distinct i) and 4 x 2 on its (j, k) loads (four distinct j): 40
+// wavefronts for 512 triples, against 24 for 256 in the 2 x 2 layout (16
+// distinct i, two distinct j), four schedulers sharing the one
+// shared-memory pipe.  Tiles on a diagonal plane run the same loop (their
 // tables are zero outside i < j < k; skipping their empty steps, as the 2 x 2
 // layout did, changed nothing here).  Four blocks per SM (120 registers): at
 // n = 1024 the kernel takes 0.0944 ms against 0.0979 ms with 2 x 2 pairs per
