@@ -288,7 +288,7 @@ int simplex_stress_bwd(int64_t n, int64_t d, const float *x, const float *y,
  * from the same residual tiles.  Workspace: simplex_workspace_bytes(
  * SIMPLEX_OP_STRESS_FWD_BWD, ...) bytes, 256-byte aligned (per-block loss
  * partials, and the tensor-core operands where prec selects them, with the
- * tile-count deal of the tensor-core backward's chunks of grid blocks).
+ * tensor-core backward's chunk starts and per-point row sums).
  * SIMPLEX_EINVAL if loss or grad is NULL.
  */
 int simplex_stress_fwd_bwd(int64_t n, int64_t d, const float *x, const float *y,

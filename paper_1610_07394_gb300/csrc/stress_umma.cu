@@ -281,12 +281,16 @@ __device__ __forceinline__ void load_xt(const CUtensorMap *mh, const CUtensorMap
     tma_load_2d(dst + 3 * box, ml, B * TN + 64, 0, bar);
 }
 
-// grad rows of block B += scale4 (G[row][d] x_row - G[row][0:d]) from the
-// accumulator at TMEM column gcol: this thread's lane quarter row, its half
-// of the d coordinates.  All lanes execute the TMEM loads.
+// The sides of a finished accumulator (rows of block B, or its columns):
+// grad_p = scale4 (S_p x_p - sum_q c_pq x_q) with S_p = sum_q c_pq, so the
+// flush adds -scale4 G[row][0:d] to grad (FP32 vector atomics, nothing
+// read back) and the row's sum G[row][d] to S[row]; a last pass adds
+// scale4 S_p x_p (k_stress_sx), so no coordinate is loaded here.  This
+// thread: its lane quarter's row, its half of the d coordinates (the sum
+// once, by half 0).  All lanes execute the TMEM loads.
 __device__ __forceinline__ void flush_g(uint32_t tmem, uint32_t gcol, int B, int quarter, int half,
-                                        int lane, int d, int64_t n, float scale4,
-                                        const float *__restrict__ x, float *__restrict__ grad) {
+                                        int lane, int d, int64_t n, float scale4, float *__restrict__ grad,
+                                        float *__restrict__ S) {
     const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + gcol;
     const float s = tmem_ld1(tl + (uint32_t)d);
     const int64_t row = (int64_t)B * TM + 32 * quarter + lane;
@@ -295,17 +299,27 @@ __device__ __forceinline__ void flush_g(uint32_t tmem, uint32_t gcol, int B, int
         float v[16];
         tmem_ld16(tl + (uint32_t)(half * hw + c), v);
         if (row < n) {
-            const float *xr = x + row * d + half * hw + c;
             float *gr = grad + row * d + half * hw + c;
 #pragma unroll
-            for (int q = 0; q < 16; q += 4) {
-                const float4 xv = __ldg(reinterpret_cast<const float4 *>(xr + q));
-                const float4 o = make_float4(scale4 * fmaf(s, xv.x, -v[q]), scale4 * fmaf(s, xv.y, -v[q + 1]),
-                                             scale4 * fmaf(s, xv.z, -v[q + 2]), scale4 * fmaf(s, xv.w, -v[q + 3]));
-                atomicAdd(reinterpret_cast<float4 *>(gr + q), o);
-            }
+            for (int q = 0; q < 16; q += 4)
+                atomicAdd(reinterpret_cast<float4 *>(gr + q),
+                          make_float4(-scale4 * v[q], -scale4 * v[q + 1], -scale4 * v[q + 2], -scale4 * v[q + 3]));
         }
     }
+    if (half == 0 && row < n) atomicAdd(S + row, s);
+}
+
+// grad_p += scale4 S_p x_p, the row-sum part of every flush (see flush_g).
+__global__ void __launch_bounds__(256) k_stress_sx(const float *__restrict__ x, const float *__restrict__ S,
+                                                   int64_t n, int d, float scale4, float *__restrict__ grad) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // float4 of grad
+    if (e >= n * d / 4) return;
+    const int64_t p = 4 * e / d;
+    const float f = scale4 * S[p];
+    const float4 xv = reinterpret_cast<const float4 *>(x)[e];
+    float4 g = reinterpret_cast<float4 *>(grad)[e];
+    g.x = fmaf(f, xv.x, g.x); g.y = fmaf(f, xv.y, g.y); g.z = fmaf(f, xv.z, g.z); g.w = fmaf(f, xv.w, g.w);
+    reinterpret_cast<float4 *>(grad)[e] = g;
 }
 
 // a = S . Delta of a tile's columns col0 + 64 half + lane and + 32 (ca, cb)
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_stress_umma_bwd(const __grid_constant__ CUtensorMap mPh, const __grid_constant__ CUtensorMap mPl,
                       const __grid_constant__ CUtensorMap mQh, const __grid_constant__ CUtensorMap mQl,
                       const __grid_constant__ CUtensorMap mTh, const __grid_constant__ CUtensorMap mTl,
-                      const float *__restrict__ x, const float *__restrict__ a, int64_t n, int d, int nb,
+                      float *__restrict__ S, const float *__restrict__ a, int64_t n, int d, int nb,
                       int gx, int64_t T, int64_t nchunks, const int64_t *__restrict__ start,
                       float scale4, float *__restrict__ grad, double *__restrict__ partials, int qshift) {
     using Walk = ChunkWalk<MAP>;
@@ -595,12 +609,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (t >= 1) {
                 // the previous tile's sides: its columns always, its rows at the end of a run
                 const uint32_t pb = (t - 1) % (uint32_t)ngx;
-                flush_g(tmem, kGY + NG * (1 + pb), pX, quarter, half, lane, d, n, scale4, x, grad);
+                flush_g(tmem, kGY + NG * (1 + pb), pX, quarter, half, lane, d, n, scale4, grad, S);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&ctl.gxfree[pb]));
                 if (Y != pY) {
-                    flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
+                    flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, grad, S);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&ctl.gyfree));
@@ -616,8 +630,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) {
             tc_fence_after();
             flush_g(tmem, kGY + NG * (1 + (t - 1) % (uint32_t)ngx), pX, quarter, half, lane, d, n, scale4,
-                    x, grad);
-            flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, x, grad);
+                    grad, S);
+            flush_g(tmem, kGY, pY, quarter, half, lane, d, n, scale4, grad, S);
         }
     }
     tc_fence_before();
@@ -907,7 +921,7 @@ __global__ void __launch_bounds__(256) k_stress_prep(const float *__restrict__ x
 }
 
 struct Layout {
-    int64_t Ph, Pl, Qh, Ql, Th, Tl, a, part, edm, deal, total, pitch;
+    int64_t Ph, Pl, Qh, Ql, Th, Tl, a, part, edm, deal, sums, total, pitch;
 };
 
 // The backward's chunks of the tile sequence: q per CTA, about kChunk
@@ -943,7 +957,8 @@ static Layout layout_of(int64_t n, int64_t d, bool bwd) {
         deal_bytes = align_up(4 * most, 1024) + align_up(8 * nblk, 1024) +
                      align_up(8 * chunks_of(nb * (nb + 1) / 2, kMaxCtas), 1024);
     }
-    L.total = L.deal + deal_bytes;
+    L.sums = L.deal + deal_bytes;   // backward: the per-point sums S of the flushes
+    L.total = L.sums + (bwd ? align_up(4 * n, 1024) : 0);
     return L;
 }
 
@@ -981,24 +996,24 @@ static int smem_optin() {
     return SIMPLEX_OK;
 }
 
-static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, const float *x,
+static cudaError_t launch_bwd(int map, unsigned ctas, cudaStream_t s, const CUtensorMap *m, float *S,
                               const float *a, int64_t n, int d, int nb, int gx, int64_t T, int64_t nchunks,
                               const int64_t *start, float scale4, float *grad, double *partials, int qshift) {
     if (map == MAP_LAMBDA)
         k_stress_umma_bwd<MAP_LAMBDA><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            m[0], m[1], m[2], m[3], m[4], m[5], S, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
             partials, qshift);
     else if (map == MAP_BBOX)
         k_stress_umma_bwd<MAP_BBOX><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            m[0], m[1], m[2], m[3], m[4], m[5], S, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
             partials, qshift);
     else if (map == MAP_RB)
         k_stress_umma_bwd<MAP_RB><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            m[0], m[1], m[2], m[3], m[4], m[5], S, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
             partials, qshift);
     else
         k_stress_umma_bwd<MAP_LINEAR><<<ctas, kThreads, SMEM_BYTES, s>>>(
-            m[0], m[1], m[2], m[3], m[4], m[5], x, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
+            m[0], m[1], m[2], m[3], m[4], m[5], S, a, n, d, nb, gx, T, nchunks, start, scale4, grad,
             partials, qshift);
     return cudaGetLastError();
 }
@@ -1160,9 +1175,11 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
         if ((st = cuda_status(chunk_starts(map, total, (int)g.gx, (int)nb, T, nchunks, loc, boff, start, s))))
             return st;
         note_launches(3);
+        float *S = reinterpret_cast<float *>(w + L.sums);
         if ((st = cuda_status(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(n * d), s)))) return st;
+        if ((st = cuda_status(cudaMemsetAsync(S, 0, sizeof(float) * (size_t)n, s)))) return st;
         prof_begin(s);
-        le = launch_bwd(map, (unsigned)ctas, s, m, x, a, n, (int)d, (int)nb, (int)g.gx, T, nchunks, start,
+        le = launch_bwd(map, (unsigned)ctas, s, m, S, a, n, (int)d, (int)nb, (int)g.gx, T, nchunks, start,
                         (float)(4.0 * gscale), grad, loss ? partials : nullptr, qshift);
     } else {
         // two-CTA clusters over the map's grid of 256 x 256 super-blocks
@@ -1182,7 +1199,14 @@ int stress_umma_run(bool bwd, int64_t n, int64_t d, const float *x, const float 
     note_launches(1);
     if (le != cudaSuccess) return cuda_status(le);
     if ((st = launch_status())) return st;
-    if (bwd) return loss ? reduce_partials(partials, ctas, partials + kMaxCtas, loss, s) : SIMPLEX_OK;
+    if (bwd) {
+        const int64_t f4 = n * d / 4;
+        k_stress_sx<<<(unsigned)((f4 + 255) / 256), 256, 0, s>>>(x, reinterpret_cast<const float *>(w + L.sums), n,
+                                                              (int)d, (float)(4.0 * gscale), grad);
+        note_launches(1);
+        if ((st = launch_status())) return st;
+        return loss ? reduce_partials(partials, ctas, partials + kMaxCtas, loss, s) : SIMPLEX_OK;
+    }
     if ((st = reduce_partials(partials, ctas, partials + kMaxCtas, loss, s))) return st;
     if (!d_out) return SIMPLEX_OK;
     // the packed D itself: tensor-core EDM where it applies, else FP32
