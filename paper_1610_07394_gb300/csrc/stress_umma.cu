@@ -430,8 +430,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_drain(smem_u32(&ctl.full[k % NS]), (k / NS) & 1);
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
+        // ---------------- MMA issuer: the whole warp, converged, so the
+        // descriptors stay warp-uniform; one elected lane issues
+        {
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
@@ -467,11 +468,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t bh = sw128_desc(src + h * xt_box + ks * 32);
                         const uint64_t bl = sw128_desc(src + (2 + h) * xt_box + ks * 32);
                         const uint32_t acc = (h == 0 && ks == 0 && !sameY) ? 0u : 1u;
-                        mma_bf16_afill(tmem + kGY, ah, bh, id_row, acc);
-                        mma_bf16_alast(tmem + kGY, ah, bl, id_row, 1u);
-                        mma_bf16(tmem + kGY, al, bh, id_row, 1u);
+                        mma_bf16_afill_w(tmem + kGY, ah, bh, id_row, acc);
+                        mma_bf16_alast_w(tmem + kGY, ah, bl, id_row, 1u);
+                        mma_bf16_w(tmem + kGY, al, bh, id_row, 1u);
                     }
-                mma_commit(smem_u32(&ctl.empty[it % NS]));
+                mma_commit_w(smem_u32(&ctl.empty[it % NS]));
                 ++it;
                 // columns: G_X = C^T [X_Y | 1], K = i; A is C read M-major (M = j
                 // over the two 64-column halves, LBO = one half tile apart)
@@ -483,13 +484,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t hb = (uint32_t)(ks >> 2), kb = (uint32_t)(ks & 3) * 32;
                     const uint64_t bh = sw128_desc(src + hb * xt_box + kb);
                     const uint64_t bl = sw128_desc(src + (2 + hb) * xt_box + kb);
-                    mma_bf16_afill(tgx, ah, bh, id_col, ks ? 1u : 0u);
-                    mma_bf16_alast(tgx, ah, bl, id_col, 1u);
-                    mma_bf16(tgx, al, bh, id_col, 1u);
+                    mma_bf16_afill_w(tgx, ah, bh, id_col, ks ? 1u : 0u);
+                    mma_bf16_alast_w(tgx, ah, bl, id_col, 1u);
+                    mma_bf16_w(tgx, al, bh, id_col, 1u);
                 }
-                mma_commit(smem_u32(&ctl.empty[it % NS]));
+                mma_commit_w(smem_u32(&ctl.empty[it % NS]));
                 ++it;
-                mma_commit(smem_u32(&ctl.g2done));
+                mma_commit_w(smem_u32(&ctl.g2done));
                 return true;
             };
             while (ok && !*fail && walk.next(X, Y)) {
@@ -506,15 +507,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t al = sw128_desc(src + TILE_BYTES + ko);
                         const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + ko);
                         const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + ko);
-                        mma_bf16_afill(dtm, ah, bh, id1, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast(dtm, ah, bl, id1, 1u);
-                        mma_bf16(dtm, al, bh, id1, 1u);
+                        mma_bf16_afill_w(dtm, ah, bh, id1, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast_w(dtm, ah, bl, id1, 1u);
+                        mma_bf16_w(dtm, al, bh, id1, 1u);
                     }
-                    mma_commit(smem_u32(&ctl.empty[it % NS]));
+                    mma_commit_w(smem_u32(&ctl.empty[it % NS]));
                     ++it;
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(&ctl.tfull[acc]));
+                mma_commit_w(smem_u32(&ctl.tfull[acc]));
                 if (t >= 1 && !(ok = gemm2(t - 1, t >= 2 && prevY == prev2Y))) break;
                 prev2Y = prevY;
                 prevY = Y;
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (ok && !*fail && t >= 1) gemm2(t - 1, t >= 2 && prevY == prev2Y);
             // everything issued has completed before the block releases TMEM
-            mma_commit(smem_u32(&ctl.done));
+            mma_commit_w(smem_u32(&ctl.done));
             mbar_drain(smem_u32(&ctl.done), 0);
         }
     } else {
