@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
-        if (lane == 0) {
+        {   // the whole warp, converged; one elected lane issues
             SuperWalk<MAP> walk(gx, total, nb2);
             int sX, sY;
             uint32_t it = 0, tt = 0;
@@ -242,14 +242,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                         const uint64_t al = sw64_desc(src + SUB + koff);
                         const uint64_t bh = sw64_desc(src + 2 * SUB + koff);
                         const uint64_t bl = sw64_desc(src + 4 * SUB + koff);
-                        mma_bf16_afill(dtm, ah, bh, kIdesc256, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast(dtm, ah, bl, kIdesc256, 1u);
-                        mma_bf16(dtm, al, bh, kIdesc256, 1u);
+                        mma_bf16_afill_w(dtm, ah, bh, kIdesc256, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast_w(dtm, ah, bl, kIdesc256, 1u);
+                        mma_bf16_w(dtm, al, bh, kIdesc256, 1u);
                     }
                     // the stage is free once this CTA's MMAs and the peer's have read it
-                    mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
+                    mma_commit_mc_w(smem_u32(&ctl.empty[s]), 3);
                 }
-                if (ok) mma_commit(smem_u32(&ctl.tfull[acc]));
+                if (ok) mma_commit_w(smem_u32(&ctl.tfull[acc]));
                 ++tt;
             }
         }
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer: tile tt into accumulator tt mod 4
-        if (lane == 0) {
+        {   // the whole warp, converged; one elected lane issues
             StepWalk<MAP> walk(gx, total, nb2, nb);
             int X0, Y;
             uint32_t it = 0, tt = 0;
@@ -613,13 +613,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
                             const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
                             const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
                             const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
-                            mma_bf16_afill(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
-                            mma_bf16_alast(dtm, ah, bl, kIdesc, 1u);
-                            mma_bf16(dtm, al, bh, kIdesc, 1u);
+                            mma_bf16_afill_w(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
+                            mma_bf16_alast_w(dtm, ah, bl, kIdesc, 1u);
+                            mma_bf16_w(dtm, al, bh, kIdesc, 1u);
                         }
-                        mma_commit(smem_u32(&ctl.empty[s]));
+                        mma_commit_w(smem_u32(&ctl.empty[s]));
                     }
-                    if (ok) mma_commit(smem_u32(&ctl.tfull[acc]));
+                    if (ok) mma_commit_w(smem_u32(&ctl.tfull[acc]));
                 }
             }
         }

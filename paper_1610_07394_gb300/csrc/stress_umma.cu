@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
-        if (lane == 0) {
+        {   // the whole warp, converged; one elected lane issues
             const uint32_t id = idesc_bf16(TM, TN2, false, false);
             SuperWalk<MAP> walk(gx, total, nb2);
             uint32_t it = 0, t = 0;
@@ -779,20 +779,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t al = sw128_desc(src + A_BYTES + ko);
                         const uint64_t bh = sw128_desc(src + 2 * A_BYTES + ko);
                         const uint64_t bl = sw128_desc(src + 2 * A_BYTES + B_BYTES + ko);
-                        mma_bf16_afill(dtm, ah, bh, id, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast(dtm, ah, bl, id, 1u);
-                        mma_bf16(dtm, al, bh, id, 1u);
+                        mma_bf16_afill_w(dtm, ah, bh, id, (c > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16_alast_w(dtm, ah, bl, id, 1u);
+                        mma_bf16_w(dtm, al, bh, id, 1u);
                     }
                     // the stage is free once this CTA's MMAs and the peer's have read it
-                    mma_commit_mc(smem_u32(&ctl.empty[s]), 3);
+                    mma_commit_mc_w(smem_u32(&ctl.empty[s]), 3);
                     ++it;
                 }
                 if (!ok) break;
-                mma_commit(smem_u32(&ctl.tfull[acc]));
+                mma_commit_w(smem_u32(&ctl.tfull[acc]));
                 ++t;
             }
             // everything issued has completed before the block releases TMEM
-            mma_commit(smem_u32(&ctl.done));
+            mma_commit_w(smem_u32(&ctl.done));
             mbar_drain(smem_u32(&ctl.done), 0);
         }
     } else {

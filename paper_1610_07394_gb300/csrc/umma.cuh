@@ -308,6 +308,16 @@ __device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
         : "memory");
 }
 
+// The multicast commit from a converged warp (one elected lane).
+__device__ __forceinline__ void mma_commit_mc_w(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;\n\t}" ::"r"(bar), "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t cols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
                  "r"(cols)
