@@ -459,6 +459,7 @@ struct AtmForceSmem {
     long long walk_w;           // the grid block being split into tiles
     long long walk_end;         // end of the run of grid blocks the block has claimed
     int walk_sub;               // the next tile of walk_w
+    int walk_pos[4];            // walk_w's place in the hand-out order (HandoutPos)
 };
 
 __device__ __forceinline__ void build_force_tables(int64_t n, int I, int J, int K, float eps,
@@ -616,23 +617,60 @@ __global__ void __launch_bounds__(256) k_atm_forcetab(int64_t n, const float *__
 // patch's span of tiles.  Which grid blocks exist, and the data blocks they
 // map to, are the map's; only the order in which the persistent blocks take
 // them changes.
-__device__ __forceinline__ void handout_block(int64_t c, int gx, int gy, int gz, uint32_t &x, uint32_t &y,
-                                              uint32_t &z) {
-    if ((gx & 7) == 0 && (gy & 7) == 0) {
+// A hand-out position c as counters that step to c + 1 without division:
+// patch order (gx, gy multiples of 8): a = offset in the 8 x 8 patch, b =
+// z-layer counted from the top, e, f = the patch's column and row; grid
+// order otherwise: a = x, b = y, e = z-layer counted from the top.  Set
+// from c (two divisions) once per claim.
+struct HandoutPos {
+    int a, b, e, f;
+};
+
+__device__ __forceinline__ bool patch_order(int gx, int gy) { return (gx & 7) == 0 && (gy & 7) == 0; }
+
+__device__ __forceinline__ HandoutPos handout_pos(int64_t c, int gx, int gy, int gz) {
+    HandoutPos h;
+    if (patch_order(gx, gy)) {
         const int64_t per_patch = 64 * (int64_t)gz;
         const int64_t patch = c / per_patch, r = c - patch * per_patch;
-        const int64_t layer = r >> 6, o = r & 63;
-        const int64_t pgx = gx >> 3, py = patch / pgx, px = patch - py * pgx;
-        x = (uint32_t)(8 * px + (o & 7));
-        y = (uint32_t)(8 * py + (o >> 3));
-        z = (uint32_t)(gz - 1 - layer);
+        const int pgx = gx >> 3;
+        h.a = (int)(r & 63);
+        h.b = (int)(r >> 6);
+        h.f = (int)(patch / pgx);
+        h.e = (int)(patch - (int64_t)h.f * pgx);
     } else {
         const int64_t gxy = (int64_t)gx * gy;
         const int64_t zz = c / gxy, rem = c - zz * gxy;
-        const int64_t yy = rem / gx;
-        x = (uint32_t)(rem - yy * gx);
-        y = (uint32_t)yy;
-        z = (uint32_t)(gz - 1 - zz);
+        h.b = (int)(rem / gx);
+        h.a = (int)(rem - (int64_t)h.b * gx);
+        h.e = (int)zz;
+        h.f = 0;
+    }
+    return h;
+}
+
+// Steps a patch-order position to the next one.
+__device__ __forceinline__ void handout_step(HandoutPos &h, int gx, int gz) {
+    if (++h.a == 64) {
+        h.a = 0;
+        if (++h.b == gz) {
+            h.b = 0;
+            if (++h.e == (gx >> 3)) { h.e = 0; ++h.f; }
+        }
+    }
+}
+
+// The grid block of a hand-out position (see grab_tile for the order).
+__device__ __forceinline__ void handout_block(const HandoutPos &h, int gx, int gy, int gz, uint32_t &x,
+                                              uint32_t &y, uint32_t &z) {
+    if (patch_order(gx, gy)) {
+        x = (uint32_t)(8 * h.e + (h.a & 7));
+        y = (uint32_t)(8 * h.f + (h.a >> 3));
+        z = (uint32_t)(gz - 1 - h.b);
+    } else {
+        x = (uint32_t)h.a;
+        y = (uint32_t)h.b;
+        z = (uint32_t)(gz - 1 - h.e);
     }
 }
 
@@ -642,11 +680,13 @@ __device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p
     const int64_t total = (int64_t)gx * gy * gz;
     long long w = S.walk_w, end = S.walk_end;
     int sub = S.walk_sub;
+    HandoutPos h{S.walk_pos[0], S.walk_pos[1], S.walk_pos[2], S.walk_pos[3]};
     int *out = S.tq[slot];
+    const bool patches = patch_order(gx, gy);
     for (;;) {
         if (w < end) {
             uint32_t bx, by, bz;
-            handout_block(w, gx, gy, gz, bx, by, bz);
+            handout_block(h, gx, gy, gz, bx, by, bz);
             const List3 L = decode3<MAP>(bx, by, bz, p, nb);
             if (sub < L.cnt) {
                 int I, J, K;
@@ -655,10 +695,17 @@ __device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p
                 S.walk_w = w;
                 S.walk_end = end;
                 S.walk_sub = sub + 1;
+                S.walk_pos[0] = h.a; S.walk_pos[1] = h.b; S.walk_pos[2] = h.e; S.walk_pos[3] = h.f;
                 return;
             }
             ++w;
             sub = 0;
+            if (patches) {
+                handout_step(h, gx, gz);
+            } else if (++h.a == gx) {
+                h.a = 0;
+                if (++h.b == gy) { h.b = 0; ++h.e; }
+            }
             continue;
         }
         // the next run of `claim` hand-out positions
@@ -672,6 +719,7 @@ __device__ void grab_tile(unsigned long long *ctr, int gx, int gy, int gz, int p
             S.walk_sub = 0;
             return;
         }
+        h = handout_pos(w, gx, gy, gz);
     }
 }
 
@@ -721,6 +769,7 @@ __global__ void __launch_bounds__(256, 2) k_atm_forces(int64_t n, const float *_
         S.walk_w = 0;
         S.walk_end = 0;
         S.walk_sub = 0;
+        S.walk_pos[0] = S.walk_pos[1] = S.walk_pos[2] = S.walk_pos[3] = 0;
         grab_tile<MAP>(ctr, gx, gy, gz, p, nb, claim, S, 0);
         grab_tile<MAP>(ctr, gx, gy, gz, p, nb, claim, S, 1);
     }
