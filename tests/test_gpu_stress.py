@@ -187,6 +187,25 @@ def test_stress_tensor_scale_config(gpu, oracle):
     assert row_err(gf.double().cpu().numpy(), G_all).max() <= TC_G_TOL
 
 
+@pytest.mark.parametrize("mp", ["lambda", "bbox"])
+def test_stress_tensor_bwd_padded_grid(gpu, oracle, mp):
+    """n = 49153, d = 64: nb = 385 tile rows, so the lambda map pads its grid
+    to 512 (idle grid blocks among the tiles) and the walk's prologue scans
+    128 blocks of 1024 grid blocks; the tiles are cut into equal chunks
+    across that sequence.  Every gradient row against the FP64 moment
+    identity, 8 rows against the oracle's pairwise sums."""
+    n, d = 49153, 64
+    x = synth.normal(n, d, seed=61)
+    y = synth.perturbed(x, 0.1, seed=62)
+    g = gpu.stress_bwd(to_gpu(x), to_gpu(y), 1.0, mp, "bf16x3").double().cpu().numpy()
+    gpu.simplex_device_errors()
+    _, G_all = stress_moments(x, y)
+    assert row_err(g, G_all).max() <= TC_G_TOL
+    rows = synth.sample_indices(8, n, seed=63)
+    assert row_err(g[rows], oracle.stress_grad_rows(x, y, rows)).max() <= TC_G_TOL
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("mp", ["lambda", "bbox", "linear", "rb"])
 @pytest.mark.parametrize("prec,n,d", [("fp32", 1, 4), ("fp32", 2, 1), ("fp32", 100, 8), ("fp32", 257, 64),
                                       ("bf16x3", 1, 32), ("bf16x3", 300, 64), ("bf16x3", 513, 96)])
