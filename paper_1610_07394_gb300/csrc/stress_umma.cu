@@ -573,7 +573,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&ctl.tempty[acc]));
-            float sq = 0.f;
 #pragma unroll
             for (int q = 0; q < 64; q += 4) {
                 const float4 aj = *reinterpret_cast<const float4 *>(ac + q);
@@ -582,10 +581,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int k = 0; k < 4; ++k) {
                     const float rq = (ai + al4[k]) - v[q + k];
                     v[q + k] = q + k < lim ? rq : 0.0f;
-                    sq = fmaf(v[q + k], v[q + k], sq);
                 }
             }
-            if (partials) add_ff(lhi, llo, sq, 0.f);
+            if (partials) {   // the loss from the same residuals (loss and gradient in one pass)
+                float sq = 0.f;
+#pragma unroll
+                for (int q = 0; q < 64; ++q) sq = fmaf(v[q], v[q], sq);
+                add_ff(lhi, llo, sq, 0.f);
+            }
             // the C buffer is free once GEMM2 of the previous tile has completed
             if (t >= 1 && !mbar_wait(smem_u32(&ctl.g2done), (t - 1) & 1, fail, &g_error)) break;
             tc_fence_after();
@@ -595,10 +598,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float f0 = v[8 * c + 2 * k], f1 = v[8 * c + 2 * k + 1];
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
-                    const __nv_bfloat162 hh = __halves2bfloat162(h0, h1);
+                    const __nv_bfloat162 hh = __floats2bfloat162_rn(f0, f1);   // both rounded at once
                     ph[k] = *reinterpret_cast<const uint32_t *>(&hh);
-                    pl[k] = pack_bf16(f0 - __bfloat162float(h0), f1 - __bfloat162float(h1));
+                    pl[k] = pack_bf16(f0 - __low2float(hh), f1 - __high2float(hh));
                 }
                 const int off = (c ^ (r & 7)) << 4;
                 *reinterpret_cast<uint4 *>(rowh + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
