@@ -212,44 +212,10 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
     return d;
 }
 
-// D (TMEM) (+)= A * B over K = 16, one instruction issued by one thread.
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// The same with matrix A kept in the tensor core's collector buffer for the
-// next MMA (fill), or taken from it and released (lastuse): two MMAs that
-// share A read it from shared memory once.
-__device__ __forceinline__ void mma_bf16_afill(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                               uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16_alast(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                               uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Warp-converged forms of the three MMAs and of the commit: the whole warp
-// executes them and one elected lane (the lowest active, the same one every
-// time) issues, so the descriptors can stay warp-uniform instead of being
-// computed in one lane of a divergent branch.
+// tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM), issued from a
+// converged warp: the whole warp executes the call and one elected lane (the
+// lowest active, the same one every time) issues, so the descriptors stay
+// warp-uniform instead of being computed in one lane of a divergent branch.
 __device__ __forceinline__ void mma_bf16_w(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                            uint32_t accumulate) {
     asm volatile(
@@ -261,6 +227,9 @@ __device__ __forceinline__ void mma_bf16_w(uint32_t tmem_d, uint64_t adesc, uint
         : "memory");
 }
 
+// The same with matrix A kept in the tensor core's collector buffer for the
+// next MMA (fill), or taken from it and released (lastuse): two MMAs that
+// share A read it from shared memory once.
 __device__ __forceinline__ void mma_bf16_afill_w(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                                  uint32_t idesc, uint32_t accumulate) {
     asm volatile(
@@ -283,6 +252,8 @@ __device__ __forceinline__ void mma_bf16_alast_w(uint32_t tmem_d, uint64_t adesc
         : "memory");
 }
 
+// Arrives on `bar` once every tcgen05 operation issued so far by the elected
+// lane has completed (from the same converged warp).
 __device__ __forceinline__ void mma_commit_w(uint32_t bar) {
     asm volatile(
         "{\n\t.reg .pred e;\n\t"
@@ -291,24 +262,7 @@ __device__ __forceinline__ void mma_commit_w(uint32_t bar) {
         : "memory");
 }
 
-// Arrives on `bar` once every tcgen05 operation issued so far by this thread
-// has completed.
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-// Arrives on the mbarrier at `bar` of every CTA of the cluster in `mask` once
-// every tcgen05 operation issued so far by this thread has completed.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(mask)
-        : "memory");
-}
-
-// The multicast commit from a converged warp (one elected lane).
+// The same on the mbarrier at `bar` of every CTA of the cluster in `mask`.
 __device__ __forceinline__ void mma_commit_mc_w(uint32_t bar, uint16_t mask) {
     asm volatile(
         "{\n\t.reg .pred e;\n\t"
