@@ -436,6 +436,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
             const uint32_t id_col = idesc_bf16(TM, NG, true, false);
+            const uint64_t dc = sw128_desc(s_c);                     // C, K-major (rows side)
+            const uint64_t dct = sw128_desc(s_c, TILE_BYTES, 1024);  // C read M-major (columns side)
             Walk walk(gx, nb, T, nchunks, start);
             uint32_t it = 0, t = 0, src;
             int X, Y, prevY = -1, prev2Y = -1;
@@ -459,34 +461,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t tgx = tmem + kGY + (uint32_t)NG * (1 + b);
                 // rows: G_Y (+)= C [X_X | 1], K = j over the two column halves of C
                 if (!ring_take<NS>(ctl, s_stages, it, src, fail)) return false;
+                const uint64_t dx = sw128_desc(src);
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint64_t ah = sw128_desc(s_c + h * TILE_BYTES + ks * 32);
-                        const uint64_t al = sw128_desc(s_c + (2 + h) * TILE_BYTES + ks * 32);
-                        const uint64_t bh = sw128_desc(src + h * xt_box + ks * 32);
-                        const uint64_t bl = sw128_desc(src + (2 + h) * xt_box + ks * 32);
                         const uint32_t acc = (h == 0 && ks == 0 && !sameY) ? 0u : 1u;
-                        mma_bf16_afill_w(tmem + kGY, ah, bh, id_row, acc);
-                        mma_bf16_alast_w(tmem + kGY, ah, bl, id_row, 1u);
-                        mma_bf16_w(tmem + kGY, al, bh, id_row, 1u);
+                        mma_bf16x3_w(tmem + kGY, desc_add(dc, h * TILE_BYTES + ks * 32),
+                                     desc_add(dc, (2 + h) * TILE_BYTES + ks * 32),
+                                     desc_add(dx, h * xt_box + ks * 32), desc_add(dx, (2 + h) * xt_box + ks * 32),
+                                     id_row, acc);
                     }
                 mma_commit_w(smem_u32(&ctl.empty[it % NS]));
                 ++it;
                 // columns: G_X = C^T [X_Y | 1], K = i; A is C read M-major (M = j
                 // over the two 64-column halves, LBO = one half tile apart)
                 if (!ring_take<NS>(ctl, s_stages, it, src, fail)) return false;
+                const uint64_t dy = sw128_desc(src);
 #pragma unroll
                 for (int ks = 0; ks < TM / 16; ++ks) {
-                    const uint64_t ah = sw128_desc(s_c + ks * 2048, TILE_BYTES, 1024);
-                    const uint64_t al = sw128_desc(s_c + 2 * TILE_BYTES + ks * 2048, TILE_BYTES, 1024);
                     const uint32_t hb = (uint32_t)(ks >> 2), kb = (uint32_t)(ks & 3) * 32;
-                    const uint64_t bh = sw128_desc(src + hb * xt_box + kb);
-                    const uint64_t bl = sw128_desc(src + (2 + hb) * xt_box + kb);
-                    mma_bf16_afill_w(tgx, ah, bh, id_col, ks ? 1u : 0u);
-                    mma_bf16_alast_w(tgx, ah, bl, id_col, 1u);
-                    mma_bf16_w(tgx, al, bh, id_col, 1u);
+                    mma_bf16x3_w(tgx, desc_add(dct, ks * 2048), desc_add(dct, 2 * TILE_BYTES + ks * 2048),
+                                 desc_add(dy, hb * xt_box + kb), desc_add(dy, (2 + hb) * xt_box + kb), id_col,
+                                 ks ? 1u : 0u);
                 }
                 mma_commit_w(smem_u32(&ctl.empty[it % NS]));
                 ++it;
@@ -500,16 +497,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t dtm = tmem + acc * TN;
                 for (int c = 0; c < nc1; ++c) {
                     if (!(ok = ring_take<NS>(ctl, s_stages, it, src, fail))) break;
+                    const uint64_t d0 = sw128_desc(src);   // P hi, P lo, Q hi, Q lo tiles of the stage
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ++ks) {
                         const uint32_t ko = ks * 32;
-                        const uint64_t ah = sw128_desc(src + ko);
-                        const uint64_t al = sw128_desc(src + TILE_BYTES + ko);
-                        const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + ko);
-                        const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + ko);
-                        mma_bf16_afill_w(dtm, ah, bh, id1, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast_w(dtm, ah, bl, id1, 1u);
-                        mma_bf16_w(dtm, al, bh, id1, 1u);
+                        mma_bf16x3_w(dtm, desc_add(d0, ko), desc_add(d0, TILE_BYTES + ko),
+                                     desc_add(d0, 2 * TILE_BYTES + ko), desc_add(d0, 3 * TILE_BYTES + ko), id1,
+                                     (c > 0 || ks > 0) ? 1u : 0u);
                     }
                     mma_commit_w(smem_u32(&ctl.empty[it % NS]));
                     ++it;

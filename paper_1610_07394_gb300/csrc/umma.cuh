@@ -178,6 +178,24 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// The three products of a BF16 hi + lo step, D (+)= Ah Bh + Ah Bl + Al Bh, for
+// a converged warp: one elected lane issues all three (A hi kept in the
+// collector buffer for the second product); the first accumulates into D
+// when `accumulate` is non-zero, the other two always.
+__device__ __forceinline__ void mma_bf16x3_w(uint32_t tmem_d, uint64_t ah, uint64_t al, uint64_t bh,
+                                             uint64_t bl, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p, e, t;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "setp.eq.b32 t, %6, %6;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %3, %5, p;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %4, %5, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %5, t;\n\t}" ::"r"(tmem_d),
+        "l"(ah), "l"(al), "l"(bh), "l"(bl), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor of an operand tile in the 128-byte swizzle
 // layout (8 rows of 128 bytes per 1024-byte atom, 16-byte chunks of row r
 // XOR-permuted by r mod 8; tile base 1024-byte aligned, so base offset 0):
@@ -198,6 +216,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo = 16
     d |= (uint64_t)2 << 61;
     return d;
 }
+
+// The descriptor of the tile `bytes` further on: the start address field
+// (bits 0-13, address >> 4) advanced, valid while the address stays inside
+// the 256 KB shared window (no carry out of the field) and `bytes` is a
+// multiple of 16.
+__device__ __forceinline__ uint64_t desc_add(uint64_t desc, uint32_t bytes) { return desc + (bytes >> 4); }
 
 // The same for an operand tile in the 64-byte swizzle layout (8 rows of 64
 // bytes per 512-byte atom, 16-byte chunks of row r XOR-permuted by
