@@ -235,16 +235,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                     if (!(ok = mbar_wait(smem_u32(&ctl.full[s]), (it / kStages) & 1, fail, &g_error))) break;
                     tc_fence_after();
                     const uint32_t src = s_stage + s * PSTAGE;
+                    const uint64_t d0 = sw64_desc(src);
 #pragma unroll
                     for (int ks = 0; ks < KC2 / 16; ++ks) {
                         const uint32_t koff = ks * 32;
-                        const uint64_t ah = sw64_desc(src + koff);
-                        const uint64_t al = sw64_desc(src + SUB + koff);
-                        const uint64_t bh = sw64_desc(src + 2 * SUB + koff);
-                        const uint64_t bl = sw64_desc(src + 4 * SUB + koff);
-                        mma_bf16_afill_w(dtm, ah, bh, kIdesc256, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast_w(dtm, ah, bl, kIdesc256, 1u);
-                        mma_bf16_w(dtm, al, bh, kIdesc256, 1u);
+                        mma_bf16x3_w(dtm, desc_add(d0, koff), desc_add(d0, SUB + koff), desc_add(d0, 2 * SUB + koff),
+                                     desc_add(d0, 4 * SUB + koff), kIdesc256, (c > 0 || ks > 0) ? 1u : 0u);
                     }
                     // the stage is free once this CTA's MMAs and the peer's have read it
                     mma_commit_mc_w(smem_u32(&ctl.empty[s]), 3);
@@ -606,16 +602,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma_wide(const __grid_cons
                             break;
                         tc_fence_after();
                         const uint32_t src = s_stages + s * STAGE_BYTES;
+                        const uint64_t d0 = sw128_desc(src);   // A hi, A lo, B hi, B lo tiles of the stage
 #pragma unroll
                         for (int ks = 0; ks < KC / 16; ++ks) {
                             const uint32_t koff = ks * 32;
-                            const uint64_t ah = sw128_desc(src + 0 * TILE_BYTES + koff);
-                            const uint64_t al = sw128_desc(src + 1 * TILE_BYTES + koff);
-                            const uint64_t bh = sw128_desc(src + 2 * TILE_BYTES + koff);
-                            const uint64_t bl = sw128_desc(src + 3 * TILE_BYTES + koff);
-                            mma_bf16_afill_w(dtm, ah, bh, kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
-                            mma_bf16_alast_w(dtm, ah, bl, kIdesc, 1u);
-                            mma_bf16_w(dtm, al, bh, kIdesc, 1u);
+                            mma_bf16x3_w(dtm, desc_add(d0, koff), desc_add(d0, TILE_BYTES + koff),
+                                         desc_add(d0, 2 * TILE_BYTES + koff), desc_add(d0, 3 * TILE_BYTES + koff),
+                                         kIdesc, (c > 0 || ks > 0) ? 1u : 0u);
                         }
                         mma_commit_w(smem_u32(&ctl.empty[s]));
                     }

@@ -768,16 +768,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!(ok = mbar_wait(smem_u32(&ctl.full[s]), (it / NS) & 1, fail, &g_error))) break;
                     tc_fence_after();
                     const uint32_t src = s_stages + s * STAGE;
+                    const uint64_t d0 = sw128_desc(src);
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ++ks) {
                         const uint32_t ko = ks * 32;
-                        const uint64_t ah = sw128_desc(src + ko);
-                        const uint64_t al = sw128_desc(src + A_BYTES + ko);
-                        const uint64_t bh = sw128_desc(src + 2 * A_BYTES + ko);
-                        const uint64_t bl = sw128_desc(src + 2 * A_BYTES + B_BYTES + ko);
-                        mma_bf16_afill_w(dtm, ah, bh, id, (c > 0 || ks > 0) ? 1u : 0u);
-                        mma_bf16_alast_w(dtm, ah, bl, id, 1u);
-                        mma_bf16_w(dtm, al, bh, id, 1u);
+                        mma_bf16x3_w(dtm, desc_add(d0, ko), desc_add(d0, A_BYTES + ko), desc_add(d0, 2 * A_BYTES + ko),
+                                     desc_add(d0, 2 * A_BYTES + B_BYTES + ko), id, (c > 0 || ks > 0) ? 1u : 0u);
                     }
                     // the stage is free once this CTA's MMAs and the peer's have read it
                     mma_commit_mc_w(smem_u32(&ctl.empty[s]), 3);

@@ -178,10 +178,14 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// The three products of a BF16 hi + lo step, D (+)= Ah Bh + Ah Bl + Al Bh, for
-// a converged warp: one elected lane issues all three (A hi kept in the
-// collector buffer for the second product); the first accumulates into D
-// when `accumulate` is non-zero, the other two always.
+// tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM): the three
+// products of a BF16 hi + lo step, D (+)= Ah Bh + Ah Bl + Al Bh, issued from a
+// converged warp.  The whole warp executes the call and one elected lane (the
+// lowest active, the same one every time) issues all three, so the
+// descriptors stay warp-uniform and the step costs one election; A hi is
+// kept in the tensor core's collector buffer for the second product (fill,
+// then lastuse), so it is read from shared memory once.  The first product
+// accumulates into D when `accumulate` is non-zero, the other two always.
 __device__ __forceinline__ void mma_bf16x3_w(uint32_t tmem_d, uint64_t ah, uint64_t al, uint64_t bh,
                                              uint64_t bl, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
@@ -234,46 +238,6 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)4 << 61;
     return d;
-}
-
-// tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM), issued from a
-// converged warp: the whole warp executes the call and one elected lane (the
-// lowest active, the same one every time) issues, so the descriptors stay
-// warp-uniform instead of being computed in one lane of a divergent branch.
-__device__ __forceinline__ void mma_bf16_w(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                           uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p, e;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// The same with matrix A kept in the tensor core's collector buffer for the
-// next MMA (fill), or taken from it and released (lastuse): two MMAs that
-// share A read it from shared memory once.
-__device__ __forceinline__ void mma_bf16_afill_w(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                                 uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p, e;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_bf16_alast_w(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                                 uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p, e;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
 }
 
 // Arrives on `bar` once every tcgen05 operation issued so far by the elected
