@@ -22,13 +22,15 @@ SX_HD void table_entry(int map, const Grid &g, int nb, int64_t w, int32_t *e) {
                 : map == MAP_BBOX   ? decode2_bbox(wx, wy, nb)
                 : map == MAP_RB     ? decode2_rb(wx, wy, nb)
                                     : decode2_linear(w, nb);
-        for (int t = 0; t < L.cnt; ++t) { e[2 * t] = L.x[t]; e[2 * t + 1] = L.y[t]; }
+        for (int t = 0; t < L.cnt; ++t) { e[2 * t] = t ? L.x[1] : L.x[0]; e[2 * t + 1] = t ? L.y[1] : L.y[0]; }
     } else {
         List3 L = map == MAP_LAMBDA ? decode3_lambda(wx, wy, wz, g.p, nb)
                 : map == MAP_BBOX   ? decode3_bbox(wx, wy, wz, nb)
                                     : decode3_linear(w, nb);
         for (int t = 0; t < L.cnt; ++t) {
-            e[3 * t] = L.i[t]; e[3 * t + 1] = L.j[t]; e[3 * t + 2] = L.k[t];
+            e[3 * t] = t ? L.i[1] : L.i[0];
+            e[3 * t + 1] = t ? L.j[1] : L.j[0];
+            e[3 * t + 2] = t ? L.k[1] : L.k[0];
         }
     }
 }
@@ -96,7 +98,8 @@ __global__ void k_cover3(int64_t n, int rho, int nb, int p, int32_t *count,
         // n <= 3,000,000 (checked by simplex_map3): the coordinates fit in
         // 32 bits; the tetrahedral number k(k+1)/2 * (k+2) / 3 stays below
         // 2^64 in unsigned 64-bit arithmetic
-        const int i = L.i[t] * rho + a, j = L.j[t] * rho + b, k = L.k[t] * rho + c;
+        const int i = (t ? L.i[1] : L.i[0]) * rho + a, j = (t ? L.j[1] : L.j[0]) * rho + b,
+                  k = (t ? L.k[1] : L.k[0]) * rho + c;
         if (i <= j && j <= k && k < n) {
             const uint64_t kk = (uint32_t)k, jj = (uint32_t)j;
             const uint64_t tet_k = kk * (kk + 1) / 2 * (kk + 2) / 3;
@@ -167,7 +170,9 @@ __global__ void k_cover4_plane(int64_t n, int nb, int p3, int32_t *count, unsign
     const List3 L = decode3<MAP_LAMBDA>(blockIdx.x, blockIdx.y, blockIdx.z, p3, nb);
     bool took = false;
     for (int t = 0; t < L.cnt; ++t) {
-        const int i = L.i[t] * RHO + a, j = L.j[t] * RHO + b, k = L.k[t] * RHO + c, l = L.k[t] * RHO + d;
+        const int Kb = t ? L.k[1] : L.k[0];
+        const int i = (t ? L.i[1] : L.i[0]) * RHO + a, j = (t ? L.j[1] : L.j[0]) * RHO + b, k = Kb * RHO + c,
+                  l = Kb * RHO + d;
         if (i <= j && j <= k && k <= l && l < n) {
             atomicAdd(count + index4(i, j, k, l), 1);
             took = true;

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_edm_simt(int64_t n, int d, const float 
         return;
     }
     for (int t = 0; t < L.cnt; ++t) {
-        const int64_t row0 = (int64_t)L.y[t] * kEdmRho, col0 = (int64_t)L.x[t] * kEdmRho;
+        const int64_t row0 = (int64_t)(t ? L.y[1] : L.y[0]) * kEdmRho, col0 = (int64_t)(t ? L.x[1] : L.x[0]) * kEdmRho;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         tile_sqdist(x, n, d, row0, col0, sm, acc);
         const int64_t j = col0 + lane;

@@ -108,12 +108,17 @@ SX_HD void push3(List3 &L, int i, int j, int k, int nb) {
 SX_HD List2 decode2_lambda(uint32_t wx, uint32_t wy, int nb) {
     List2 L;
     L.cnt = 0; L.pair = false; L.d0 = L.d1 = -1;
+    L.x[0] = L.x[1] = L.y[0] = L.y[1] = 0;
     if (wy == 0) {
+        // the diagonal pair (d0, d0), (d1, d1) with d1 = d0 + 1, each kept if
+        // below nb: the kept ones are a prefix, so the list is written with
+        // constant indices (a data-dependent index would put it in local memory)
         L.pair = true;
         L.d0 = (int)(2 * wx);
         L.d1 = (int)(2 * wx + 1);
-        push2(L, L.d0, L.d0, nb);
-        push2(L, L.d1, L.d1, nb);
+        L.x[0] = L.y[0] = L.d0;
+        L.x[1] = L.y[1] = L.d1;
+        L.cnt = (L.d0 < nb ? 1 : 0) + (L.d1 < nb ? 1 : 0);
         return L;
     }
     const int l = floor_log2(wy);        // recursion level: b = 2^l
