@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_edm_umma(const __grid_constant_
                 const int X = 2 * sX + u;
                 const bool valid = X <= Y && Y < nb;
                 const int64_t row0 = (int64_t)Y * TM, col0 = (int64_t)X * TN;
-                const float pa = pcn[2 * u], pb = pcn[2 * u + 1], ni = prn;
+                const float pa = u ? pcn[2] : pcn[0], pb = u ? pcn[3] : pcn[1], ni = prn;   // constant indices
                 __syncwarp();   // the previous half-step's reads of nc are done
                 nc[lane] = pa;
                 nc[lane + 32] = pb;
