@@ -431,7 +431,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer: the whole warp, converged, so the
-        // descriptors stay warp-uniform; one elected lane issues
+        // descriptors stay warp-uniform; one elected lane issues each BF16
+        // step's three products at once, from descriptors stepped off a
+        // per-stage base.  The warp shares its scheduler with two epilogue
+        // warps and a 128 x 80 x 16 MMA of GEMM2 runs about 40 cycles, so the
+        // instructions between MMAs decide whether the tensor pipe idles.
         {
             const uint32_t id1 = idesc_bf16(TM, TN, false, false);
             const uint32_t id_row = idesc_bf16(TM, NG, false, false);
