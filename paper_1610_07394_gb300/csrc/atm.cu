@@ -499,7 +499,7 @@ struct PairPack {
 //   e = g (2/3 + 2 Cp),  de/da = g (S - 2 Z - H q_a), ...
 // The energy goes to acc, de/da to wa (summed over k in registers), de/dc to
 // ecs (summed over the thread's two j) and de/db, summed over the two
-// i-lanes, is returned.  32 packed operations and one scalar add.
+// i-lanes, is returned.  31 packed operations and one scalar add.
 __device__ __forceinline__ float triple_grad2(const PairPack &c, float4 C0, float4 C1, float4 C2,
                                               float4 B0, float4 B1, float4 B2, float2 &acc,
                                               float2 &wa, float2 &ecs) {
@@ -510,10 +510,11 @@ __device__ __forceinline__ float triple_grad2(const PairPack &c, float4 C0, floa
     const float2 pi = fma2(c.wx, cx, fma2(c.wy, cy, mul2(c.wz, cz)));
     const float2 pj = fma2(c.wx, bx, fma2(c.wy, by, mul2(c.wz, bz)));
     const float2 pk = fma2(cx, bx, fma2(cy, by, mul2(cz, bz)));
-    const float2 xn = mul2(mul2(pj, pk), sb);               // -X
-    const float2 y = mul2(mul2(pi, pk), sc);                //  Y
+    const float2 t1 = mul2(pk, sb), t2 = mul2(pk, sc);     // shared by X, Y and Cp
+    const float2 xn = mul2(pj, t1);                         // -X
+    const float2 y = mul2(pi, t2);                          //  Y
     const float2 zn = mul2(mul2(pi, pj), c.sa);             // -Z
-    const float2 cpn = mul2(mul2(zn, pk), mul2(sb, sc));    // -Cp
+    const float2 cpn = mul2(mul2(zn, t1), sc);              // -Cp = -Z pk sb sc
     const float2 g = mul2(c.ga, mul2(rb3, rc3));            // 1.5 R^3
     acc = fma2(g, fma2(f2(-2.0f, -2.0f), cpn, f2(2.0f / 3.0f, 2.0f / 3.0f)), acc);
     const float2 nh = fma2(f2(5.0f, 5.0f), cpn, f2(-1.0f, -1.0f));   // -H
