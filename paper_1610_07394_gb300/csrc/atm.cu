@@ -499,7 +499,7 @@ struct PairPack {
 //   e = g (2/3 + 2 Cp),  de/da = g (S - 2 Z - H q_a), ...
 // The energy goes to acc, de/da to wa (summed over k in registers), de/dc to
 // ecs (summed over the thread's two j) and de/db, summed over the two
-// i-lanes, is returned.  31 packed operations and one scalar add.
+// i-lanes, is returned.  33 packed operations and one scalar add.
 __device__ __forceinline__ float triple_grad2(const PairPack &c, float4 C0, float4 C1, float4 C2,
                                               float4 B0, float4 B1, float4 B2, float2 &acc,
                                               float2 &wa, float2 &ecs) {
