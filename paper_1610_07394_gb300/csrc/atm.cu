@@ -499,7 +499,7 @@ struct PairPack {
 //   e = g (2/3 + 2 Cp),  de/da = g (S - 2 Z - H q_a), ...
 // The energy goes to acc, de/da to wa (summed over k in registers), de/dc to
 // ecs (summed over the thread's two j) and de/db, summed over the two
-// i-lanes, is returned.  33 packed operations and one scalar add.
+// i-lanes, is returned.  32 packed operations and one scalar add.
 __device__ __forceinline__ float triple_grad2(const PairPack &c, float4 C0, float4 C1, float4 C2,
                                               float4 B0, float4 B1, float4 B2, float2 &acc,
                                               float2 &wa, float2 &ecs) {
@@ -518,10 +518,13 @@ __device__ __forceinline__ float triple_grad2(const PairPack &c, float4 C0, floa
     const float2 g = mul2(c.ga, mul2(rb3, rc3));            // 1.5 R^3
     acc = fma2(g, fma2(f2(-2.0f, -2.0f), cpn, f2(2.0f / 3.0f, 2.0f / 3.0f)), acc);
     const float2 nh = fma2(f2(5.0f, 5.0f), cpn, f2(-1.0f, -1.0f));   // -H
-    const float2 sg = fma2(add2(xn, zn), f2(-1.0f, -1.0f), y);        //  S
-    wa = fma2(g, fma2(nh, c.qa, fma2(f2(2.0f, 2.0f), zn, sg)), wa);
-    ecs = fma2(g, fma2(nh, qc, fma2(f2(-2.0f, -2.0f), y, sg)), ecs);
-    const float2 eb = mul2(g, fma2(nh, qb, fma2(f2(2.0f, 2.0f), xn, sg)));
+    // S - 2Z, S - 2Y, S - 2X with S = X + Y + Z, from w = S - 2X = y + xn - zn:
+    // S - 2Z = 2y - w, S - 2Y = -2zn - w (the negated addend folds into the FMA)
+    const float2 w = add2(fma2(zn, f2(-1.0f, -1.0f), y), xn);
+    const float2 nw = f2(-w.x, -w.y);
+    wa = fma2(g, fma2(nh, c.qa, fma2(f2(2.0f, 2.0f), y, nw)), wa);
+    ecs = fma2(g, fma2(nh, qc, fma2(f2(-2.0f, -2.0f), zn, nw)), ecs);
+    const float2 eb = mul2(g, fma2(nh, qb, w));
     return eb.x + eb.y;
 }
 
