@@ -79,53 +79,3 @@ __device__ __forceinline__ void pair_sqdist(const float *__restrict__ x, int64_t
 }
 
 }  // namespace sx
-
-namespace sx {
-
-// Residual of two configurations, r_ij = |x_i - x_j|^2 - |y_i - y_j|^2, as
-// sum_t (S_it - S_jt)(Delta_it - Delta_jt) with Delta = x - y and S = x + y
-// staged per point: a difference of squares per coordinate, so the
-// cancellation between the two squared distances never happens.
-struct ResidSmem {
-    float dr[32][33], dc[32][33];   // Delta of the row / column tile
-    float sr[32][33], sc[32][33];   // S of the row / column tile
-};
-
-__device__ __forceinline__ void load_resid_chunk(const float *__restrict__ x,
-                                                 const float *__restrict__ y, int64_t n, int d,
-                                                 int64_t p0, int c0, int dc, float (*dd)[33],
-                                                 float (*ss)[33]) {
-    for (int e = threadIdx.x; e < 32 * dc; e += 256) {
-        const int rr = e / dc, cc = e - rr * dc;
-        const int64_t p = p0 + rr;
-        float xv = 0.f, yv = 0.f;
-        if (p < n) { xv = __ldg(x + p * d + c0 + cc); yv = __ldg(y + p * d + c0 + cc); }
-        dd[rr][cc] = xv - yv;
-        ss[rr][cc] = xv + yv;
-    }
-}
-
-// acc[m] += r_{row0+w+8m, col0+lane} over all d coordinates.
-__device__ __forceinline__ void tile_resid(const float *__restrict__ x, const float *__restrict__ y,
-                                           int64_t n, int d, int64_t row0, int64_t col0,
-                                           ResidSmem &sm, float acc[4]) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int c0 = 0; c0 < d; c0 += 32) {
-        const int dc = d - c0 < 32 ? d - c0 : 32;
-        __syncthreads();
-        load_resid_chunk(x, y, n, d, row0, c0, dc, sm.dr, sm.sr);
-        load_resid_chunk(x, y, n, d, col0, c0, dc, sm.dc, sm.sc);
-        __syncthreads();
-        for (int cc = 0; cc < dc; ++cc) {
-            const float dj = sm.dc[lane][cc], sj = sm.sc[lane][cc];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const float t = sm.dr[w + 8 * m][cc] - dj;
-                const float s = sm.sr[w + 8 * m][cc] - sj;
-                acc[m] = fmaf(s, t, acc[m]);
-            }
-        }
-    }
-}
-
-}  // namespace sx
